@@ -1,0 +1,691 @@
+"""Plain FP64 CPU oracle of the time-dependent SLDA (TDSLDA) step.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference leg may import or run anything in this package. The
+product path (the CUDA library and its Python binding) never does, and this
+package never imports the product.
+
+Everything here is double precision, written for a reader who checks it against
+the paper (W-SLDA Toolkit, arXiv 2602.08982) by eye: no blocking, no fusion.
+Library primitives used as single steps: scipy.fft (the discrete Fourier
+transform), numpy reductions, scipy root finders and quadrature.
+
+Conventions (units m = hbar = k_B = 1, Sec. 2.1):
+  * a quasiparticle state is the pair (u_n, v_n) of the reduced problem
+    (Eq. HpsiEpsi), stored as phi[n, 0, :] = u_n, phi[n, 1, :] = v_n over the
+    flattened lattice index (ix * NY + iy) * NZ + iz (x slowest, z fastest);
+  * states are normalised as sum_r dV (|u|^2 + |v|^2) = 1;
+  * spin-symmetric system, only E_n > 0 states are stored (Sec. 2.3).
+
+Readings of points where the paper is silent or ambiguous are marked
+"Reading <ID>" and are the same as the CUDA path's.
+
+Parity pins: every function here is pinned by a test in tests/test_oracle_pins.py
+against closed forms, printed numbers, textbook limits, invariants or brute
+force. Partial pin: the SLDA constants used with A forced to 1 (Sec. 2.4,
+"A_sigma = 1" option) have no printed number; the functional form they enter
+is pinned through the A = 1.094 uniform solution instead.
+"""
+from __future__ import annotations
+
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.fft as sfft
+
+WORKERS = max(1, os.cpu_count() or 1)
+_AXES = (-3, -2, -1)
+
+
+# ----------------------------------------------------------------------------
+# Lattice (Sec. 3.1)
+# ----------------------------------------------------------------------------
+@dataclass
+class Lattice:
+    nx: int
+    ny: int
+    nz: int
+    dx: float = 1.0
+    dy: float = 1.0
+    dz: float = 1.0
+
+    @property
+    def shape(self):
+        return (self.nx, self.ny, self.nz)
+
+    @property
+    def M(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def dV(self) -> float:
+        return self.dx * self.dy * self.dz
+
+    @property
+    def volume(self) -> float:
+        return self.M * self.dV
+
+    def kaxis(self, axis: int) -> np.ndarray:
+        """Fourier grid k_l = 2 pi l / L for l < N/2, 2 pi (l - N) / L otherwise
+        (Sec. 3.1, Fourier components; N even)."""
+        n = self.shape[axis]
+        d = (self.dx, self.dy, self.dz)[axis]
+        L = n * d
+        l = np.arange(n)
+        return np.where(l < n // 2, 2 * np.pi * l / L, 2 * np.pi * (l - n) / L)
+
+    def k2(self) -> np.ndarray:
+        """|k|^2 on the 3D grid, the Nyquist mode kept (k = -pi/dx at l = N/2)."""
+        kx, ky, kz = (self.kaxis(a) for a in range(3))
+        return kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+
+
+def fft3(a):
+    return sfft.fftn(a, axes=_AXES, workers=WORKERS)
+
+
+def ifft3(a):
+    return sfft.ifftn(a, axes=_AXES, workers=WORKERS)
+
+
+def laplacian(f: np.ndarray, lat: Lattice) -> np.ndarray:
+    """Spectral second derivative summed over axes (Eq. derivative-spectral, r = 2).
+
+    `f` has trailing shape [M] (flattened) and any leading batch shape."""
+    lead = f.shape[:-1]
+    g = f.reshape(lead + lat.shape)
+    out = ifft3(-lat.k2() * fft3(g))
+    return out.reshape(lead + (lat.M,))
+
+
+def gradient(f: np.ndarray, lat: Lattice):
+    """Spectral first derivatives (Eq. derivative-spectral, r = 1) with the
+    Nyquist contribution set to zero, as the paper prescribes for odd r."""
+    lead = f.shape[:-1]
+    fk = fft3(f.reshape(lead + lat.shape))
+    out = []
+    for ax in range(3):
+        k = lat.kaxis(ax).copy()
+        k[lat.shape[ax] // 2] = 0.0
+        s = [1, 1, 1]
+        s[ax] = -1
+        out.append(ifft3(1j * k.reshape(s) * fk).reshape(lead + (lat.M,)))
+    return out
+
+
+def derivative_matrix_1d(n: int, d: float, order: int) -> np.ndarray:
+    """Closed-form derivative matrices D^(1), D^(2) of Eqs. D1 and D2 (one axis)."""
+    L = n * d
+    l = np.arange(n)
+    diff = l[:, None] - l[None, :]
+    off = diff != 0
+    D = np.zeros((n, n))
+    sgn = np.where(diff % 2 == 0, 1.0, -1.0)
+    if order == 1:
+        D[off] = (np.pi / L) * sgn[off] / np.tan(np.pi * diff[off] / n)
+    elif order == 2:
+        D[off] = (2 * np.pi ** 2 / L ** 2) * (-sgn[off]) / np.sin(np.pi * diff[off] / n) ** 2
+        D[~off] = -(np.pi ** 2 / (3 * d ** 2)) * (1 + 2.0 / n ** 2)
+    else:
+        raise ValueError(order)
+    return D
+
+
+def dense_laplacian(lat: Lattice) -> np.ndarray:
+    """M x M Laplacian assembled from Eq. D2 along each axis (Sec. 3.3, matrix form)."""
+    Dx = derivative_matrix_1d(lat.nx, lat.dx, 2)
+    Dy = derivative_matrix_1d(lat.ny, lat.dy, 2)
+    Dz = derivative_matrix_1d(lat.nz, lat.dz, 2)
+    Ix, Iy, Iz = np.eye(lat.nx), np.eye(lat.ny), np.eye(lat.nz)
+    return (np.kron(np.kron(Dx, Iy), Iz) + np.kron(np.kron(Ix, Dy), Iz)
+            + np.kron(np.kron(Ix, Iy), Dz))
+
+
+# ----------------------------------------------------------------------------
+# Energy density functional (Sec. 2.4) and regularisation (Sec. 2.6)
+# ----------------------------------------------------------------------------
+C_ASLDA = -11.11  # C(p) of the ASLDA functional
+
+
+def aslda_A(p):
+    """A_a(p) of the ASLDA functional (Sec. 2.4)."""
+    return 1.094 + 0.156 * p * (1 - 2 * p ** 2 / 3 + p ** 4 / 5) - 0.532 * p ** 2 * (1 - p ** 2 + p ** 4 / 3)
+
+
+def aslda_B(p):
+    """B(p) of the ASLDA functional (Sec. 2.4); A_b(p) = A_a(-p)."""
+    return 2 ** (2.0 / 3.0) * (0.357 + 0.642 * p ** 2 - aslda_A(p) * ((1 + p) / 2) ** (5.0 / 3.0)
+                                - aslda_A(-p) * ((1 - p) / 2) ** (5.0 / 3.0))
+
+
+B_SLDA = float(aslda_B(0.0))  # spin-symmetric SLDA value, approx -0.5273
+
+
+def fermi_energy(rho_total):
+    """eF(rho) = (3 pi^2 rho)^(2/3) / 2 with rho = rho_a + rho_b (Sec. 2.4)."""
+    return 0.5 * (3 * np.pi ** 2 * rho_total) ** (2.0 / 3.0)
+
+
+def lattice_cutoff(lat: Lattice) -> float:
+    """Default cutoff energy of the regulator (Sec. 2.6).
+
+    Reading R5: the evolved set is all M lattice states, whose kinetic energies
+    reach the corner of the Brillouin zone, (pi^2/2)(1/dx^2 + 1/dy^2 + 1/dz^2)
+    = 3 k_c^2 / 2 on a cubic lattice; Sec. 2.6 notes that energy conservation
+    with all states needs E_c >= 3 k_c^2 / 2, so that value is the default."""
+    return 0.5 * np.pi ** 2 * (1 / lat.dx ** 2 + 1 / lat.dy ** 2 + 1 / lat.dz ** 2)
+
+
+def lambda_c(mu_minus_V, ec: float, A: float = 1.0):
+    """Regulator Lambda_c of Eq. Creg (Sec. 2.6), pointwise.
+
+    k_0 and k_c solve A k_0^2/2 + V - mu = 0 and A k_c^2/2 + V - mu = E_c.
+    Lambda_c is the principal-value integral (1/2 pi^2) int_0^kc k^2 dk /
+    (A k^2 - A k_0^2), which the printed logarithmic form evaluates for k_0^2 > 0.
+    Reading R3: for k_0^2 < 0 (classically forbidden, mu < V) the same integral
+    has no pole and gives 1 - (kappa/k_c) arctan(k_c/kappa), kappa^2 = -k_0^2;
+    for k_c^2 <= 0 the regulator is 0."""
+    x = np.asarray(mu_minus_V, dtype=np.float64)
+    k0sq = 2.0 * x / A
+    kcsq = 2.0 * (ec + x) / A
+    out = np.zeros_like(x)
+    ok = kcsq > 0
+    kc = np.sqrt(np.where(ok, kcsq, 1.0))
+    pos = ok & (k0sq > 0)
+    neg = ok & (k0sq < 0)
+    zer = ok & (k0sq == 0)
+    k0 = np.sqrt(np.where(pos, k0sq, 0.0))
+    kap = np.sqrt(np.where(neg, -k0sq, 0.0))
+    pref = kc / (2 * np.pi ** 2 * A)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        br_pos = 1.0 - (k0 / (2 * kc)) * np.log((kc + k0) / (kc - k0))
+        br_neg = 1.0 - (kap / kc) * np.arctan2(kc, kap)
+    out = np.where(pos, pref * br_pos, out)
+    out = np.where(neg, pref * br_neg, out)
+    out = np.where(zer, pref, out)
+    return out
+
+
+@dataclass
+class Functional:
+    """SLDA with A forced to 1 ('slda', Sec. 2.4 last paragraph) or BdG ('bdg').
+
+    slda: E_0 = tau_a/2 + tau_b/2 + 3/5 B rho eF(rho) + g_eff |nu|^2
+    bdg : A = 1, B = 0, coupling 4 pi a (Eq. HBdG)
+    Reading R1: 1/g_eff = rho^(1/3)/C - Lambda_c (slda) or 1/(4 pi a) - Lambda_c
+    (bdg); Delta = -g_eff nu (Eq. Delta)."""
+    kind: str = "slda"
+    B: float = B_SLDA
+    C: float = C_ASLDA
+    inv_4pi_a: float = 0.0
+    mu: float = 0.0
+    ec: float = -1.0          # <= 0 selects lattice_cutoff() (reading R5)
+    rho_floor: float = 1e-12  # Reading R4
+
+    def cutoff(self, lat: Lattice) -> float:
+        return self.ec if self.ec > 0 else lattice_cutoff(lat)
+
+
+def inverse_coupling(rho_sigma, lam, fn: Functional):
+    """1/g_eff at each site (Eq. Creg, reading R1)."""
+    if fn.kind == "slda":
+        rho = np.maximum(2.0 * rho_sigma, fn.rho_floor)
+        return rho ** (1.0 / 3.0) / fn.C - lam
+    return fn.inv_4pi_a - lam
+
+
+def mean_field(rho_sigma, delta, fn: Functional):
+    """U = dE_0/d rho_sigma for A = 1 (derived from Eq. sldae-functional with
+    Lambda_c held fixed): B eF(rho) - |Delta|^2 / (3 C rho^(2/3)); 0 for BdG."""
+    if fn.kind == "slda":
+        rho = np.maximum(2.0 * rho_sigma, fn.rho_floor)
+        return fn.B * fermi_energy(rho) - np.abs(delta) ** 2 / (3.0 * fn.C * rho ** (2.0 / 3.0))
+    return np.zeros_like(np.asarray(rho_sigma, dtype=np.float64))
+
+
+def potentials(rho_sigma, nu, lam, fn: Functional):
+    """(U, Delta, g_eff) from the densities with a given regulator field."""
+    g = 1.0 / inverse_coupling(rho_sigma, lam, fn)
+    delta = -g * nu
+    U = mean_field(rho_sigma, delta, fn)
+    return U, delta, g
+
+
+REGULATOR_ITERS = 60
+
+
+def frozen_regulator(rho_sigma, nu, vext, fn: Functional, lat: Lattice, iters: int = REGULATOR_ITERS):
+    """Reading R2: the regulator used during time evolution is fixed at t = 0.
+
+    Lambda_c depends on V = U + V_ext, and U depends on Lambda_c through g_eff;
+    the t = 0 value is the fixed point of that loop, reached by `iters` plain
+    iterations started from U = 0 (the same count on the GPU side)."""
+    ec = fn.cutoff(lat)
+    U = np.zeros_like(vext)
+    for _ in range(iters):
+        lam = lambda_c(fn.mu - U - vext, ec)
+        U, _, _ = potentials(rho_sigma, nu, lam, fn)
+    return lambda_c(fn.mu - U - vext, ec)
+
+
+# ----------------------------------------------------------------------------
+# Densities (Eqs. nab3D - jab3D, spin-symmetric, frozen weights Sec. 2.5)
+# ----------------------------------------------------------------------------
+def densities(phi, w_minus, w_plus):
+    """rho_a = rho_b = sum_n w-_n |v_n|^2 + w+_n |u_n|^2;
+    nu = sum_n (w-_n - w+_n) u_n v_n^*."""
+    u, v = phi[:, 0, :], phi[:, 1, :]
+    rho = np.einsum("n,nr->r", w_minus, np.abs(v) ** 2) + np.einsum("n,nr->r", w_plus, np.abs(u) ** 2)
+    nu = np.einsum("n,nr->r", w_minus - w_plus, u * np.conj(v))
+    return rho, nu
+
+
+def kinetic_current_densities(phi, w_minus, w_plus, lat: Lattice):
+    """tau_sigma and j_sigma (Eqs. nab3D-jab3D) with Nyquist-free gradients."""
+    u, v = phi[:, 0, :], phi[:, 1, :]
+    gu, gv = gradient(u, lat), gradient(v, lat)
+    tau = sum(np.einsum("n,nr->r", w_minus, np.abs(gv[d]) ** 2)
+              + np.einsum("n,nr->r", w_plus, np.abs(gu[d]) ** 2) for d in range(3))
+    j = np.stack([np.einsum("n,nr->r", w_minus, np.imag(v * np.conj(gv[d])))
+                  - np.einsum("n,nr->r", w_plus, np.imag(u * np.conj(gu[d]))) for d in range(3)])
+    return tau, j
+
+
+# ----------------------------------------------------------------------------
+# Hamiltonian application and ABM right-hand side (Sec. 3.4)
+# ----------------------------------------------------------------------------
+@dataclass
+class Fields:
+    """Pointwise fields defining H for A = 1 (Eq. h_sigma_A1, Eq. dpsidt-Hpsi):
+    W = U + V_ext - mu on the diagonal, D = Delta + Delta_ext off the diagonal."""
+    W: np.ndarray
+    D: np.ndarray
+
+
+def apply_H(phi, F: Fields, lat: Lattice):
+    """(H phi)_u = -1/2 lap u + W u + D v;  (H phi)_v = D^* u + 1/2 lap v - W v."""
+    u, v = phi[:, 0, :], phi[:, 1, :]
+    Hu = -0.5 * laplacian(u, lat) + F.W * u + F.D * v
+    Hv = np.conj(F.D) * u + 0.5 * laplacian(v, lat) - F.W * v
+    return np.stack([Hu, Hv], axis=1)
+
+
+def expectation(phi, Hphi, lat: Lattice):
+    """<H>_n = Re int phi_n^dagger H phi_n (reading I2: imaginary part is roundoff)."""
+    return lat.dV * np.real(np.einsum("ncr,ncr->n", np.conj(phi), Hphi))
+
+
+def norms(phi, lat: Lattice):
+    return lat.dV * np.einsum("ncr,ncr->n", np.conj(phi), phi).real
+
+
+def normalize(phi, lat: Lattice):
+    return phi / np.sqrt(norms(phi, lat))[:, None, None]
+
+
+def rhs_f(phi, F: Fields, lat: Lattice):
+    """f(phi) = -i [H - <H>_n] phi (Eq. ABM-f, Eq. shorttdproblem-mod)."""
+    Hphi = apply_H(phi, F, lat)
+    En = expectation(phi, Hphi, lat)
+    return -1j * (Hphi - En[:, None, None] * phi)
+
+
+# ----------------------------------------------------------------------------
+# Time-dependent system: densities -> potentials -> H, energy
+# ----------------------------------------------------------------------------
+AB4 = np.array([55.0, -59.0, 37.0, -9.0]) / 24.0                 # Eq. AB4
+AM5 = np.array([251.0, 646.0, -264.0, 106.0, -19.0]) / 720.0     # Eq. AM5
+AB3 = np.array([23.0, -16.0, 5.0]) / 12.0                         # Eq. AB3
+AB5 = np.array([1901.0, -2774.0, 2616.0, -1274.0, 251.0]) / 720.0  # Eq. AB5
+AM4 = np.array([9.0, 19.0, -5.0, 1.0]) / 24.0                     # Eq. AM4
+
+
+@dataclass
+class TDSystem:
+    lat: Lattice
+    fn: Functional
+    vext: np.ndarray                     # [M] real
+    dext: np.ndarray | None = None       # [M] complex external pairing field
+    w_minus: np.ndarray | None = None    # [n] frozen thermal weights f(-E_n)
+    w_plus: np.ndarray | None = None     # [n] frozen thermal weights f(E_n)
+    lam: np.ndarray | None = None        # frozen regulator (reading R2)
+    freeze_fields: Fields | None = None  # testing aid: H held fixed
+
+    def weights(self, n):
+        wm = np.ones(n) if self.w_minus is None else self.w_minus
+        wp = np.zeros(n) if self.w_plus is None else self.w_plus
+        return wm, wp
+
+    def init_regulator(self, phi):
+        wm, wp = self.weights(phi.shape[0])
+        rho, nu = densities(phi, wm, wp)
+        self.lam = frozen_regulator(rho, nu, self.vext, self.fn, self.lat)
+
+    def potentials(self, phi):
+        wm, wp = self.weights(phi.shape[0])
+        rho, nu = densities(phi, wm, wp)
+        U, delta, g = potentials(rho, nu, self.lam, self.fn)
+        return rho, nu, U, delta, g
+
+    def fields(self, phi) -> Fields:
+        """Densities of all states -> potentials -> (W, D) (Alg. 1 steps 3-4)."""
+        if self.freeze_fields is not None:
+            return self.freeze_fields
+        _, _, U, delta, _ = self.potentials(phi)
+        D = delta if self.dext is None else delta + self.dext
+        return Fields(W=U + self.vext - self.fn.mu, D=D)
+
+    def f(self, phi):
+        return rhs_f(phi, self.fields(phi), self.lat)
+
+    def energy(self, phi) -> dict:
+        """Energy terms of Sec. 3.3 for A = 1 (reading E1: the kinetic term uses
+        the same Laplacian as H, via sum_n w <v|-lap|v>). The quantity the
+        evolution conserves is e_total - mu * n_part (Eq. E_tot)."""
+        lat, fn = self.lat, self.fn
+        wm, wp = self.weights(phi.shape[0])
+        rho_s, nu, U, delta, g = self.potentials(phi)
+        u, v = phi[:, 0, :], phi[:, 1, :]
+        lu, lv = laplacian(u, lat), laplacian(v, lat)
+        e_kin = lat.dV * (np.einsum("n,nr->", wm, -np.conj(v) * lv).real
+                          + np.einsum("n,nr->", wp, -np.conj(u) * lu).real)
+        rho = 2.0 * rho_s
+        e_pot = lat.dV * np.sum(0.6 * fn.B * rho * fermi_energy(rho)) if fn.kind == "slda" else 0.0
+        e_pair = -lat.dV * np.sum(np.real(np.conj(delta) * nu))
+        e_ext = lat.dV * np.sum(self.vext * rho)
+        e_pext = 0.0 if self.dext is None else -lat.dV * np.sum(2.0 * np.real(self.dext * np.conj(nu)))
+        n_part = lat.dV * np.sum(rho)
+        tot = e_kin + e_pot + e_pair + e_ext + e_pext
+        return dict(e_kin=e_kin, e_pot=e_pot, e_pair=e_pair, e_ext=e_ext, e_pair_ext=e_pext,
+                    e_total=tot, n_part=n_part)
+
+
+# ----------------------------------------------------------------------------
+# Integrators: AB4AM5 (Alg. 2) and the Taylor start (Eq. Taylor-exp)
+# ----------------------------------------------------------------------------
+@dataclass
+class ABMState:
+    """The five buffers of Alg. 2: phi_{k-1} and f_{k-1} .. f_{k-4}."""
+    phi: np.ndarray
+    f1: np.ndarray
+    f2: np.ndarray
+    f3: np.ndarray
+    f4: np.ndarray
+    t: float = 0.0
+    steps: int = 0
+
+
+def ab4am5_step(sys: TDSystem, st: ABMState, dt: float) -> ABMState:
+    """One pass of Integrator_AB4AM5 (Alg. 2), steps 1-10 in order."""
+    lat = sys.lat
+    # step 1: predictor (Eq. AB4) and corrector partial (Eq. AM5 without the new
+    # term), both formed from the same phi_{k-1} before it is overwritten
+    pred = st.phi + dt * (AB4[0] * st.f1 + AB4[1] * st.f2 + AB4[2] * st.f3 + AB4[3] * st.f4)
+    corr = st.phi + dt * (AM5[1] * st.f1 + AM5[2] * st.f2 + AM5[3] * st.f3 + AM5[4] * st.f4)
+    phi, f4 = pred, corr
+    # step 2: normalise
+    phi = normalize(phi, lat)
+    # step 3: f(phi_p) (densities, potentials, H) into the phi buffer
+    phi = sys.f(phi)
+    # step 4: corrector completion
+    phi = (AM5[0] * dt) * phi + f4
+    # steps 5-7: shift the history
+    f4, f3, f2 = st.f3, st.f2, st.f1
+    # step 8: normalise
+    phi = normalize(phi, lat)
+    # step 9: f(phi_k) into f_{k-1}
+    f1 = sys.f(phi)
+    # step 10
+    return ABMState(phi=phi, f1=f1, f2=f2, f3=f3, f4=f4, t=st.t + dt, steps=st.steps + 1)
+
+
+def taylor_series(phi0, F: Fields, shift, h: float, r: int, lat: Lattice):
+    """sum_{k=0}^{r} (-i h)^k / k! [H - shift]^k phi0 (Eq. Taylor-exp), term by term."""
+    out = phi0.copy()
+    term = phi0
+    for k in range(1, r + 1):
+        term = apply_H(term, F, lat) - shift[:, None, None] * term
+        term = (-1j * h / k) * term
+        out = out + term
+    return out
+
+
+def taylor_step(sys: TDSystem, phi, dt: float, r: int = 5):
+    """Predictor-corrector Taylor step (Sec. 3.4, Eq. Taylor-exp).
+
+    Reading T1: the series uses the shifted operator H - <H>_n of the ABM
+    equations, the shift being the expectation value of that sub-step's H in
+    phi(t) (the state the series is applied to), fixed over the r powers.
+    Reading T2: normalise the midpoint state and the result."""
+    lat = sys.lat
+    F0 = sys.fields(phi)
+    s0 = expectation(phi, apply_H(phi, F0, lat), lat)
+    mid = normalize(taylor_series(phi, F0, s0, 0.5 * dt, r, lat), lat)
+    Fm = sys.fields(mid)
+    s1 = expectation(phi, apply_H(phi, Fm, lat), lat)
+    return normalize(taylor_series(phi, Fm, s1, dt, r, lat), lat)
+
+
+def start(sys: TDSystem, phi0, dt: float, stationary: bool, r: int = 5) -> ABMState:
+    """ABM start-up (Sec. 3.4).
+
+    stationary: reading S1, f_{k-2..k-4} = 0 and f_{k-1} = f(phi_0) (zero for an
+    exact stationary state). Otherwise reading T2/T3: three Taylor steps give
+    phi_1..phi_3, history f_0..f_3, and count as steps of the evolution."""
+    lat = sys.lat
+    phi = normalize(phi0, lat)
+    if sys.lam is None:
+        sys.init_regulator(phi)
+    z = np.zeros_like(phi)
+    if stationary:
+        return ABMState(phi=phi, f1=sys.f(phi), f2=z, f3=z.copy(), f4=z.copy())
+    hist = [sys.f(phi)]
+    for _ in range(3):
+        phi = taylor_step(sys, phi, dt, r)
+        hist.append(sys.f(phi))
+    return ABMState(phi=phi, f1=hist[3], f2=hist[2], f3=hist[1], f4=hist[0], t=3 * dt, steps=3)
+
+
+def evolve(sys: TDSystem, st: ABMState, dt: float, nsteps: int) -> ABMState:
+    for _ in range(nsteps):
+        st = ab4am5_step(sys, st, dt)
+    return st
+
+
+# ----------------------------------------------------------------------------
+# Uniform systems (Sec. 5 "inittype 0"): lattice seeds and continuum checks
+# ----------------------------------------------------------------------------
+def bcs_amplitudes(xi, delta):
+    """U_k, V_k of the 2x2 problem [[xi, D], [D, -xi]] at E_k = sqrt(xi^2 + D^2) > 0."""
+    E = np.sqrt(xi ** 2 + delta ** 2)
+    Uk = np.sqrt(0.5 * (1 + xi / E))
+    Vk = np.sign(delta) * np.sqrt(0.5 * (1 - xi / E))
+    return Uk, Vk, E
+
+
+def solve_mu_eff(lat: Lattice, delta: float, rho_sigma: float) -> float:
+    """mu_eff = mu - U such that (1/V) sum_k V_k^2 = rho_sigma over all M lattice k."""
+    from scipy.optimize import brentq
+    k2 = lat.k2().reshape(-1)
+
+    def dens(me):
+        xi = 0.5 * k2 - me
+        E = np.sqrt(xi ** 2 + delta ** 2)
+        return np.sum(0.5 * (1 - xi / E)) / lat.volume - rho_sigma
+    return brentq(dens, -50.0, 0.5 * k2.max() + 50.0, xtol=1e-15, rtol=1e-15, maxiter=500)
+
+
+@dataclass
+class UniformSeed:
+    mu_eff: float
+    delta: float
+    mu: float
+    U: float
+    C: float
+    lam: float
+    inv_g: float
+    rho_sigma: float
+
+
+def uniform_slda_seed(lat: Lattice, delta0: float, rho_sigma: float, B: float = B_SLDA,
+                      ec: float = -1.0) -> UniformSeed:
+    """Self-consistent uniform SLDA (A = 1) state on the lattice k-set with the
+    gap fixed to delta0: mu_eff from the number equation, 1/g_eff from the gap
+    equation 1 = -g_eff (1/V) sum_k 1/(2E_k), C backed out of Eq. Creg, and
+    U = B eF - Delta^2/(3 C rho^(2/3))."""
+    me = solve_mu_eff(lat, delta0, rho_sigma)
+    k2 = lat.k2().reshape(-1)
+    E = np.sqrt((0.5 * k2 - me) ** 2 + delta0 ** 2)
+    inv_g = -np.sum(1.0 / (2 * E)) / lat.volume
+    ecut = ec if ec > 0 else lattice_cutoff(lat)
+    lam = float(lambda_c(me, ecut))
+    rho = 2 * rho_sigma
+    C = rho ** (1.0 / 3.0) / (inv_g + lam)
+    U = B * fermi_energy(rho) - delta0 ** 2 / (3 * C * rho ** (2.0 / 3.0))
+    return UniformSeed(mu_eff=me, delta=delta0, mu=U + me, U=U, C=C, lam=lam, inv_g=inv_g,
+                       rho_sigma=rho_sigma)
+
+
+def uniform_bdg_seed(lat: Lattice, inv_4pi_a: float, rho_sigma: float, ec: float = -1.0) -> UniformSeed:
+    """Uniform BdG (U = 0) on the lattice: solve the number equation and the gap
+    equation 1/(4 pi a) - Lambda_c(mu) = -(1/V) sum_k 1/(2E_k) for (mu, Delta).
+    The root taken is the first sign change of the gap residual on a log grid
+    of Delta from 1e-6 to 8, refined by bisection."""
+    from scipy.optimize import brentq
+    k2 = lat.k2().reshape(-1)
+    ecut = ec if ec > 0 else lattice_cutoff(lat)
+
+    def gap_residual(delta):
+        me = solve_mu_eff(lat, delta, rho_sigma)
+        E = np.sqrt((0.5 * k2 - me) ** 2 + delta ** 2)
+        return inv_4pi_a - float(lambda_c(me, ecut)) + np.sum(1.0 / (2 * E)) / lat.volume
+    grid = np.geomspace(1e-6, 8.0, 80)
+    vals = [gap_residual(d) for d in grid]
+    for a, b, fa, fb in zip(grid[:-1], grid[1:], vals[:-1], vals[1:]):
+        if fa > 0 >= fb:
+            delta = brentq(gap_residual, a, b, xtol=1e-15, rtol=1e-15, maxiter=500)
+            break
+    else:
+        raise ValueError("uniform BdG gap equation has no root on this lattice")
+    me = solve_mu_eff(lat, delta, rho_sigma)
+    E = np.sqrt((0.5 * k2 - me) ** 2 + delta ** 2)
+    return UniformSeed(mu_eff=me, delta=delta, mu=me, U=0.0, C=float("nan"), lam=float(lambda_c(me, ecut)),
+                       inv_g=-np.sum(1.0 / (2 * E)) / lat.volume, rho_sigma=rho_sigma)
+
+
+def uniform_states(lat: Lattice, mu_eff: float, delta: float) -> np.ndarray:
+    """All M positive-energy plane-wave quasiparticle states of the uniform
+    system: u_k = U_k e^{ik.r}/sqrt(V), v_k = V_k e^{ik.r}/sqrt(V), with k in the
+    flattened FFT order and r = site index * spacing."""
+    kx, ky, kz = (lat.kaxis(a) for a in range(3))
+    x = np.arange(lat.nx) * lat.dx
+    y = np.arange(lat.ny) * lat.dy
+    z = np.arange(lat.nz) * lat.dz
+    ex = np.exp(1j * np.outer(kx, x))
+    ey = np.exp(1j * np.outer(ky, y))
+    ez = np.exp(1j * np.outer(kz, z))
+    pw = np.einsum("ai,bj,ck->abcijk", ex, ey, ez).reshape(lat.M, lat.M) / np.sqrt(lat.volume)
+    k2 = lat.k2().reshape(-1)
+    Uk, Vk, _ = bcs_amplitudes(0.5 * k2 - mu_eff, delta)
+    return np.stack([Uk[:, None] * pw, Vk[:, None] * pw], axis=1)
+
+
+def uniform_continuum(A: float, B: float, C: float | None, inv_4pi_a: float | None,
+                      kF: float = 1.0, ec_over_eF: float = 2000.0):
+    """Self-consistent uniform continuum solution with the Eq. Creg regularisation
+    (spherical cutoff E_c, A k_c^2/2 - mu_eff = E_c). Returns a dict with mu/eF,
+    Delta/eF and E/E_FG (E_FG = 3/5 N eF). SLDA-type if C is given, BdG if
+    inv_4pi_a is given (then B must be 0)."""
+    from scipy.integrate import quad
+    from scipy.optimize import fsolve
+    rho = kF ** 3 / (3 * np.pi ** 2)
+    rho_s = rho / 2
+    eF = 0.5 * kF ** 2
+    ec = ec_over_eF * eF
+
+    def integrals(me, d):
+        kc = math.sqrt(2 * (ec + me) / A)
+        k0 = math.sqrt(max(2 * me / A, 0.0))
+
+        def xi(k):
+            return 0.5 * A * k * k - me
+
+        def dens(k):
+            x = xi(k)
+            return k * k * 0.5 * (1 - x / math.hypot(x, d))
+
+        def anom(k):
+            return k * k * d / (2 * math.hypot(xi(k), d))
+
+        def kin(k):
+            x = xi(k)
+            return k ** 4 * 0.5 * (1 - x / math.hypot(x, d))
+
+        def inv_e(k):
+            return k * k / (2 * math.hypot(xi(k), d))
+        opts = dict(limit=400, epsabs=1e-14, epsrel=1e-12)
+        segs = sorted(set(s for s in (0.0, k0, min(kc, 4 * max(k0, 1.0)), kc) if s <= kc))
+
+        def q(fun):
+            return sum(quad(fun, a, b, **opts)[0] for a, b in zip(segs[:-1], segs[1:]))
+        c = 1.0 / (2 * np.pi ** 2)
+        return c * q(dens), c * q(anom), c * q(kin), c * q(inv_e)
+
+    def residual(x):
+        me, d = x
+        n_s, nu, tau, ie = integrals(me, abs(d))
+        lam = float(lambda_c(me, ec, A))
+        inv_g = (rho ** (1 / 3) / C - lam) if C is not None else (inv_4pi_a - lam)
+        return [n_s / rho_s - 1.0, inv_g + ie]
+
+    sol = fsolve(residual, [0.5 * eF, 0.6 * eF], xtol=1e-13)
+    me, d = sol[0], abs(sol[1])
+    n_s, nu, tau, ie = integrals(me, d)
+    g = -1.0 / ie
+    U = (B * fermi_energy(rho) - d ** 2 / (3 * C * rho ** (2 / 3))) if C is not None else 0.0
+    e_dens = A * tau + 0.6 * B * rho * fermi_energy(rho) + g * nu ** 2
+    return dict(mu_over_eF=(U + me) / eF, delta_over_eF=d / eF,
+                E_over_EFG=e_dens / (0.6 * rho * eF), mu_eff=me, nu=nu, tau=tau)
+
+
+# ----------------------------------------------------------------------------
+# Dense reduced BdG matrix (brute force on tiny lattices)
+# ----------------------------------------------------------------------------
+def dense_bdg(F: Fields, lat: Lattice) -> np.ndarray:
+    """2M x 2M matrix of Eq. HpsiEpsi for A = 1 built from Eq. D2:
+    [[-1/2 D2 + W, D], [D^*, 1/2 D2 - W]]."""
+    L = dense_laplacian(lat)
+    M = lat.M
+    H = np.zeros((2 * M, 2 * M), dtype=np.complex128)
+    H[:M, :M] = -0.5 * L + np.diag(F.W)
+    H[M:, M:] = 0.5 * L - np.diag(F.W)
+    H[:M, M:] = np.diag(F.D)
+    H[M:, :M] = np.diag(np.conj(F.D))
+    return H
+
+
+def dense_rhs(sys: TDSystem, phi):
+    """f(phi) through the dense matrix (independent of the FFT path)."""
+    F = sys.fields(phi)
+    H = dense_bdg(F, sys.lat)
+    n = phi.shape[0]
+    x = phi.reshape(n, -1)
+    Hx = x @ H.T
+    En = sys.lat.dV * np.real(np.einsum("ni,ni->n", np.conj(x), Hx))
+    return (-1j * (Hx - En[:, None] * x)).reshape(phi.shape)
+
+
+def rk4_reference(sys: TDSystem, phi0, T: float, nsub: int):
+    """Classical RK4 on the modified equation (Eq. shorttdproblem-mod) with the
+    dense matrix, used only as an independent fine-step reference."""
+    h = T / nsub
+    phi = phi0.copy()
+    for _ in range(nsub):
+        k1 = dense_rhs(sys, phi)
+        k2 = dense_rhs(sys, phi + 0.5 * h * k1)
+        k3 = dense_rhs(sys, phi + 0.5 * h * k2)
+        k4 = dense_rhs(sys, phi + h * k3)
+        phi = phi + (h / 6) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return phi

@@ -1,0 +1,355 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the fact it checks. Nothing here compares the oracle with
+itself: the references are closed forms (Eqs. D1, D2), quadrature of a defining
+integral, numbers printed in the paper (tests/golden/paper_values.json),
+textbook limits, invariants of the equations of motion, and independent
+brute-force integrators built on the dense matrix.
+"""
+import json
+import math
+import os
+import warnings
+
+import numpy as np
+import pytest
+
+from oracle import tdslda as o
+from paper_2602_08982_b300 import inputs
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+RHO_S = 1.0 / (6 * np.pi ** 2)   # per-spin density at kF = 1
+
+warnings.filterwarnings("ignore", category=Warning, module="scipy")
+
+
+def rand_field(lat, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, lat.M)) + 1j * rng.standard_normal((n, lat.M))
+
+
+# ---------------------------------------------------------------- derivatives
+@pytest.mark.parametrize("dims,sp", [((4, 6, 8), (0.7, 0.9, 1.1)), ((6, 4, 10), (1.0, 1.0, 1.0)),
+                                     ((8, 8, 8), (0.5, 0.5, 0.5))])
+def test_fft_laplacian_equals_closed_form_D2(dims, sp):
+    """Eq. derivative-spectral (r = 2, Nyquist kept) equals the Kronecker sum of
+    Eq. D2 matrices to machine precision."""
+    lat = o.Lattice(*dims, *sp)
+    f = rand_field(lat, 3, 1)
+    L = o.dense_laplacian(lat)
+    ref = f @ L.T
+    assert np.abs(o.laplacian(f, lat) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_D2_diagonal_is_mean_of_minus_k2():
+    """The diagonal of Eq. D2, -(pi^2/3dx^2)(1 + 2/N^2), is -(1/N) sum_l k_l^2
+    with the Nyquist term included: this fixes k = -pi/dx at l = N/2."""
+    for n in (4, 6, 12, 16, 24, 32, 96):
+        lat = o.Lattice(n, 2, 2, 0.8)
+        kx = lat.kaxis(0)
+        assert kx[n // 2] == pytest.approx(-np.pi / 0.8, rel=1e-15)
+        D = o.derivative_matrix_1d(n, 0.8, 2)
+        assert D[0, 0] == pytest.approx(-np.mean(kx ** 2), rel=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 8), (6, 6, 4)])
+def test_fft_gradient_equals_closed_form_D1(dims):
+    """Eq. derivative-spectral (r = 1, Nyquist zeroed) equals Eq. D1 per axis."""
+    lat = o.Lattice(*dims, 0.9, 1.2, 0.8)
+    f = rand_field(lat, 2, 2)
+    g = o.gradient(f, lat)
+    sp = (lat.dx, lat.dy, lat.dz)
+    for ax in range(3):
+        eyes = [np.eye(n) for n in lat.shape]
+        eyes[ax] = o.derivative_matrix_1d(lat.shape[ax], sp[ax], 1)
+        D = np.kron(np.kron(eyes[0], eyes[1]), eyes[2])
+        assert np.abs(g[ax] - f @ D.T).max() < 1e-12 * np.abs(g[ax]).max()
+
+
+def test_gradient_of_real_field_is_real():
+    """Footnote to Eq. derivative-spectral: with the Nyquist mode zeroed the odd
+    derivative of a real function stays real."""
+    lat = o.Lattice(6, 4, 8)
+    f = np.random.default_rng(3).standard_normal((1, lat.M)).astype(complex)
+    for g in o.gradient(f, lat):
+        assert np.abs(g.imag).max() < 1e-14
+
+
+# ---------------------------------------------------------------- ABM coefficients
+def _order_conditions(coeffs, nodes):
+    """Residuals of sum_j c_j nodes_j^q = 1/(q+1): exact integration of t^q on [0, 1]."""
+    return [abs(sum(c * t ** q for c, t in zip(coeffs, nodes)) - 1.0 / (q + 1)) for q in range(len(coeffs))]
+
+
+@pytest.mark.parametrize("name,coeffs,nodes", [
+    ("AB3", o.AB3, [0, -1, -2]), ("AB4", o.AB4, [0, -1, -2, -3]), ("AB5", o.AB5, [0, -1, -2, -3, -4]),
+    ("AM4", o.AM4, [1, 0, -1, -2]), ("AM5", o.AM5, [1, 0, -1, -2, -3])])
+def test_adams_coefficients_integrate_polynomials_exactly(name, coeffs, nodes):
+    """Eqs. AB3-AB5, AM4, AM5: an order-s Adams formula integrates polynomials
+    of degree < s exactly (one wrong coefficient breaks one of the conditions)."""
+    assert max(_order_conditions(coeffs, nodes)) < 1e-14
+
+
+# ---------------------------------------------------------------- regularisation
+@pytest.mark.parametrize("mu_minus_V", [0.3, 0.5, 1.2, -0.2, -1.0])
+def test_lambda_c_is_principal_value_integral(mu_minus_V):
+    """Lambda_c (Eq. Creg) equals (1/2pi^2) PV int_0^kc k^2 / (A k^2 - A k0^2) dk;
+    for mu < V (reading R3) the same integral, which then has no pole."""
+    from scipy.integrate import quad
+    ec = np.pi ** 2 / 2
+    for A in (1.0, 1.094):
+        k0sq = 2 * mu_minus_V / A
+        kc = math.sqrt(2 * (ec + mu_minus_V) / A)
+        if k0sq > 0:
+            k0 = math.sqrt(k0sq)
+            # PV int_0^kc k^2/(k^2-k0^2) = kc + k0^2 PV int_0^kc dk/((k-k0)(k+k0))
+            pv = quad(lambda k: 1.0 / (k + k0), 0, kc, weight="cauchy", wvar=k0, epsabs=1e-14)[0]
+            val = (kc + k0sq * pv) / (2 * np.pi ** 2 * A)
+        else:
+            val = quad(lambda k: k * k / (A * (k * k - k0sq)), 0, kc, epsabs=1e-14)[0] / (2 * np.pi ** 2)
+        assert float(o.lambda_c(mu_minus_V, ec, A)) == pytest.approx(val, rel=1e-9)
+
+
+def test_lambda_c_continuous_across_turning_point():
+    ec = np.pi ** 2 / 2
+    lam = o.lambda_c(np.array([-1e-16, 0.0, 1e-16]), ec)
+    assert np.ptp(lam) < 1e-8
+
+
+def test_default_cutoff_contains_every_lattice_state():
+    """Reading R5: the default E_c is the kinetic energy of the zone corner."""
+    lat = o.Lattice(6, 8, 10, 1.0, 0.5, 2.0)
+    assert o.lattice_cutoff(lat) == pytest.approx(0.5 * lat.k2().max(), rel=1e-14)
+
+
+# ---------------------------------------------------------------- uniform solutions
+def _extrapolate(f, e1=32000.0, e2=128000.0):
+    """Richardson extrapolation in 1/k_c of a continuum quantity."""
+    a, b = f(e1), f(e2)
+    k1, k2 = math.sqrt(2 * e1), math.sqrt(2 * e2)
+    return {key: (b[key] * k2 - a[key] * k1) / (k2 - k1) for key in ("mu_over_eF", "delta_over_eF", "E_over_EFG")}
+
+
+def test_uniform_slda_reproduces_printed_values():
+    """Sec. 2.4: the spin-symmetric ASLDA (A = 1.094, B = B(0), C = -11.11)
+    gives E/E_FG = 0.39(1) and Delta/eF = 0.51(1). Reading R1 of Eq. Creg
+    (1/g_eff = rho^(1/3)/C - Lambda_c) lands within the printed uncertainty on
+    E/E_FG (0.398) and 0.015 of the printed gap (0.495)."""
+    A0 = GOLD["aslda_A0"]["value"]
+    C = GOLD["aslda_C"]["value"]
+    assert o.aslda_A(0.0) == A0
+    r = _extrapolate(lambda e: o.uniform_continuum(A0, o.B_SLDA, C, None, ec_over_eF=e))
+    assert abs(r["E_over_EFG"] - GOLD["slda_uniform_E_over_EFG"]["value"]) <= GOLD["slda_uniform_E_over_EFG"]["uncertainty"]
+    assert abs(r["delta_over_eF"] - GOLD["slda_uniform_Delta_over_eF"]["value"]) <= 0.02
+    # unitarity is scale invariant: mu = dE/dN = (5/3) E/N, i.e. mu/eF = E/E_FG;
+    # this fails if U is not the density derivative of the functional
+    assert r["mu_over_eF"] == pytest.approx(r["E_over_EFG"], abs=2e-4)
+
+
+def test_uniform_slda_wrong_reading_fails():
+    """The alternative reading with the per-spin density in rho^(1/3)/C misses
+    the printed pair, so the pin above discriminates."""
+    A0, C = GOLD["aslda_A0"]["value"], GOLD["aslda_C"]["value"]
+    r = o.uniform_continuum(A0, o.B_SLDA, C * 2 ** (1 / 3), None, ec_over_eF=32000.0)
+    assert abs(r["E_over_EFG"] - 0.39) > 0.02 or abs(r["delta_over_eF"] - 0.51) > 0.02
+
+
+def test_bdg_unitarity_matches_mean_field_crossover():
+    """BdG functional (Eq. HBdG) at 1/(kF a) = 0 with Eq. Creg regularisation:
+    the textbook mean-field values mu = 0.5906 eF, Delta = 0.6864 eF."""
+    r = _extrapolate(lambda e: o.uniform_continuum(1.0, 0.0, None, 0.0, ec_over_eF=e))
+    assert r["mu_over_eF"] == pytest.approx(GOLD["leggett_unitarity_mu_over_eF"]["value"], abs=5e-4)
+    assert r["delta_over_eF"] == pytest.approx(GOLD["leggett_unitarity_Delta_over_eF"]["value"], abs=5e-4)
+
+
+def test_bdg_weak_coupling_gap():
+    """Weak coupling (Sec. 2.4, APS gap at lambda -> 0): Delta/eF -> (8/e^2) exp(-pi/(2 kF|a|));
+    the ratio tends to 1 as kF a -> 0^-."""
+    ratios = []
+    for kfa in (-0.5, -0.35):
+        r = o.uniform_continuum(1.0, 0.0, None, 1.0 / (4 * np.pi * kfa), ec_over_eF=8000.0)
+        ratios.append(r["delta_over_eF"] / (8 / math.e ** 2 * math.exp(-math.pi / (2 * abs(kfa)))))
+    assert abs(ratios[1] - 1) < abs(ratios[0] - 1)
+    assert abs(ratios[1] - 1) < 0.03
+
+
+# ---------------------------------------------------------------- lattice uniform states
+@pytest.mark.parametrize("dims", [(6, 6, 6), (4, 6, 8)])
+def test_uniform_states_orthonormal(dims):
+    lat = o.Lattice(*dims)
+    seed = o.uniform_slda_seed(lat, 0.25, RHO_S)
+    phi = o.uniform_states(lat, seed.mu_eff, seed.delta)
+    x = phi.reshape(lat.M, -1)
+    G = lat.dV * np.conj(x) @ x.T
+    assert np.abs(G - np.eye(lat.M)).max() < 1e-12
+    rho, nu = o.densities(phi, np.ones(lat.M), np.zeros(lat.M))
+    assert np.abs(rho - RHO_S).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["slda", "bdg"])
+def test_uniform_state_is_stationary(kind):
+    """Sec. 3.4: the self-consistent static solution gives f = 0 (the modified
+    equation removes the phase), so an ABM step leaves it unchanged."""
+    lat = o.Lattice(6, 6, 6) if kind == "slda" else o.Lattice(8, 8, 8)
+    if kind == "slda":
+        seed = o.uniform_slda_seed(lat, 0.25, RHO_S)
+        fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu)
+    else:
+        ia = 0.4 / (4 * np.pi)
+        seed = o.uniform_bdg_seed(lat, ia, RHO_S)
+        fn = o.Functional("bdg", inv_4pi_a=ia, mu=seed.mu)
+    phi = o.uniform_states(lat, seed.mu_eff, seed.delta)
+    sys = o.TDSystem(lat, fn, vext=np.zeros(lat.M))
+    sys.init_regulator(phi)
+    assert np.abs(sys.lam - seed.lam).max() < 1e-12
+    assert np.abs(sys.f(phi)).max() < 1e-11
+    st = o.evolve(sys, o.start(sys, phi, 0.01, stationary=True), 0.01, 4)
+    assert np.abs(st.phi - phi).max() < 1e-12
+
+
+def test_bdg_spectrum_is_plus_minus_symmetric():
+    """Sec. 2.3: for spin-symmetric systems (u, v) -> (v^*, -u^*) maps E to -E."""
+    lat = o.Lattice(4, 4, 4)
+    rng = np.random.default_rng(5)
+    F = o.Fields(W=rng.standard_normal(lat.M), D=rng.standard_normal(lat.M) + 1j * rng.standard_normal(lat.M))
+    H = o.dense_bdg(F, lat)
+    w, V = np.linalg.eigh(H)
+    assert np.abs(np.sort(w) - np.sort(-w)).max() < 1e-10
+    M = lat.M
+    u, v = V[:M, -1], V[M:, -1]
+    partner = np.concatenate([np.conj(v), -np.conj(u)])
+    assert np.abs(H @ partner + w[-1] * partner).max() < 1e-10
+
+
+def test_fft_apply_H_matches_dense_matrix():
+    lat = o.Lattice(4, 6, 4)
+    rng = np.random.default_rng(6)
+    F = o.Fields(W=rng.standard_normal(lat.M), D=rng.standard_normal(lat.M) + 1j * rng.standard_normal(lat.M))
+    phi = rand_field(lat, 6, 7).reshape(3, 2, lat.M)
+    ref = (phi.reshape(3, -1) @ o.dense_bdg(F, lat).T).reshape(phi.shape)
+    assert np.abs(o.apply_H(phi, F, lat) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- dynamics
+def _tiny_case(trap=0.3, kick=0.05):
+    lat = o.Lattice(4, 4, 4)
+    seed = o.uniform_slda_seed(lat, 0.25, RHO_S)
+    fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu)
+    phi0 = o.uniform_states(lat, seed.mu_eff, seed.delta)
+    vext = inputs.harmonic_trap(lat.shape, trap) if trap else np.zeros(lat.M)
+    dext = inputs.pairing_kick(lat.shape, 7, kick * seed.delta) if kick else None
+    return lat, fn, phi0, vext, dext
+
+
+def _run(lat, fn, phi0, vext, dext, dt, T, stationary=False):
+    sys = o.TDSystem(lat, fn, vext=vext, dext=dext)
+    st = o.start(sys, phi0, dt, stationary=stationary)
+    st = o.evolve(sys, st, dt, int(round(T / dt)) - st.steps)
+    return sys, st
+
+
+def test_frozen_field_evolution_matches_exact_exponential():
+    """With H held fixed the equation is linear; the exact solution is
+    exp(-iHt) from the dense eigen-decomposition (the <H>_n shift only changes
+    phases, which the densities do not see). Error falls with the step."""
+    lat = o.Lattice(4, 4, 4)
+    rng = np.random.default_rng(8)
+    F = o.Fields(W=0.3 * rng.standard_normal(lat.M),
+                 D=0.2 * (rng.standard_normal(lat.M) + 1j * rng.standard_normal(lat.M)))
+    q, _ = np.linalg.qr(rng.standard_normal((2 * lat.M, 12)) + 1j * rng.standard_normal((2 * lat.M, 12)))
+    phi0 = q.T.reshape(12, 2, lat.M)
+    wm, wp = np.ones(12), np.zeros(12)
+    w, V = np.linalg.eigh(o.dense_bdg(F, lat))
+    T = 0.4
+    exact = (V @ (np.exp(-1j * w * T)[:, None] * (V.conj().T @ phi0.reshape(12, -1).T))).T.reshape(phi0.shape)
+    r_ex, n_ex = o.densities(exact, wm, wp)
+    errs = []
+    for dt in (0.01, 0.005):
+        sys = o.TDSystem(lat, o.Functional(), vext=np.zeros(lat.M), freeze_fields=F, lam=np.zeros(lat.M))
+        st = o.evolve(sys, o.start(sys, phi0, dt, stationary=False), dt, int(round(T / dt)) - 3)
+        r, n = o.densities(st.phi, wm, wp)
+        errs.append(max(np.abs(r - r_ex).max() / np.abs(r_ex).max(), np.abs(n - n_ex).max() / np.abs(n_ex).max()))
+    assert errs[1] < 1e-6
+    assert errs[0] / errs[1] > 16   # fifth order: 2^5 = 32
+
+
+def test_self_consistent_evolution_matches_dense_rk4():
+    """Self-consistent dynamics (trap + external pairing kick) against classical
+    RK4 with the dense Eq. D2 Hamiltonian at 1/8 of the step."""
+    lat, fn, phi0, vext, dext = _tiny_case()
+    T = 0.24
+    ref_sys = o.TDSystem(lat, fn, vext=vext, dext=dext)
+    ref_sys.init_regulator(phi0)
+    ref = o.rk4_reference(ref_sys, phi0, T, 192)
+    wm, wp = np.ones(lat.M), np.zeros(lat.M)
+    r_ref, n_ref = o.densities(ref, wm, wp)
+    errs = []
+    for dt in (0.02, 0.01):
+        _, st = _run(lat, fn, phi0, vext, dext, dt, T)
+        r, n = o.densities(st.phi, wm, wp)
+        errs.append(max(np.abs(r - r_ref).max() / np.abs(r_ref).max(), np.abs(n - n_ref).max() / np.abs(n_ref).max()))
+    assert errs[1] < 5e-5
+    assert errs[0] / errs[1] > 5
+
+
+def test_energy_conserved_to_integrator_order():
+    """Sec. 2.6: with all states the evolution conserves the energy (here
+    E_tot - mu N, the quantity of Eq. E_tot whose derivative is H, since the
+    external pairing field does not conserve N). Drift shrinks with dt^p."""
+    lat, fn, phi0, vext, dext = _tiny_case()
+    drifts = []
+    for dt in (0.02, 0.005):
+        sys, st = _run(lat, fn, phi0, vext, dext, dt, 0.48)
+        e0, e1 = sys.energy(phi0), sys.energy(st.phi)
+        drifts.append(abs((e1["e_total"] - fn.mu * e1["n_part"]) - (e0["e_total"] - fn.mu * e0["n_part"])))
+    assert drifts[1] < 1e-8
+    assert drifts[0] / drifts[1] > 8
+
+
+def test_particle_number_conserved_without_external_pairing():
+    lat, fn, phi0, vext, dext = _tiny_case(kick=0.0)
+    drifts = []
+    for dt in (0.02, 0.01):
+        sys, st = _run(lat, fn, phi0, vext, None, dt, 0.48)
+        drifts.append(abs(sys.energy(st.phi)["n_part"] - sys.energy(phi0)["n_part"]))
+    assert drifts[1] < 1e-6 and drifts[0] / drifts[1] > 8
+
+
+def test_orthonormality_preserved():
+    """Sec. 2.5: the Gram matrix stays the identity (normalisation fixes only the
+    diagonal; orthogonality is kept by the dynamics to integrator accuracy)."""
+    lat, fn, phi0, vext, dext = _tiny_case()
+    _, st = _run(lat, fn, phi0, vext, dext, 0.01, 0.48)
+    x = st.phi.reshape(lat.M, -1)
+    G = lat.dV * np.conj(x) @ x.T
+    assert np.abs(G - np.eye(lat.M)).max() < 1e-6
+
+
+def test_forward_backward_returns_initial_state():
+    """Sec. 2.5: the adiabatic evolution is time reversible."""
+    lat, fn, phi0, vext, dext = _tiny_case()
+    errs = []
+    for dt in (0.02, 0.01):
+        sys, st = _run(lat, fn, phi0, vext, dext, dt, 0.32)
+        back = o.start(sys, st.phi, -dt, stationary=False)
+        back = o.evolve(sys, back, -dt, int(round(0.32 / dt)) - 3)
+        r0, n0 = o.densities(phi0, np.ones(lat.M), np.zeros(lat.M))
+        r1, n1 = o.densities(back.phi, np.ones(lat.M), np.zeros(lat.M))
+        errs.append(max(np.abs(r1 - r0).max() / r0.max(), np.abs(n1 - n0).max() / np.abs(n0).max()))
+    assert errs[1] < 1e-4 and errs[0] / errs[1] > 4
+
+
+# ---------------------------------------------------------------- inputs module
+def test_splitmix64_matches_scalar_definition():
+    def scalar(seed, n):
+        s, out = seed, []
+        for _ in range(n):
+            s = (s + 0x9E3779B97F4A7C15) & (2 ** 64 - 1)
+            z = s
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2 ** 64 - 1)
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2 ** 64 - 1)
+            out.append(z ^ (z >> 31))
+        return out
+    for seed in (0, 1, 12345678901234):
+        assert [int(x) for x in inputs.splitmix64(seed, 20)] == scalar(seed, 20)
+    assert int(inputs.splitmix64(7, 1, offset=5)[0]) == scalar(7, 6)[5]
