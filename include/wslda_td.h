@@ -1,0 +1,170 @@
+/*
+ * wslda_td.h -- C ABI of the B300 time-dependent SLDA (TDSLDA) library.
+ *
+ * The library advances every quasiparticle pair (u_n, v_n) of one or more
+ * periodic 3D boxes with the modified equation of motion
+ *     i d(phi_n)/dt = [H - <H>_n] phi_n                (Sec. 3.4, Eq. shorttdproblem-mod)
+ * using the AB4AM5 predictor-corrector of Alg. 2, the kinetic term through
+ * FFTs (Eq. derivative-spectral, A_sigma = 1 so only the Laplacian, Eq. h_sigma_A1),
+ * the densities rho, nu summed over all states (Eqs. nab3D..jab3D, spin
+ * symmetric, frozen thermal weights Sec. 2.5) and the potentials rebuilt from
+ * the SLDA or BdG functional with the regularised coupling of Eq. Creg.
+ *
+ * Conventions shared by every call
+ *  - Units m = hbar = 1 (Sec. 2.1). Lattice sites are flattened as
+ *    (ix * ny + iy) * nz + iz (x slowest, z fastest), M = nx * ny * nz.
+ *  - A set of states is stored as [n][2][M] complex numbers, component 0 = u,
+ *    component 1 = v, each complex as two doubles (re, im), normalised to
+ *    sum_r dV (|u|^2 + |v|^2) = 1.
+ *  - Complex fields ([M] complex) are interleaved (re, im) doubles.
+ *  - Ownership: the caller owns every buffer it passes; the library copies
+ *    in and out and keeps no pointer after a call returns. Device pointers
+ *    (on_device = 1) must be device memory of the context's device; they are
+ *    read or written on the context's stream and the call synchronises that
+ *    stream before returning.
+ *  - Errors: every call returns a wslda_status; nothing aborts or throws
+ *    across the ABI. The first failure is sticky on the context (later calls
+ *    return WSLDA_ESTATE) and wslda_last_error() describes it.
+ *  - Precision: WSLDA_FP64 keeps states, FFTs and all arithmetic in double.
+ *    WSLDA_MIXED stores states as complex float, runs FFTs, the Hamiltonian
+ *    and the integrator combinations in float, and accumulates densities,
+ *    norms and energies in double through compensated float partial sums;
+ *    potentials and the regulator are double. Inputs and outputs of the ABI
+ *    are always double.
+ */
+#ifndef WSLDA_TD_H
+#define WSLDA_TD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wslda_ctx wslda_ctx;
+
+typedef enum {
+  WSLDA_OK = 0,
+  WSLDA_EINVAL = 1,      /* bad argument (sizes, null pointers, dt = 0, ...) */
+  WSLDA_ENOMEM = 2,      /* device memory budget exceeded; nothing was allocated */
+  WSLDA_ECUDA = 3,       /* a CUDA runtime call failed */
+  WSLDA_ENAN = 4,        /* a non-finite value in an input or a state norm */
+  WSLDA_EDRIFT = 5,      /* conservation check exceeded its tolerance */
+  WSLDA_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  WSLDA_ESTATE = 7,      /* call out of order, or the context holds an earlier error */
+  WSLDA_EUNSUPPORTED = 8 /* lattice shape / precision without a compiled kernel */
+} wslda_status;
+
+typedef enum { WSLDA_FP64 = 0, WSLDA_MIXED = 1 } wslda_precision;
+
+typedef enum {
+  WSLDA_FUNC_SLDA_A1 = 0, /* SLDA with A forced to 1 (Sec. 2.4, last paragraph) */
+  WSLDA_FUNC_BDG = 1      /* BdG: A = 1, B = 0, coupling 4 pi a (Eq. HBdG) */
+} wslda_functional_kind;
+
+/* Periodic lattice (Sec. 3.1). Every n must be even; see
+ * wslda_lattice_supported() for the shapes with compiled kernels. */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+} wslda_lattice;
+
+/* Energy density functional and its regularised coupling (Sec. 2.4, 2.6).
+ *  slda: E_0 = (tau_a + tau_b)/2 + 3/5 B rho eF(rho) + g_eff |nu|^2,
+ *        1/g_eff = rho^(1/3)/C - Lambda_c,  U = B eF - |Delta|^2/(3 C rho^(2/3))
+ *  bdg : 1/g_eff = inv_4pi_a - Lambda_c,     U = 0
+ *  Delta = -g_eff nu (Eq. Delta). mu is the chemical potential on the diagonal
+ *  of H. ec <= 0 selects the zone-corner cutoff (pi^2/2)(1/dx^2+1/dy^2+1/dz^2).
+ *  rho_floor bounds rho from below inside the potentials only. */
+typedef struct {
+  int kind;
+  double B, C;
+  double inv_4pi_a;
+  double mu;
+  double ec;
+  double rho_floor;
+} wslda_functional;
+
+/* Energy terms of Sec. 3.3 for A = 1. e_total is their sum; the evolution
+ * conserves e_total - mu * n_part (Eq. E_tot). */
+typedef struct {
+  double e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part;
+} wslda_energy;
+
+/* Create a context on the current CUDA device. `cuda_stream` is a borrowed
+ * cudaStream_t (NULL = legacy default stream) on which all work is queued. */
+wslda_status wslda_create(int precision, void* cuda_stream, wslda_ctx** out);
+void wslda_destroy(wslda_ctx* ctx);
+const char* wslda_last_error(const wslda_ctx* ctx);
+
+/* 1 if kernels for this lattice shape and precision are compiled in. */
+int wslda_lattice_supported(int precision, int nx, int ny, int nz);
+
+/* Add a box with `nstates` quasiparticle states. Allocates its five state
+ * buffers (phi and four ABM history slots, Alg. 2) after checking the device
+ * budget. Returns the box id (>= 0) or -(wslda_status) on failure. */
+int wslda_add_box(wslda_ctx* ctx, const wslda_lattice* lat, const wslda_functional* fn, int64_t nstates);
+
+/* External potential V_ext [M] and external pairing field Delta_ext [M complex]
+ * (Eq. E_tot, Eq. HpsiEpsi). Both default to zero. */
+wslda_status wslda_set_vext(wslda_ctx* ctx, int box, const double* vext, int on_device);
+wslda_status wslda_set_dext(wslda_ctx* ctx, int box, const double* dext, int on_device);
+
+/* Load states [n][2][M] complex. w_minus / w_plus are the frozen weights
+ * f_beta(-E_n), f_beta(E_n) (Sec. 2.5) as [n] host doubles, or NULL for T = 0
+ * (w_minus = 1, w_plus = 0). The mixed path rounds the states to complex float.
+ * Non-finite input gives WSLDA_ENAN. */
+wslda_status wslda_load_states(wslda_ctx* ctx, int box, const double* uv, const double* w_minus,
+                               const double* w_plus, int on_device);
+
+/* Prepare the integrator for every box (Sec. 3.4, start-up). Computes the
+ * densities, freezes the regulator Lambda_c at its t = 0 value, then either
+ * assumes a stationary state (stationary = 1: f_{k-2..k-4} = 0) or runs three
+ * Taylor predictor-corrector steps of order 5 (Eq. Taylor-exp), which advance
+ * the time by 3 dt. Must be called again after changing the sign of dt. */
+wslda_status wslda_start(wslda_ctx* ctx, int stationary, double dt);
+
+/* Advance every box by nsteps AB4AM5 steps of size dt (Alg. 2). */
+wslda_status wslda_step(wslda_ctx* ctx, double dt, int nsteps);
+
+/* Copy the current states out as [n][2][M] complex double. */
+wslda_status wslda_get_states(wslda_ctx* ctx, int box, double* uv, int on_device);
+
+/* Densities of the current states: rho = rho_a = rho_b [M], nu [M complex];
+ * tau [M] and j [3][M] (Eqs. nab3D..jab3D, gradients with the Nyquist mode
+ * zeroed) are computed when the pointers are not NULL. Host pointers. */
+wslda_status wslda_get_densities(wslda_ctx* ctx, int box, double* rho, double* nu, double* tau, double* j);
+
+/* Potentials built from the current densities: U [M] and Delta [M complex]
+ * (without Delta_ext). Host pointers. */
+wslda_status wslda_get_fields(wslda_ctx* ctx, int box, double* U, double* delta);
+
+/* Energy terms of the current states (Sec. 3.3). */
+wslda_status wslda_get_energy(wslda_ctx* ctx, int box, wslda_energy* out);
+
+/* Diagnostic: f(phi) = -i [H - <H>_n] phi (Eq. ABM-f) of the current states
+ * with potentials from their densities, [n][2][M] complex double on the host. */
+wslda_status wslda_eval_f(wslda_ctx* ctx, int box, double* f);
+
+/* Save / restore the full integrator state (states, history, regulator,
+ * time and step counter) to a file; resuming is bit-identical. */
+wslda_status wslda_save(wslda_ctx* ctx, const char* path);
+wslda_status wslda_load(wslda_ctx* ctx, const char* path);
+
+/* Simulation time and steps taken (including start-up steps). */
+wslda_status wslda_get_time(wslda_ctx* ctx, double* t, int64_t* steps);
+
+/* Device bytes held by the context. */
+int64_t wslda_memory_bytes(const wslda_ctx* ctx);
+
+/* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
+ * the context's stream and its duration is added to the kernel's total.
+ * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction,
+ * 3 potentials, 4 start-up / diagnostics. */
+wslda_status wslda_set_profiling(wslda_ctx* ctx, int enable);
+wslda_status wslda_get_kernel_time(wslda_ctx* ctx, int kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WSLDA_TD_H */

@@ -1,0 +1,893 @@
+// Host runtime of the C ABI declared in include/wslda_td.h.
+//
+// A context owns boxes; a box owns five state buffers (phi and four ABM
+// history slots of Alg. 2), the site fields and the chunked density partials.
+// The AB4AM5 step is four launches per box on the context's stream:
+//   stage X (f, predictor, corrector partial, normalise)   -> phi_p, c, f_{k-1}
+//   densities(phi_p) + potentials                          -> W, D
+//   stage Y (f(phi_p), corrector completion, normalise)    -> phi_k
+//   densities(phi_k) + potentials                          -> W, D
+// followed by a pointer rotation of the history slots (Alg. 2 steps 5-7).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/wslda_td.h"
+#include "internal.cuh"
+
+namespace wslda {
+std::vector<KernelSet>& registry() {
+  static std::vector<KernelSet> r;
+  return r;
+}
+}  // namespace wslda
+
+using namespace wslda;
+
+namespace {
+
+enum { PROF_X = 0, PROF_Y = 1, PROF_DENS = 2, PROF_POT = 3, PROF_AUX = 4, NPROF = 5 };
+
+struct Box {
+  wslda_lattice lat{};
+  wslda_functional fn{};
+  FunctionalDev fdev{};
+  int64_t n = 0;
+  int M = 0;
+  const KernelSet* ks = nullptr;
+  size_t csize = 0;      // bytes per complex element (8 or 16)
+  void* slot[5] = {};    // state buffers [n][2][M]
+  int iphi = 0, ih[4] = {1, 2, 3, 4};
+  double *vext = nullptr, *dext = nullptr, *lam = nullptr, *rho = nullptr, *nu = nullptr, *U = nullptr,
+         *delta = nullptr;
+  void *W = nullptr, *D = nullptr;      // working-precision H fields
+  void *ktab = nullptr, *tw = nullptr;  // per-axis kinetic symbol and twiddles
+  double *wm = nullptr, *wp = nullptr;  // double weights
+  void *wm_r = nullptr, *wp_r = nullptr;
+  double* part = nullptr;
+  int nchunk = 1;
+  int64_t chunk = 1;
+  double* Ebuf = nullptr;
+  double* ekin2 = nullptr;
+  double* out8 = nullptr;
+  bool loaded = false;
+  void* ptr(int i) const { return slot[i]; }
+};
+
+}  // namespace
+
+struct wslda_ctx {
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Box> boxes;
+  std::string err;
+  int status = WSLDA_OK;
+  int* err_d = nullptr;
+  double t = 0.0;
+  int64_t steps = 0;
+  bool started = false;
+  double dt_start = 0.0;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> evpool;
+  double prof_ms[NPROF] = {};
+  int64_t prof_n[NPROF] = {};
+};
+
+namespace {
+
+wslda_status fail(wslda_ctx* c, wslda_status st, const std::string& msg) {
+  if (c && c->status == WSLDA_OK) {
+    c->status = st;
+    c->err = msg;
+  }
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                              \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return fail(ctx, WSLDA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+#define CUDA_TRY_NEG(ctx, call)                                                                          \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return -fail(ctx, WSLDA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+#define CHECK_CTX(ctx)                                                           \
+  do {                                                                           \
+    if (!(ctx)) return WSLDA_EINVAL;                                             \
+    if ((ctx)->status != WSLDA_OK) return WSLDA_ESTATE;                          \
+  } while (0)
+
+cudaError_t dalloc(wslda_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    c->allocs.push_back(*p);
+    c->bytes += int64_t(bytes);
+  }
+  return e;
+}
+
+const KernelSet* find_kernels(int prec, int nx, int ny, int nz) {
+  for (const KernelSet& k : registry())
+    if (k.prec == prec && k.nx == nx && k.ny == ny && k.nz == nz) return &k;
+  return nullptr;
+}
+
+int brev_host(int j, int T) {
+  int r = 0;
+  for (int b = 1; b < T; b <<= 1) {
+    r <<= 1;
+    if (j & b) r |= 1;
+  }
+  return r;
+}
+
+// Kinetic symbol per slot along one axis: slot s = j + T m holds frequency
+// m + N1 brev(j) after the forward pencil transform (identity for T = 1).
+void axis_tables(int N, int T, double d, double scale, std::vector<double>& k2, std::vector<double>& twr,
+                 std::vector<double>& twi) {
+  const int N1 = N / T;
+  const long double L = (long double)N * d;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int s = 0; s < N; ++s) {
+    const int j = s % T, m = s / T;
+    const int f = m + N1 * brev_host(j, T);
+    const long double k = (f < N / 2) ? 2 * pi * f / L : 2 * pi * (f - N) / L;
+    k2.push_back(double(k * k) * scale);
+    twr.push_back(double(cosl(2 * pi * s / N)));
+    twi.push_back(double(-sinl(2 * pi * s / N)));
+  }
+}
+
+double default_cutoff(const wslda_lattice& l) {
+  return 0.5 * M_PI * M_PI * (1.0 / (l.dx * l.dx) + 1.0 / (l.dy * l.dy) + 1.0 / (l.dz * l.dz));
+}
+
+cudaEvent_t take_event(wslda_ctx* c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  wslda_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(wslda_ctx* c_, int k) : c(c_), kind(k) {
+    if (c->prof) {
+      a = take_event(c);
+      b = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof) {
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({kind, {a, b}});
+    }
+  }
+};
+
+void collect_profile(wslda_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    c->prof_ms[p.first] += ms;
+    c->prof_n[p.first] += 1;
+    c->evpool.push_back(p.second.first);
+    c->evpool.push_back(p.second.second);
+  }
+  c->pending.clear();
+}
+
+template <typename R>
+StageArgs<R> base_args(const Box& b, double dV) {
+  StageArgs<R> a = {};
+  a.W = static_cast<const R*>(b.W);
+  a.D = static_cast<const cx<R>*>(b.D);
+  a.ktab = static_cast<const R*>(b.ktab);
+  a.tw = static_cast<const cx<R>*>(b.tw);
+  a.E = b.Ebuf;
+  a.out2 = b.ekin2;
+  a.dV = dV;
+  a.nstates = int(b.n);
+  return a;
+}
+
+double box_dV(const Box& b) { return b.lat.dx * b.lat.dy * b.lat.dz; }
+
+template <typename R>
+wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int kind) {
+  a.err = c->err_d;
+  if (b.n == 0) return WSLDA_OK;
+  ProfScope ps(c, kind);
+  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), c->stream));
+  return WSLDA_OK;
+}
+
+// densities of slot `islot` -> potentials -> H fields
+template <typename R>
+wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
+  if (b.n > 0) {
+    ProfScope ps(c, PROF_DENS);
+    CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), static_cast<const R*>(b.wm_r),
+                                          static_cast<const R*>(b.wp_r), b.n, b.M, b.nchunk, b.chunk, b.part,
+                                          c->stream));
+  } else {
+    CUDA_TRY(c, cudaMemsetAsync(b.part, 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->stream));
+  }
+  ProfScope ps2(c, PROF_POT);
+  CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu, b.U,
+                                   b.delta, static_cast<R*>(b.W), static_cast<cx<R>*>(b.D), c->stream));
+  return WSLDA_OK;
+}
+
+wslda_status refresh_fields(wslda_ctx* c, Box& b, int islot, int init_lam) {
+  return c->prec == WSLDA_MIXED ? refresh_fields_t<float>(c, b, islot, init_lam)
+                                : refresh_fields_t<double>(c, b, islot, init_lam);
+}
+
+template <typename R>
+wslda_status stage_x(wslda_ctx* c, Box& b, double dt) {
+  StageArgs<R> a = base_args<R>(b, box_dV(b));
+  a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
+  a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[0]));
+  a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[1]));
+  a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
+  a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  a.dt = dt;
+  return launch_mode<R>(c, b, MODE_X, a, PROF_X);
+}
+
+template <typename R>
+wslda_status stage_y(wslda_ctx* c, Box& b, double dt) {
+  StageArgs<R> a = base_args<R>(b, box_dV(b));
+  a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
+  a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  a.dt = dt;
+  return launch_mode<R>(c, b, MODE_Y, a, PROF_Y);
+}
+
+template <typename R>
+wslda_status eval_f_into(wslda_ctx* c, Box& b, int in_slot, int out_slot) {
+  StageArgs<R> a = base_args<R>(b, box_dV(b));
+  a.phi = static_cast<cx<R>*>(b.ptr(in_slot));
+  a.h0 = static_cast<cx<R>*>(b.ptr(out_slot));
+  return launch_mode<R>(c, b, MODE_F, a, PROF_AUX);
+}
+
+// One Horner step out = base + coef (H - E) in (Taylor series, Eq. Taylor-exp).
+template <typename R>
+wslda_status horner(wslda_ctx* c, Box& b, int in_slot, int base_slot, int out_slot, double coef_im, int compute_e,
+                    int normalize) {
+  StageArgs<R> a = base_args<R>(b, box_dV(b));
+  a.phi = static_cast<cx<R>*>(b.ptr(in_slot));
+  a.h1 = static_cast<const cx<R>*>(b.ptr(base_slot));
+  a.h0 = static_cast<cx<R>*>(b.ptr(out_slot));
+  a.coef_re = 0.0;
+  a.coef_im = coef_im;
+  a.compute_e = compute_e;
+  a.normalize = normalize;
+  return launch_mode<R>(c, b, MODE_HORNER, a, PROF_AUX);
+}
+
+// sum_{k=0}^{r} (-i h)^k/k! (H - E)^k phi by Horner's rule: p = phi;
+// p = phi + (-i h / k) (H - E) p for k = r..1; E = <phi|H|phi> taken in the
+// first application (reading T1). The result is normalised (reading T2).
+template <typename R>
+wslda_status taylor_series(wslda_ctx* c, Box& b, int phi_slot, int out_slot, double h, int r) {
+  for (int k = r; k >= 1; --k) {
+    const int in = (k == r) ? phi_slot : out_slot;
+    wslda_status st = horner<R>(c, b, in, phi_slot, out_slot, -h / k, k == r, k == 1);
+    if (st) return st;
+  }
+  return WSLDA_OK;
+}
+
+// Predictor-corrector Taylor step of Sec. 3.4 (order r = 5).
+template <typename R>
+wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
+  const int y = b.ih[0];
+  wslda_status st;
+  if ((st = taylor_series<R>(c, b, b.iphi, y, 0.5 * dt, 5))) return st;  // midpoint state
+  if ((st = refresh_fields(c, b, y, 0))) return st;                      // H(t + dt/2)
+  if ((st = taylor_series<R>(c, b, b.iphi, y, dt, 5))) return st;       // phi(t + dt)
+  std::swap(b.iphi, b.ih[0]);
+  return refresh_fields(c, b, b.iphi, 0);
+}
+
+template <typename R>
+wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
+  wslda_status st;
+  if ((st = refresh_fields(c, b, b.iphi, 1))) return st;
+  const size_t bytes = size_t(b.n) * 2 * b.M * b.csize;
+  if (stationary) {
+    for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
+    return WSLDA_OK;
+  }
+  // history f(phi_0), f(phi_1), f(phi_2) into f_{k-4}, f_{k-3}, f_{k-2};
+  // f(phi_3) is formed by the first stage X.
+  if ((st = eval_f_into<R>(c, b, b.iphi, b.ih[3]))) return st;
+  for (int s = 1; s <= 3; ++s) {
+    if ((st = taylor_step<R>(c, b, dt))) return st;
+    if (s < 3 && (st = eval_f_into<R>(c, b, b.iphi, b.ih[3 - s]))) return st;
+  }
+  return WSLDA_OK;
+}
+
+template <typename R>
+wslda_status step_all(wslda_ctx* c, double dt) {
+  wslda_status st;
+  for (Box& b : c->boxes)
+    if ((st = stage_x<R>(c, b, dt))) return st;
+  for (Box& b : c->boxes)
+    if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
+  for (Box& b : c->boxes)
+    if ((st = stage_y<R>(c, b, dt))) return st;
+  for (Box& b : c->boxes) {
+    if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
+    // Alg. 2 steps 5-7: the slot that held c becomes the slot for the next f_{k-1}
+    const int freed = b.ih[3];
+    b.ih[3] = b.ih[2];
+    b.ih[2] = b.ih[1];
+    b.ih[1] = b.ih[0];
+    b.ih[0] = freed;
+  }
+  return WSLDA_OK;
+}
+
+wslda_status check_device_error(wslda_ctx* c) {
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h & 1) return fail(c, WSLDA_ENAN, "a state norm became non-finite or zero");
+  if (h & 2) return fail(c, WSLDA_ENAN, "non-finite value in the loaded states");
+  return WSLDA_OK;
+}
+
+Box* get_box(wslda_ctx* c, int box) {
+  if (box < 0 || box >= int(c->boxes.size())) return nullptr;
+  return &c->boxes[box];
+}
+
+wslda_status copy_in(wslda_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+  CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  return WSLDA_OK;
+}
+
+constexpr size_t kStageBytes = size_t(256) << 20;  // staging buffer for state transfers
+
+}  // namespace
+
+extern "C" {
+
+int wslda_lattice_supported(int precision, int nx, int ny, int nz) {
+  return find_kernels(precision == WSLDA_MIXED ? 1 : 0, nx, ny, nz) != nullptr;
+}
+
+wslda_status wslda_create(int precision, void* stream, wslda_ctx** out) {
+  if (!out || (precision != WSLDA_FP64 && precision != WSLDA_MIXED)) return WSLDA_EINVAL;
+  wslda_ctx* c = new wslda_ctx();
+  c->prec = precision;
+  c->stream = static_cast<cudaStream_t>(stream);
+  void* p = nullptr;
+  cudaError_t e = dalloc(c, &p, sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    *out = nullptr;
+    return WSLDA_ECUDA;
+  }
+  c->err_d = static_cast<int*>(p);
+  cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream);
+  *out = c;
+  return WSLDA_OK;
+}
+
+void wslda_destroy(wslda_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* wslda_last_error(const wslda_ctx* c) {
+  if (!c) return "null context";
+  return c->err.empty() ? "" : c->err.c_str();
+}
+
+int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional* fn, int64_t nstates) {
+  if (!c) return -WSLDA_EINVAL;
+  if (c->status != WSLDA_OK) return -WSLDA_ESTATE;
+  if (!lat || !fn || nstates < 0) return -fail(c, WSLDA_EINVAL, "add_box: null argument or negative state count");
+  if (c->started) return -fail(c, WSLDA_ESTATE, "add_box after wslda_start");
+  if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0 || (lat->nx | lat->ny | lat->nz) & 1)
+    return -fail(c, WSLDA_EINVAL, "lattice sizes must be positive and even");
+  if (!(lat->dx > 0 && lat->dy > 0 && lat->dz > 0)) return -fail(c, WSLDA_EINVAL, "lattice spacings must be > 0");
+  if (fn->kind != WSLDA_FUNC_SLDA_A1 && fn->kind != WSLDA_FUNC_BDG)
+    return -fail(c, WSLDA_EINVAL, "unknown functional kind");
+  if (fn->kind == WSLDA_FUNC_SLDA_A1 && !(fn->C != 0.0)) return -fail(c, WSLDA_EINVAL, "SLDA needs C != 0");
+  const int prec = c->prec == WSLDA_MIXED ? 1 : 0;
+  const KernelSet* ks = find_kernels(prec, lat->nx, lat->ny, lat->nz);
+  if (!ks) return -fail(c, WSLDA_EUNSUPPORTED, "no compiled kernels for this lattice shape and precision");
+  const int64_t M = int64_t(lat->nx) * lat->ny * lat->nz;
+  if (nstates > (int64_t(1) << 31) / ks->cs - 1) return -fail(c, WSLDA_EINVAL, "too many states for one launch");
+
+  Box b;
+  b.lat = *lat;
+  b.fn = *fn;
+  b.n = nstates;
+  b.M = int(M);
+  b.ks = ks;
+  b.csize = prec ? 8 : 16;
+  const size_t rsize = prec ? 4 : 8;
+  b.fdev.kind = fn->kind;
+  b.fdev.B = fn->B;
+  b.fdev.C = fn->C;
+  b.fdev.inv_4pi_a = fn->inv_4pi_a;
+  b.fdev.mu = fn->mu;
+  b.fdev.ec = fn->ec > 0 ? fn->ec : default_cutoff(*lat);
+  b.fdev.rho_floor = fn->rho_floor > 0 ? fn->rho_floor : 1e-12;
+  const int sites_blocks = int((M + 255) / 256);
+  b.nchunk = int(std::max<int64_t>(1, std::min<int64_t>({256, (4 * 148 + sites_blocks - 1) / sites_blocks,
+                                                          std::max<int64_t>(1, nstates / 16)})));
+  b.chunk = std::max<int64_t>(1, (nstates + b.nchunk - 1) / b.nchunk);
+
+  const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
+  const size_t field_bytes = size_t(M) * (8 * 9 + rsize * 3) + size_t(3) * M * 8 * b.nchunk +
+                             size_t(nstates) * (8 * 5 + rsize * 2) + 4096;
+  const size_t need = 5 * state_bytes + field_bytes;
+  size_t freeb = 0, totalb = 0;
+  CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
+  const size_t margin = size_t(1) << 30;
+  if (need + margin > freeb) {
+    fail(c, WSLDA_ENOMEM, "box needs " + std::to_string(need >> 20) + " MiB, " + std::to_string(freeb >> 20) +
+                              " MiB free");
+    return -WSLDA_ENOMEM;
+  }
+  int ncl = 0;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ks->cs * 16);
+    cfg.blockDim = dim3(ks->bt);
+    cfg.dynamicSmemBytes = ks->smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ks->cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    for (int m = 0; m < NMODES; ++m) {
+      cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks->smem));
+      if (ks->cs > 8) cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    CUDA_TRY_NEG(c, cudaOccupancyMaxActiveClusters(&ncl, ks->fn[MODE_X], &cfg));
+    if (ncl < 1) return -fail(c, WSLDA_EUNSUPPORTED, "stage kernel cannot be resident on this device");
+  }
+
+#define ALLOC(ptr, bytes)                                                            \
+  do {                                                                               \
+    void* p_ = nullptr;                                                              \
+    cudaError_t e_ = dalloc(c, &p_, (bytes));                                        \
+    if (e_ != cudaSuccess) {                                                         \
+      fail(c, WSLDA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e_));  \
+      return -WSLDA_ENOMEM;                                                          \
+    }                                                                                \
+    ptr = decltype(ptr)(p_);                                                         \
+  } while (0)
+
+  for (int i = 0; i < 5; ++i) ALLOC(b.slot[i], state_bytes);
+  ALLOC(b.vext, M * 8);
+  ALLOC(b.dext, 2 * M * 8);
+  ALLOC(b.lam, M * 8);
+  ALLOC(b.rho, M * 8);
+  ALLOC(b.nu, 2 * M * 8);
+  ALLOC(b.U, M * 8);
+  ALLOC(b.delta, 2 * M * 8);
+  ALLOC(b.W, M * rsize);
+  ALLOC(b.D, 2 * M * rsize);
+  const int naxis = lat->nx + lat->ny + lat->nz;
+  ALLOC(b.ktab, naxis * rsize);
+  ALLOC(b.tw, 2 * naxis * rsize);
+  ALLOC(b.wm, std::max<int64_t>(nstates, 1) * 8);
+  ALLOC(b.wp, std::max<int64_t>(nstates, 1) * 8);
+  ALLOC(b.wm_r, std::max<int64_t>(nstates, 1) * rsize);
+  ALLOC(b.wp_r, std::max<int64_t>(nstates, 1) * rsize);
+  ALLOC(b.part, size_t(3) * M * 8 * b.nchunk);
+  ALLOC(b.Ebuf, std::max<int64_t>(nstates, 1) * 8);
+  ALLOC(b.ekin2, std::max<int64_t>(nstates, 1) * 16);
+  ALLOC(b.out8, 8 * 8);
+#undef ALLOC
+  CUDA_TRY_NEG(c, cudaMemsetAsync(b.vext, 0, M * 8, c->stream));
+  CUDA_TRY_NEG(c, cudaMemsetAsync(b.dext, 0, 2 * M * 8, c->stream));
+
+  // kinetic symbol k_d^2 * 0.5 / M per slot (1/M folds in the unnormalised inverse FFT)
+  std::vector<double> k2, twr, twi;
+  const double scale = 0.5 / double(M);
+  axis_tables(lat->nx, ks->tx, lat->dx, scale, k2, twr, twi);
+  axis_tables(lat->ny, ks->ty, lat->dy, scale, k2, twr, twi);
+  axis_tables(lat->nz, ks->tz, lat->dz, scale, k2, twr, twi);
+  std::vector<double> tw(2 * naxis);
+  for (int i = 0; i < naxis; ++i) {
+    tw[2 * i] = twr[i];
+    tw[2 * i + 1] = twi[i];
+  }
+  void* tmp = nullptr;
+  CUDA_TRY_NEG(c, cudaMalloc(&tmp, 3 * naxis * 8));
+  cudaMemcpyAsync(tmp, k2.data(), naxis * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(static_cast<char*>(tmp) + naxis * 8, tw.data(), 2 * naxis * 8, cudaMemcpyHostToDevice, c->stream);
+  if (prec) {
+    launch_to_real<float>(static_cast<double*>(tmp), static_cast<float*>(b.ktab), naxis, c->stream);
+    launch_to_real<float>(static_cast<double*>(tmp) + naxis, static_cast<float*>(b.tw), 2 * naxis, c->stream);
+  } else {
+    cudaMemcpyAsync(b.ktab, tmp, naxis * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(b.tw, static_cast<double*>(tmp) + naxis, 2 * naxis * 8, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  CUDA_TRY_NEG(c, cudaStreamSynchronize(c->stream));
+  cudaFree(tmp);
+  c->boxes.push_back(b);
+  return int(c->boxes.size()) - 1;
+}
+
+wslda_status wslda_set_vext(wslda_ctx* c, int box, const double* vext, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !vext) return fail(c, WSLDA_EINVAL, "set_vext: bad box or null pointer");
+  if (c->started) return fail(c, WSLDA_ESTATE, "set_vext after wslda_start");
+  return copy_in(c, b->vext, vext, size_t(b->M) * 8, on_device);
+}
+
+wslda_status wslda_set_dext(wslda_ctx* c, int box, const double* dext, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !dext) return fail(c, WSLDA_EINVAL, "set_dext: bad box or null pointer");
+  if (c->started) return fail(c, WSLDA_ESTATE, "set_dext after wslda_start");
+  return copy_in(c, b->dext, dext, size_t(b->M) * 16, on_device);
+}
+
+wslda_status wslda_load_states(wslda_ctx* c, int box, const double* uv, const double* w_minus, const double* w_plus,
+                               int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || (!uv && b->n > 0)) return fail(c, WSLDA_EINVAL, "load_states: bad box or null pointer");
+  if (c->started) return fail(c, WSLDA_ESTATE, "load_states after wslda_start");
+  const int64_t total = b->n * 2 * int64_t(b->M);  // complex elements
+  const int64_t per = int64_t(kStageBytes / 16);
+  void* stage = nullptr;
+  if (total > 0) CUDA_TRY(c, cudaMalloc(&stage, size_t(std::min(total, per)) * 16));
+  for (int64_t off = 0; off < total; off += per) {
+    const int64_t cnt = std::min(per, total - off);
+    const double* src = uv + 2 * off;
+    const double* dsrc = src;
+    if (!on_device) {
+      CUDA_TRY(c, cudaMemcpyAsync(stage, src, cnt * 16, cudaMemcpyHostToDevice, c->stream));
+      dsrc = static_cast<const double*>(stage);
+    }
+    cudaError_t e;
+    if (c->prec == WSLDA_MIXED)
+      e = launch_narrow<float>(dsrc, static_cast<float2*>(b->slot[b->iphi]) + off, cnt, c->err_d, c->stream);
+    else
+      e = launch_narrow<double>(dsrc, static_cast<double2*>(b->slot[b->iphi]) + off, cnt, c->err_d, c->stream);
+    if (e != cudaSuccess) {
+      cudaFree(stage);
+      return fail(c, WSLDA_ECUDA, std::string("narrow: ") + cudaGetErrorString(e));
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stage) cudaFree(stage);
+  std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
+  for (int64_t i = 0; i < b->n; ++i) {
+    if (w_minus) wm[i] = w_minus[i];
+    if (w_plus) wp[i] = w_plus[i];
+    if (!std::isfinite(wm[i]) || !std::isfinite(wp[i])) return fail(c, WSLDA_ENAN, "non-finite weight");
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(b->wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(b->wp, wp.data(), wp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == WSLDA_MIXED) {
+    CUDA_TRY(c, launch_to_real<float>(b->wm, static_cast<float*>(b->wm_r), int64_t(wm.size()), c->stream));
+    CUDA_TRY(c, launch_to_real<float>(b->wp, static_cast<float*>(b->wp_r), int64_t(wp.size()), c->stream));
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(b->wm_r, b->wm, wm.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(b->wp_r, b->wp, wp.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  wslda_status st = check_device_error(c);
+  if (st) return st;
+  b->loaded = true;
+  return WSLDA_OK;
+}
+
+wslda_status wslda_start(wslda_ctx* c, int stationary, double dt) {
+  CHECK_CTX(c);
+  if (!(dt != 0.0) || !std::isfinite(dt)) return fail(c, WSLDA_EINVAL, "dt must be finite and non-zero");
+  if (c->boxes.empty()) return fail(c, WSLDA_ESTATE, "no boxes");
+  for (Box& b : c->boxes)
+    if (!b.loaded) return fail(c, WSLDA_ESTATE, "wslda_start before load_states");
+  wslda_status st;
+  for (Box& b : c->boxes) {
+    st = c->prec == WSLDA_MIXED ? start_box<float>(c, b, stationary, dt) : start_box<double>(c, b, stationary, dt);
+    if (st) return st;
+  }
+  collect_profile(c);
+  if ((st = check_device_error(c))) return st;
+  c->started = true;
+  c->dt_start = dt;
+  c->t = stationary ? 0.0 : 3 * dt;
+  c->steps = stationary ? 0 : 3;
+  return WSLDA_OK;
+}
+
+wslda_status wslda_step(wslda_ctx* c, double dt, int nsteps) {
+  CHECK_CTX(c);
+  if (!c->started) return fail(c, WSLDA_ESTATE, "wslda_step before wslda_start");
+  if (nsteps < 0) return fail(c, WSLDA_EINVAL, "nsteps < 0");
+  if (dt != c->dt_start) return fail(c, WSLDA_EINVAL, "dt differs from the start-up dt; call wslda_start again");
+  for (int i = 0; i < nsteps; ++i) {
+    wslda_status st = c->prec == WSLDA_MIXED ? step_all<float>(c, dt) : step_all<double>(c, dt);
+    if (st) return st;
+    if (c->prof && c->pending.size() > 4096) collect_profile(c);
+  }
+  collect_profile(c);
+  wslda_status st = check_device_error(c);
+  if (st) return st;
+  c->t += nsteps * dt;
+  c->steps += nsteps;
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_states(wslda_ctx* c, int box, double* uv, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || (!uv && b->n > 0)) return fail(c, WSLDA_EINVAL, "get_states: bad box or null pointer");
+  const int64_t total = b->n * 2 * int64_t(b->M);
+  const int64_t per = int64_t(kStageBytes / 16);
+  void* stage = nullptr;
+  if (total > 0 && !on_device) CUDA_TRY(c, cudaMalloc(&stage, size_t(std::min(total, per)) * 16));
+  for (int64_t off = 0; off < total; off += per) {
+    const int64_t cnt = std::min(per, total - off);
+    double* dst = on_device ? uv + 2 * off : static_cast<double*>(stage);
+    cudaError_t e = c->prec == WSLDA_MIXED
+                        ? launch_widen<float>(static_cast<float2*>(b->slot[b->iphi]) + off, dst, cnt, c->stream)
+                        : launch_widen<double>(static_cast<double2*>(b->slot[b->iphi]) + off, dst, cnt, c->stream);
+    if (e != cudaSuccess) {
+      if (stage) cudaFree(stage);
+      return fail(c, WSLDA_ECUDA, std::string("widen: ") + cudaGetErrorString(e));
+    }
+    if (!on_device) CUDA_TRY(c, cudaMemcpyAsync(uv + 2 * off, stage, cnt * 16, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stage) cudaFree(stage);
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu, double* tau, double* j) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "get_densities: bad box");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_densities before load_states");
+  if (tau || j) return fail(c, WSLDA_EUNSUPPORTED, "tau and j are not available yet");
+  if (!c->started) {
+    // densities of the loaded states (regulator from the t = 0 fixed point)
+    wslda_status st = refresh_fields(c, *b, b->iphi, 1);
+    if (st) return st;
+  }
+  if (rho) CUDA_TRY(c, cudaMemcpyAsync(rho, b->rho, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (nu) CUDA_TRY(c, cudaMemcpyAsync(nu, b->nu, size_t(b->M) * 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_fields(wslda_ctx* c, int box, double* U, double* delta) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "get_fields: bad box");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_fields before load_states");
+  if (!c->started) {
+    wslda_status st = refresh_fields(c, *b, b->iphi, 1);
+    if (st) return st;
+  }
+  if (U) CUDA_TRY(c, cudaMemcpyAsync(U, b->U, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (delta) CUDA_TRY(c, cudaMemcpyAsync(delta, b->delta, size_t(b->M) * 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_energy(wslda_ctx* c, int box, wslda_energy* out) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !out) return fail(c, WSLDA_EINVAL, "get_energy: bad box or null pointer");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_energy before load_states");
+  wslda_status st;
+  if (!c->started && (st = refresh_fields(c, *b, b->iphi, 1))) return st;
+  if (c->prec == WSLDA_MIXED) {
+    StageArgs<float> a = base_args<float>(*b, box_dV(*b));
+    a.phi = static_cast<float2*>(b->ptr(b->iphi));
+    if ((st = launch_mode<float>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
+  } else {
+    StageArgs<double> a = base_args<double>(*b, box_dV(*b));
+    a.phi = static_cast<double2*>(b->ptr(b->iphi));
+    if ((st = launch_mode<double>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
+  }
+  CUDA_TRY(c, launch_energy(b->M, b->n, b->fdev, b->rho, b->nu, b->delta, b->vext, b->dext, b->ekin2, b->wm, b->wp,
+                            box_dV(*b), b->out8, c->stream));
+  double h[8];
+  CUDA_TRY(c, cudaMemcpyAsync(h, b->out8, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  collect_profile(c);
+  out->e_kin = h[0];
+  out->e_pot = h[1];
+  out->e_pair = h[2];
+  out->e_ext = h[3];
+  out->e_pair_ext = h[4];
+  out->e_total = h[5];
+  out->n_part = h[6];
+  return WSLDA_OK;
+}
+
+wslda_status wslda_eval_f(wslda_ctx* c, int box, double* f) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || (!f && b->n > 0)) return fail(c, WSLDA_EINVAL, "eval_f: bad box or null pointer");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "eval_f before load_states");
+  if (c->started) return fail(c, WSLDA_ESTATE, "eval_f is a diagnostic of the loaded states, before wslda_start");
+  wslda_status st;
+  if ((st = refresh_fields(c, *b, b->iphi, 1))) return st;
+  const int out = b->ih[0];
+  st = c->prec == WSLDA_MIXED ? eval_f_into<float>(c, *b, b->iphi, out) : eval_f_into<double>(c, *b, b->iphi, out);
+  if (st) return st;
+  std::swap(b->iphi, b->ih[0]);
+  st = wslda_get_states(c, box, f, 0);
+  std::swap(b->iphi, b->ih[0]);
+  if (st) return st;
+  collect_profile(c);
+  return check_device_error(c);
+}
+
+wslda_status wslda_get_time(wslda_ctx* c, double* t, int64_t* steps) {
+  CHECK_CTX(c);
+  if (t) *t = c->t;
+  if (steps) *steps = c->steps;
+  return WSLDA_OK;
+}
+
+int64_t wslda_memory_bytes(const wslda_ctx* c) { return c ? c->bytes : 0; }
+
+wslda_status wslda_set_profiling(wslda_ctx* c, int enable) {
+  CHECK_CTX(c);
+  collect_profile(c);
+  c->prof = enable != 0;
+  for (int i = 0; i < NPROF; ++i) {
+    c->prof_ms[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_kernel_time(wslda_ctx* c, int kind, double* total_ms, int64_t* launches) {
+  CHECK_CTX(c);
+  if (kind < 0 || kind >= NPROF) return fail(c, WSLDA_EINVAL, "kernel kind out of range");
+  collect_profile(c);
+  if (total_ms) *total_ms = c->prof_ms[kind];
+  if (launches) *launches = c->prof_n[kind];
+  return WSLDA_OK;
+}
+
+// File layout: "WSLDATD1", prec, nboxes, t, steps, dt_start, started; per box:
+// nx ny nz n iphi ih[4], then phi, h0..h3 (slot order), lam, vext, dext, wm, wp.
+wslda_status wslda_save(wslda_ctx* c, const char* path) {
+  CHECK_CTX(c);
+  if (!path) return fail(c, WSLDA_EINVAL, "save: null path");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, WSLDA_EINVAL, std::string("save: cannot open ") + path);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '1'};
+  int32_t hdr[3] = {c->prec, int32_t(c->boxes.size()), c->started ? 1 : 0};
+  fwrite(magic, 1, 8, f);
+  fwrite(hdr, sizeof(hdr), 1, f);
+  fwrite(&c->t, 8, 1, f);
+  fwrite(&c->steps, 8, 1, f);
+  fwrite(&c->dt_start, 8, 1, f);
+  std::vector<char> host;
+  auto dump = [&](const void* d, size_t bytes) -> bool {
+    host.resize(bytes);
+    if (cudaMemcpy(host.data(), d, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return fwrite(host.data(), 1, bytes, f) == bytes;
+  };
+  bool ok = true;
+  for (Box& b : c->boxes) {
+    int64_t bh[9] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3]};
+    fwrite(bh, sizeof(bh), 1, f);
+    const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
+    for (int i = 0; i < 5 && ok; ++i) ok = dump(b.slot[i], sb);
+    ok = ok && dump(b.lam, size_t(b.M) * 8) && dump(b.vext, size_t(b.M) * 8) && dump(b.dext, size_t(b.M) * 16) &&
+         dump(b.wm, std::max<int64_t>(b.n, 1) * 8) && dump(b.wp, std::max<int64_t>(b.n, 1) * 8);
+  }
+  fclose(f);
+  if (!ok) return fail(c, WSLDA_ECUDA, "save: device read or file write failed");
+  return WSLDA_OK;
+}
+
+wslda_status wslda_load(wslda_ctx* c, const char* path) {
+  CHECK_CTX(c);
+  if (!path) return fail(c, WSLDA_EINVAL, "load: null path");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, WSLDA_EINVAL, std::string("load: cannot open ") + path);
+  char magic[8];
+  int32_t hdr[3];
+  double t, dts;
+  int64_t steps;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD1", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+            fread(&t, 8, 1, f) == 1 && fread(&steps, 8, 1, f) == 1 && fread(&dts, 8, 1, f) == 1;
+  if (!ok || hdr[0] != c->prec || hdr[1] != int32_t(c->boxes.size())) {
+    fclose(f);
+    return fail(c, WSLDA_EINVAL, "load: file does not match this context (precision / box count)");
+  }
+  std::vector<char> host;
+  auto slurp = [&](void* d, size_t bytes) -> bool {
+    host.resize(bytes);
+    if (fread(host.data(), 1, bytes, f) != bytes) return false;
+    return cudaMemcpy(d, host.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  for (Box& b : c->boxes) {
+    int64_t bh[9];
+    ok = ok && fread(bh, sizeof(bh), 1, f) == 1 && bh[0] == b.lat.nx && bh[1] == b.lat.ny && bh[2] == b.lat.nz &&
+         bh[3] == b.n;
+    if (!ok) break;
+    b.iphi = int(bh[4]);
+    for (int i = 0; i < 4; ++i) b.ih[i] = int(bh[5 + i]);
+    const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
+    for (int i = 0; i < 5 && ok; ++i) ok = slurp(b.slot[i], sb);
+    ok = ok && slurp(b.lam, size_t(b.M) * 8) && slurp(b.vext, size_t(b.M) * 8) && slurp(b.dext, size_t(b.M) * 16) &&
+         slurp(b.wm, std::max<int64_t>(b.n, 1) * 8) && slurp(b.wp, std::max<int64_t>(b.n, 1) * 8);
+    if (!ok) break;
+    if (c->prec == WSLDA_MIXED) {
+      launch_to_real<float>(b.wm, static_cast<float*>(b.wm_r), std::max<int64_t>(b.n, 1), c->stream);
+      launch_to_real<float>(b.wp, static_cast<float*>(b.wp_r), std::max<int64_t>(b.n, 1), c->stream);
+    } else {
+      cudaMemcpyAsync(b.wm_r, b.wm, std::max<int64_t>(b.n, 1) * 8, cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(b.wp_r, b.wp, std::max<int64_t>(b.n, 1) * 8, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    b.loaded = true;
+    wslda_status st = refresh_fields(c, b, b.iphi, 0);
+    if (st) {
+      fclose(f);
+      return st;
+    }
+  }
+  fclose(f);
+  if (!ok) return fail(c, WSLDA_EINVAL, "load: truncated or mismatched file");
+  c->t = t;
+  c->steps = steps;
+  c->dt_start = dts;
+  c->started = hdr[2] != 0;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+// Site-major kernels: density reduction over states (spin-symmetric, frozen
+// weights: Eqs. nab3D.., Sec. 2.5), potentials from the SLDA / BdG functional
+// with the regularised coupling (Sec. 2.4, Eq. Creg), energy terms (Sec. 3.3),
+// and precision conversions at the ABI boundary.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace wslda {
+
+// ---------------------------------------------------------------------------
+// Density partial sums. Thread = lattice site, grid.y = chunk of states.
+// rho += w- |v|^2 + w+ |u|^2 ;  nu += (w- - w+) u v^*.
+// Float states: products in float, Kahan-compensated float sums over groups
+// of kGroup states, each group folded into double accumulators.
+// Double states: plain double sums.
+// ---------------------------------------------------------------------------
+constexpr int kGroup = 32;
+
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __restrict__ phi, const R* __restrict__ wm,
+                                                              const R* __restrict__ wp, int64_t nstates, int M,
+                                                              int64_t chunk, double* __restrict__ part) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int64_t n0 = int64_t(blockIdx.y) * chunk;
+  const int64_t n1 = min(n0 + chunk, nstates);
+  const int64_t stride = 2 * int64_t(M);
+  double ar = 0.0, anr = 0.0, ani = 0.0;
+  if constexpr (sizeof(R) == 4) {
+    for (int64_t g = n0; g < n1; g += kGroup) {
+      float sr = 0.f, cr = 0.f, snr = 0.f, cnr = 0.f, sni = 0.f, cni = 0.f;
+      const int64_t ge = min(g + kGroup, n1);
+#pragma unroll 4
+      for (int64_t n = g; n < ge; ++n) {
+        const float2 u = phi[n * stride + s];
+        const float2 v = phi[n * stride + M + s];
+        const float a = wm[n], b = wp[n], d = a - b;
+        kahan(sr, cr, a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y));
+        kahan(snr, cnr, d * (u.x * v.x + u.y * v.y));
+        kahan(sni, cni, d * (u.y * v.x - u.x * v.y));
+      }
+      ar += double(sr) - double(cr);
+      anr += double(snr) - double(cnr);
+      ani += double(sni) - double(cni);
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t n = n0; n < n1; ++n) {
+      const double2 u = phi[n * stride + s];
+      const double2 v = phi[n * stride + M + s];
+      const double a = wm[n], b = wp[n], d = a - b;
+      ar += a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y);
+      anr += d * (u.x * v.x + u.y * v.y);
+      ani += d * (u.y * v.x - u.x * v.y);
+    }
+  }
+  double* p = part + int64_t(blockIdx.y) * 3 * M;
+  p[s] = ar;
+  p[M + s] = anr;
+  p[2 * M + s] = ani;
+}
+
+template <typename R>
+cudaError_t launch_density_partial(const cx<R>* phi, const R* wm, const R* wp, int64_t nstates, int M, int nchunk,
+                                   int64_t chunk, double* part, cudaStream_t s) {
+  dim3 grid((M + 255) / 256, nchunk);
+  density_partial_kernel<R><<<grid, 256, 0, s>>>(phi, wm, wp, nstates, M, chunk, part);
+  return cudaGetLastError();
+}
+template cudaError_t launch_density_partial<float>(const float2*, const float*, const float*, int64_t, int, int,
+                                                   int64_t, double*, cudaStream_t);
+template cudaError_t launch_density_partial<double>(const double2*, const double*, const double*, int64_t, int, int,
+                                                    int64_t, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Functional (Sec. 2.4) and regulator (Sec. 2.6) at one site.
+// ---------------------------------------------------------------------------
+__device__ double regulator(double mu_minus_V, double ec) {
+  // Lambda_c = (1/2 pi^2) PV int_0^kc k^2 dk / (k^2 - k0^2), A = 1:
+  // k0^2 = 2 (mu - V), kc^2 = 2 (E_c + mu - V).
+  const double k0sq = 2.0 * mu_minus_V;
+  const double kcsq = 2.0 * (ec + mu_minus_V);
+  if (!(kcsq > 0.0)) return 0.0;
+  const double kc = sqrt(kcsq);
+  const double pref = kc / (2.0 * M_PI * M_PI);
+  if (k0sq > 0.0) {
+    const double k0 = sqrt(k0sq);
+    return pref * (1.0 - (k0 / (2.0 * kc)) * log((kc + k0) / (kc - k0)));
+  }
+  if (k0sq < 0.0) {
+    const double kap = sqrt(-k0sq);
+    return pref * (1.0 - (kap / kc) * atan2(kc, kap));
+  }
+  return pref;
+}
+
+__device__ __forceinline__ double fermi_energy(double rho_total) {
+  const double c = cbrt(3.0 * M_PI * M_PI * rho_total);
+  return 0.5 * c * c;
+}
+
+// (U, Delta) at one site from rho_sigma, nu and the regulator value lam.
+__device__ void site_potentials(const FunctionalDev& fn, double rho_s, double nr, double ni, double lam, double& U,
+                                double& dr, double& di) {
+  double inv_g;
+  double rho = 2.0 * rho_s;
+  if (fn.kind == 0) {
+    rho = fmax(rho, fn.rho_floor);
+    inv_g = cbrt(rho) / fn.C - lam;
+  } else {
+    inv_g = fn.inv_4pi_a - lam;
+  }
+  const double g = 1.0 / inv_g;
+  dr = -g * nr;
+  di = -g * ni;
+  if (fn.kind == 0) {
+    const double r13 = cbrt(rho);
+    U = fn.B * fermi_energy(rho) - (dr * dr + di * di) / (3.0 * fn.C * r13 * r13);
+  } else {
+    U = 0.0;
+  }
+}
+
+constexpr int kRegulatorIters = 60;  // fixed-point iterations for the t = 0 regulator
+
+template <typename R>
+__global__ void potentials_kernel(const double* __restrict__ part, int nchunk, int M, FunctionalDev fn,
+                                  const double* __restrict__ vext, const double* __restrict__ dext, double* lam,
+                                  int init_lam, double* rho, double* nu, double* Uo, double* delta, R* W, cx<R>* D) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  double r = 0.0, nr = 0.0, ni = 0.0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double* p = part + int64_t(c) * 3 * M;
+    r += p[s];
+    nr += p[M + s];
+    ni += p[2 * M + s];
+  }
+  const double ve = vext[s];
+  double l;
+  if (init_lam) {
+    // Regulator frozen at its t = 0 value: fixed point of U -> Lambda_c -> U.
+    double U = 0.0, dr, di;
+    for (int it = 0; it < kRegulatorIters; ++it) {
+      l = regulator(fn.mu - U - ve, fn.ec);
+      site_potentials(fn, r, nr, ni, l, U, dr, di);
+    }
+    l = regulator(fn.mu - U - ve, fn.ec);
+    lam[s] = l;
+  } else {
+    l = lam[s];
+  }
+  double U, dr, di;
+  site_potentials(fn, r, nr, ni, l, U, dr, di);
+  rho[s] = r;
+  nu[2 * s] = nr;
+  nu[2 * s + 1] = ni;
+  Uo[s] = U;
+  delta[2 * s] = dr;
+  delta[2 * s + 1] = di;
+  W[s] = R(U + ve - fn.mu);
+  cx<R> d;
+  d.x = R(dr + dext[2 * s]);
+  d.y = R(di + dext[2 * s + 1]);
+  D[s] = d;
+}
+
+template <typename R>
+cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
+                              const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
+                              double* delta, R* W, cx<R>* D, cudaStream_t s) {
+  potentials_kernel<R><<<(M + 127) / 128, 128, 0, s>>>(part, nchunk, M, fn, vext, dext, lam, init_lam, rho, nu, U,
+                                                       delta, W, D);
+  return cudaGetLastError();
+}
+template cudaError_t launch_potentials<float>(const double*, int, int, FunctionalDev, const double*, const double*,
+                                              double*, int, double*, double*, double*, double*, float*, float2*,
+                                              cudaStream_t);
+template cudaError_t launch_potentials<double>(const double*, int, int, FunctionalDev, const double*, const double*,
+                                               double*, int, double*, double*, double*, double*, double*, double2*,
+                                               cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Energy (Sec. 3.3, A = 1): one block, fixed-order tree sums in double.
+// out8 = e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) energy_kernel(int M, int64_t nstates, FunctionalDev fn,
+                                                      const double* rho_s, const double* nu, const double* delta,
+                                                      const double* vext, const double* dext, const double* ekin2,
+                                                      const double* wm, const double* wp, double dV, double* out8) {
+  __shared__ double sh[6][32];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t n = threadIdx.x; n < nstates; n += blockDim.x)
+    acc[0] += 2.0 * (wm[n] * ekin2[2 * n + 1] + wp[n] * ekin2[2 * n]);  // <v|-lap|v> = 2 <v|T|v>
+  for (int s = threadIdx.x; s < M; s += blockDim.x) {
+    const double rho = 2.0 * rho_s[s];
+    if (fn.kind == 0) acc[1] += 0.6 * fn.B * rho * fermi_energy(rho) * dV;
+    acc[2] += -(delta[2 * s] * nu[2 * s] + delta[2 * s + 1] * nu[2 * s + 1]) * dV;
+    acc[3] += vext[s] * rho * dV;
+    acc[4] += -2.0 * (dext[2 * s] * nu[2 * s] + dext[2 * s + 1] * nu[2 * s + 1]) * dV;
+    acc[5] += rho * dV;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[k][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6];
+    for (int k = 0; k < 6; ++k) {
+      t[k] = 0.0;
+      for (int i = 0; i < int(blockDim.x >> 5); ++i) t[k] += sh[k][i];
+    }
+    out8[0] = t[0];
+    out8[1] = t[1];
+    out8[2] = t[2];
+    out8[3] = t[3];
+    out8[4] = t[4];
+    out8[5] = t[0] + t[1] + t[2] + t[3] + t[4];
+    out8[6] = t[5];
+  }
+}
+
+cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
+                          const double* delta, const double* vext, const double* dext, const double* ekin2,
+                          const double* wm, const double* wp, double dV, double* out8, cudaStream_t s) {
+  energy_kernel<<<1, 1024, 0, s>>>(M, nstates, fn, rho, nu, delta, vext, dext, ekin2, wm, wp, dV, out8);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Conversions at the boundary (complex double <-> working precision).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void narrow_kernel(const double* __restrict__ src, cx<R>* __restrict__ dst, int64_t n, int* err) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = src[2 * i], b = src[2 * i + 1];
+  if (!isfinite(a) || !isfinite(b)) atomicOr(err, 2);
+  cx<R> c;
+  c.x = R(a);
+  c.y = R(b);
+  dst[i] = c;
+}
+template <typename R>
+__global__ void widen_kernel(const cx<R>* __restrict__ src, double* __restrict__ dst, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const cx<R> c = src[i];
+  dst[2 * i] = double(c.x);
+  dst[2 * i + 1] = double(c.y);
+}
+template <typename R>
+__global__ void to_real_kernel(const double* __restrict__ src, R* __restrict__ dst, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = R(src[i]);
+}
+
+template <typename R>
+cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t n, int* err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  narrow_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n, err);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  widen_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_to_real(const double* src, R* dst, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  to_real_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_narrow<float>(const double*, float2*, int64_t, int*, cudaStream_t);
+template cudaError_t launch_narrow<double>(const double*, double2*, int64_t, int*, cudaStream_t);
+template cudaError_t launch_widen<float>(const float2*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_widen<double>(const double2*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_to_real<float>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_to_real<double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace wslda

@@ -1,0 +1,5 @@
+// Compiled lattice shapes, complex float (mixed precision), 18^3 - 24^3 boxes.
+#include "internal.cuh"
+WSLDA_INSTANCE(float, 18, 18, 18, 1, 224, 1, 1, 1)
+WSLDA_INSTANCE(float, 20, 20, 20, 2, 416, 1, 1, 1)
+WSLDA_INSTANCE(float, 24, 24, 24, 2, 288, 1, 1, 1)

@@ -1,0 +1,118 @@
+// Internal declarations shared by the host runtime and the kernel instances.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "stage.cuh"
+
+namespace wslda {
+
+using LaunchFn = cudaError_t (*)(const void* args, int nstates, cudaStream_t s);
+
+// One compiled lattice shape / precision: launchers for every stage mode.
+struct KernelSet {
+  int prec;  // 0 = double, 1 = float (mixed)
+  int nx, ny, nz;
+  int cs, bt, tx, ty, tz;
+  size_t smem;
+  LaunchFn launch[NMODES];
+  const void* fn[NMODES];
+};
+
+std::vector<KernelSet>& registry();
+
+struct Registrar {
+  explicit Registrar(const KernelSet& k) { registry().push_back(k); }
+};
+
+template <class G, int MODE>
+cudaError_t launch_stage(const void* args, int nstates, cudaStream_t s) {
+  auto kern = stage_kernel<G, MODE>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::smem_bytes));
+    if (e != cudaSuccess) return e;
+    if (G::CS > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    configured = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(nstates) * G::CS);
+  cfg.blockDim = dim3(G::BT);
+  cfg.dynamicSmemBytes = G::smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = G::CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, *static_cast<const StageArgs<typename G::R>*>(args));
+}
+
+template <class G>
+KernelSet make_set() {
+  KernelSet k;
+  k.prec = sizeof(typename G::R) == 4 ? 1 : 0;
+  k.nx = G::NX; k.ny = G::NY; k.nz = G::NZ;
+  k.cs = G::CS; k.bt = G::BT; k.tx = G::TX; k.ty = G::TY; k.tz = G::TZ;
+  k.smem = G::smem_bytes;
+  k.launch[MODE_X] = launch_stage<G, MODE_X>;
+  k.launch[MODE_Y] = launch_stage<G, MODE_Y>;
+  k.launch[MODE_F] = launch_stage<G, MODE_F>;
+  k.launch[MODE_HORNER] = launch_stage<G, MODE_HORNER>;
+  k.launch[MODE_EKIN] = launch_stage<G, MODE_EKIN>;
+  k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X>;
+  k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y>;
+  k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F>;
+  k.fn[MODE_HORNER] = (const void*)stage_kernel<G, MODE_HORNER>;
+  k.fn[MODE_EKIN] = (const void*)stage_kernel<G, MODE_EKIN>;
+  return k;
+}
+
+#define WSLDA_CAT2(a, b) a##b
+#define WSLDA_CAT(a, b) WSLDA_CAT2(a, b)
+// WSLDA_INSTANCE(real type, NX, NY, NZ, cluster size, threads, lanes per x/y/z pencil)
+#define WSLDA_INSTANCE(R, NX, NY, NZ, CS, BT, TX, TY, TZ)                                   \
+  static ::wslda::Registrar WSLDA_CAT(wslda_reg_, __COUNTER__)(                            \
+      ::wslda::make_set<::wslda::Geometry<R, NX, NY, NZ, CS, BT, TX, TY, TZ>>());
+
+// ---------------------------------------------------------------------------
+// Site-major kernels (densities.cu)
+// ---------------------------------------------------------------------------
+struct FunctionalDev {
+  int kind;  // 0 slda(A=1), 1 bdg
+  double B, C, inv_4pi_a, mu, ec, rho_floor;
+};
+
+// Partial sums over chunks of states: part[c][0..2][M] = rho, Re nu, Im nu.
+template <typename R>
+cudaError_t launch_density_partial(const cx<R>* phi, const R* wm, const R* wp, int64_t nstates, int M, int nchunk,
+                                   int64_t chunk, double* part, cudaStream_t s);
+
+// Sum the chunk partials, build (U, Delta) with the frozen regulator lam
+// (or first compute lam by the t = 0 fixed point when init_lam), and write
+// the H fields in precision R.
+template <typename R>
+cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
+                              const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
+                              double* delta, R* W, cx<R>* D, cudaStream_t s);
+
+// Energy terms (Sec. 3.3) from the site fields and per-state kinetic values.
+cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
+                          const double* delta, const double* vext, const double* dext, const double* ekin2,
+                          const double* wm, const double* wp, double dV, double* out8, cudaStream_t s);
+
+template <typename R>
+cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t ncomplex, int* err, cudaStream_t s);
+template <typename R>
+cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t ncomplex, cudaStream_t s);
+template <typename R>
+cudaError_t launch_to_real(const double* src, R* dst, int64_t n, cudaStream_t s);
+
+}  // namespace wslda

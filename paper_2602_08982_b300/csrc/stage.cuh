@@ -1,0 +1,351 @@
+// Fused per-state kernels of the TDSLDA step.
+//
+// One thread-block cluster of CS CTAs owns one quasiparticle state (u, v).
+// CTA `rank` keeps the x-slab [rank*P, (rank+1)*P) of both components in
+// shared memory (P = NX / CS), rows padded to an odd pitch so that per-thread
+// z-pencils are bank-conflict free. The kinetic term T phi = -1/2 lap phi is a
+// 3D FFT (Eq. derivative-spectral, Nyquist kept) done as
+//   z-forward, y-forward   (local pencils)
+//   x-forward, * k^2/2, x-inverse   (pencils gathered across the cluster
+//                                     through distributed shared memory)
+//   y-inverse, z-inverse   (local)
+// and the result stays on chip for the pointwise epilogue of the mode:
+//   MODE_X   f(phi) = -i[H - <H>_n] phi (Eq. ABM-f), AB4 predictor and the
+//            AM5 partial sum (Alg. 2 step 1), normalisation of the predictor
+//            (Alg. 2 step 2). Reads phi, f_{k-2..k-4}; writes f_{k-1},
+//            phi_p (over phi) and the partial sum c (over f_{k-4}).
+//   MODE_Y   f(phi_p), corrector completion c + 251/720 dt f (Alg. 2 step 4),
+//            normalisation (Alg. 2 step 8). Reads phi_p and c; writes phi.
+//   MODE_F   f(phi) into a separate buffer (start-up history, diagnostics).
+//   MODE_HORNER  out = base + coef [H - E_n] in (one Horner step of the
+//            Taylor series of Eq. Taylor-exp); E_n = <in|H|in> is computed and
+//            stored when requested, else read; optional normalisation.
+//   MODE_EKIN    per-state <u|T|u>, <v|T|v> for the kinetic energy.
+// Per-state reductions (<H>_n, norms) are summed per thread in the working
+// precision, then across threads and CTAs in double in a fixed order, so all
+// CTAs of the cluster obtain bit-identical values.
+#pragma once
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace wslda {
+namespace cg = cooperative_groups;
+
+enum Mode : int { MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, NMODES = 5 };
+
+template <typename R>
+struct StageArgs {
+  cx<R>* phi;        // X, Y: phi slot; F, HORNER, EKIN: input states
+  cx<R>* h0;         // X: receives f_{k-1};            F: output f;  HORNER: output
+  const cx<R>* h1;   // X: f_{k-2}                                   HORNER: base
+  const cx<R>* h2;   // X: f_{k-3}
+  cx<R>* h3;         // X: f_{k-4} in, c out;  Y: c in
+  const R* W;        // [M] U + V_ext - mu
+  const cx<R>* D;    // [M] Delta + Delta_ext
+  const R* ktab;     // [NX+NY+NZ] per-slot k_d^2 * 0.5 / M
+  const cx<R>* tw;   // [NX+NY+NZ] W_N^k per axis (used where a pencil spans lanes)
+  double* E;         // HORNER: per-state shift (written when compute_e)
+  double* out2;      // EKIN: [n][2] <u|T|u>, <v|T|v>
+  int* err;          // error word: bit 0 non-finite norm
+  double dt;
+  double dV;
+  double coef_re, coef_im;  // HORNER coefficient
+  int compute_e;
+  int normalize;
+  int nstates;
+};
+
+// Integrator coefficients of Eqs. AB4 and AM5.
+struct ABM {
+  static constexpr double b0 = 55.0 / 24.0, b1 = -59.0 / 24.0, b2 = 37.0 / 24.0, b3 = -9.0 / 24.0;
+  static constexpr double a0 = 251.0 / 720.0, a1 = 646.0 / 720.0, a2 = -264.0 / 720.0, a3 = 106.0 / 720.0,
+                          a4 = -19.0 / 720.0;
+};
+
+template <typename R_, int NX_, int NY_, int NZ_, int CS_, int BT_, int TX_, int TY_, int TZ_>
+struct Geometry {
+  using R = R_;
+  using C = cx<R_>;
+  static constexpr int NX = NX_, NY = NY_, NZ = NZ_, CS = CS_, BT = BT_;
+  static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
+  static constexpr int P = NX / CS;         // x-planes per CTA
+  static constexpr int ZP = NZ + 1;         // odd row pitch (N even)
+  static constexpr int SLAB = P * NY * ZP;  // complex elements per component
+  static constexpr int NS = P * NY * NZ;    // sites per CTA
+  static constexpr int M = NX * NY * NZ;
+  static constexpr int NW = BT / 32;
+  static constexpr int NCOL = 2 * NY * NZ / CS;  // x-pencils per CTA
+  static constexpr size_t smem_bytes =
+      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + size_t(NW + 16) * sizeof(double);
+  static_assert(NX % CS == 0, "cluster must split x evenly");
+  static_assert((2 * NY * NZ) % CS == 0, "columns must split evenly");
+  static_assert(BT % 32 == 0 && BT % TX == 0 && BT % TY == 0 && BT % TZ == 0, "block");
+  static_assert(CS <= 16, "cluster size");
+};
+
+// Sum over the threads of the CTA and the CTAs of the cluster (double, fixed order).
+template <class G>
+__device__ __forceinline__ double cluster_sum(double v, double* red, cg::cluster_group& cl) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < G::NW; ++i) s += red[i];
+    double* dst = cl.map_shared_rank(red + G::NW, 0);
+    dst[cl.block_rank()] = s;
+  }
+  cl.sync();
+  const double* src = cl.map_shared_rank(red + G::NW, 0);
+  double tot = 0.0;
+  for (int r = 0; r < G::CS; ++r) tot += src[r];
+  cl.sync();
+  return tot;
+}
+
+// Local pencils along z (rows) or y, forward or inverse, over both components.
+template <class G, int AXIS, bool INV>
+__device__ __forceinline__ void local_pass(typename G::C* buf, const typename G::C* tw) {
+  using C = typename G::C;
+  constexpr int N = AXIS == 2 ? G::NZ : G::NY;
+  constexpr int T = AXIS == 2 ? G::TZ : G::TY;
+  constexpr int N1 = N / T;
+  constexpr int NPEN = AXIS == 2 ? 2 * G::P * G::NY : 2 * G::P * G::NZ;
+  constexpr int PER = G::BT / T;
+  constexpr int ITERS = (NPEN + PER - 1) / PER;
+  const int j = threadIdx.x % T;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int p = it * PER + threadIdx.x / T;
+    const bool act = p < NPEN;
+    const int pp = act ? p : 0;
+    C* base;
+    int stride;
+    if constexpr (AXIS == 2) {
+      const int comp = pp / (G::P * G::NY), row = pp % (G::P * G::NY);
+      base = buf + comp * G::SLAB + row * G::ZP;
+      stride = 1;
+    } else {
+      const int comp = pp / (G::P * G::NZ), rem = pp % (G::P * G::NZ);
+      const int xl = rem / G::NZ, z = rem % G::NZ;
+      base = buf + comp * G::SLAB + xl * G::NY * G::ZP + z;
+      stride = G::ZP;
+    }
+    C x[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) x[m] = base[(j + T * m) * stride];
+    if constexpr (INV) pencil_inv<N, T>(x, j, tw);
+    else pencil_fwd<N, T>(x, j, tw);
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) base[(j + T * m) * stride] = x[m];
+    }
+  }
+}
+
+// x pencils across the cluster: forward, multiply by the kinetic symbol, inverse.
+template <class G>
+__device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* ktab, const typename G::C* tw,
+                                       cg::cluster_group& cl) {
+  using C = typename G::C;
+  using R = typename G::R;
+  constexpr int T = G::TX, N = G::NX, N1 = N / T;
+  constexpr int PER = G::BT / T;
+  constexpr int ITERS = (G::NCOL + PER - 1) / PER;
+  const int j = threadIdx.x % T;
+  const int rank = cl.block_rank();
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int q = rank * G::NCOL + it * PER + threadIdx.x / T;
+    const bool act = (it * PER + threadIdx.x / T) < G::NCOL;
+    const int qq = act ? q : rank * G::NCOL;
+    const int comp = qq / (G::NY * G::NZ), yz = qq % (G::NY * G::NZ);
+    const int y = yz / G::NZ, z = yz % G::NZ;
+    const int off = comp * G::SLAB + y * G::ZP + z;
+    C x[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const int xg = j + T * m;
+      const C* src = cl.map_shared_rank(buf, xg / G::P);
+      x[m] = src[off + (xg % G::P) * G::NY * G::ZP];
+    }
+    pencil_fwd<N, T>(x, j, tw);
+    const R kyz = ktab[G::NX + y] + ktab[G::NX + G::NY + z];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) x[m] = scl(x[m], ktab[j + T * m] + kyz);
+    pencil_inv<N, T>(x, j, tw);
+    // a column is read and written only by its own lane group: no barrier here
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const int xg = j + T * m;
+        C* dst = cl.map_shared_rank(buf, xg / G::P);
+        dst[off + (xg % G::P) * G::NY * G::ZP] = x[m];
+      }
+    }
+  }
+}
+
+template <class G, int MODE>
+__global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G::R> a) {
+  using C = typename G::C;
+  using R = typename G::R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* buf = reinterpret_cast<C*>(smem);
+  R* ktab = reinterpret_cast<R*>(buf + 2 * G::SLAB);
+  C* tws = reinterpret_cast<C*>(ktab + (G::NX + G::NY + G::NZ));
+  double* red = reinterpret_cast<double*>(tws + (G::NX + G::NY + G::NZ));
+  // keep the reduction scratch 8-byte aligned
+  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = cl.block_rank();
+  const int n = blockIdx.x / G::CS;
+  const int tid = threadIdx.x;
+  const size_t sbase = size_t(n) * 2 * G::M;
+  const int gs0 = rank * G::NS;  // first global site of this slab
+
+  for (int i = tid; i < G::NX + G::NY + G::NZ; i += G::BT) { ktab[i] = a.ktab[i]; tws[i] = a.tw[i]; }
+  const C* twx = tws;
+  const C* twy = tws + G::NX;
+  const C* twz = tws + G::NX + G::NY;
+
+  const C* in = a.phi + sbase;
+  // load the slab of both components
+  for (int i = tid; i < 2 * G::NS; i += G::BT) {
+    const int comp = i / G::NS, s = i % G::NS;
+    buf[comp * G::SLAB + (s / G::NZ) * G::ZP + (s % G::NZ)] = in[comp * G::M + gs0 + s];
+  }
+  __syncthreads();
+  local_pass<G, 2, false>(buf, twz);
+  __syncthreads();
+  local_pass<G, 1, false>(buf, twy);
+  cl.sync();
+  x_pass<G>(buf, ktab, twx, cl);
+  cl.sync();
+  local_pass<G, 1, true>(buf, twy);
+  __syncthreads();
+  local_pass<G, 2, true>(buf, twz);
+  __syncthreads();
+  // buf now holds T phi = -1/2 lap phi of this slab (natural order).
+
+  const C* inu = in;
+  const C* inv = in + G::M;
+  auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
+
+  if constexpr (MODE == MODE_EKIN) {
+    R eu = 0, ev = 0;
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const C u = inu[gs0 + s], v = inv[gs0 + s];
+      const C tu = buf[sidx(s)], tv = buf[G::SLAB + sidx(s)];
+      eu += u.x * tu.x + u.y * tu.y;
+      ev += v.x * tv.x + v.y * tv.y;
+    }
+    const double su = cluster_sum<G>(double(eu), red, cl);
+    const double sv = cluster_sum<G>(double(ev), red, cl);
+    if (rank == 0 && tid == 0) { a.out2[2 * n] = su * a.dV; a.out2[2 * n + 1] = sv * a.dV; }
+    return;
+  } else {
+    // H phi = [T u + W u + D v, D^* u - T v - W v] (Eq. dpsidt-Hpsi, A = 1)
+    double En = 0.0;
+    const bool need_e = (MODE != MODE_HORNER) || a.compute_e;
+    if (need_e) {
+      R ep = 0, ec = 0;  // compensated partial sum
+      for (int s = tid; s < G::NS; s += G::BT) {
+        const int g = gs0 + s;
+        const C u = inu[g], v = inv[g];
+        const R w = a.W[g];
+        const C d = a.D[g];
+        const C hu = add(add(buf[sidx(s)], scl(u, w)), mul(d, v));
+        const C hv = sub(sub(mulc(u, d), buf[G::SLAB + sidx(s)]), scl(v, w));
+        buf[sidx(s)] = hu;
+        buf[G::SLAB + sidx(s)] = hv;
+        const R t = (u.x * hu.x + u.y * hu.y + v.x * hv.x + v.y * hv.y) - ec;
+        const R nsum = ep + t;
+        ec = (nsum - ep) - t;
+        ep = nsum;
+      }
+      En = cluster_sum<G>(double(ep), red, cl) * a.dV;
+      if (MODE == MODE_HORNER && rank == 0 && tid == 0) a.E[n] = En;
+    } else {
+      En = a.E[n];
+      for (int s = tid; s < G::NS; s += G::BT) {
+        const int g = gs0 + s;
+        const C u = inu[g], v = inv[g];
+        const R w = a.W[g];
+        const C d = a.D[g];
+        buf[sidx(s)] = add(add(buf[sidx(s)], scl(u, w)), mul(d, v));
+        buf[G::SLAB + sidx(s)] = sub(sub(mulc(u, d), buf[G::SLAB + sidx(s)]), scl(v, w));
+      }
+    }
+    const R Er = R(En);
+    // buf now holds H phi; each thread touches only its own sites below.
+    if constexpr (MODE == MODE_F) {
+      C* out = a.h0 + sbase;
+      for (int s = tid; s < G::NS; s += G::BT) {
+        const int g = gs0 + s;
+        // -i (H phi - E phi)
+        out[g] = mul_mi(sub(buf[sidx(s)], scl(inu[g], Er)));
+        out[G::M + g] = mul_mi(sub(buf[G::SLAB + sidx(s)], scl(inv[g], Er)));
+      }
+      return;
+    } else {
+      R np = 0, nc = 0;  // compensated norm partial
+      const bool norm_out = (MODE == MODE_X || MODE == MODE_Y) || a.normalize;
+      C* dst = MODE == MODE_HORNER ? a.h0 + sbase : a.phi + sbase;
+      for (int comp = 0; comp < 2; ++comp) {
+        for (int s = tid; s < G::NS; s += G::BT) {
+          const int g = comp * G::M + gs0 + s;
+          const int b = comp * G::SLAB + sidx(s);
+          const C ph = in[g];
+          const C fv = mul_mi(sub(buf[b], scl(ph, Er)));
+          C res;
+          if constexpr (MODE == MODE_X) {
+            const C f1 = a.h1[sbase + g], f2 = a.h2[sbase + g], f3 = a.h3[sbase + g];
+            const R dt = R(a.dt);
+            const C pred = add(ph, scl(add(add(scl(fv, R(ABM::b0)), scl(f1, R(ABM::b1))),
+                                           add(scl(f2, R(ABM::b2)), scl(f3, R(ABM::b3)))), dt));
+            const C corr = add(ph, scl(add(add(scl(fv, R(ABM::a1)), scl(f1, R(ABM::a2))),
+                                           add(scl(f2, R(ABM::a3)), scl(f3, R(ABM::a4)))), dt));
+            a.h0[sbase + g] = fv;
+            a.h3[sbase + g] = corr;
+            res = pred;
+          } else if constexpr (MODE == MODE_Y) {
+            const C c = a.h3[sbase + g];
+            res = add(c, scl(fv, R(ABM::a0 * a.dt)));
+          } else {  // HORNER: base + coef * (-i)^{-1}... out = base + coef (H - E) in
+            const C hv = sub(buf[b], scl(ph, Er));
+            const C cf = mk<C>(R(a.coef_re), R(a.coef_im));
+            res = add(a.h1[sbase + g], mul(cf, hv));
+          }
+          if (norm_out) {
+            buf[b] = res;
+            const R t = (res.x * res.x + res.y * res.y) - nc;
+            const R nsum = np + t;
+            nc = (nsum - np) - t;
+            np = nsum;
+          } else {
+            dst[g] = res;
+          }
+        }
+      }
+      if (norm_out) {
+        const double nrm = cluster_sum<G>(double(np), red, cl) * a.dV;
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+          if (tid == 0) atomicOr(a.err, 1);
+        }
+        const R sc = R(1.0 / sqrt(nrm));
+        for (int comp = 0; comp < 2; ++comp)
+          for (int s = tid; s < G::NS; s += G::BT)
+            dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
+      }
+    }
+  }
+}
+
+}  // namespace wslda

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libwslda_td.so (include/wslda_td.h).
+
+Argument marshalling only: every step of the TDSLDA path runs in the CUDA
+library. Methods of `Context` carry the names of the C calls without the
+`wslda_` prefix. Arrays may be numpy arrays (host) or torch CUDA tensors
+(device, borrowed for the duration of the call). The library must have been
+built (`python -m paper_2602_08982_b300.build`); importing this module without
+it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libwslda_td.so")
+
+FP64, MIXED = 0, 1
+SLDA_A1, BDG = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN", 5: "EDRIFT", 6: "ETIMEOUT", 7: "ESTATE",
+          8: "EUNSUPPORTED"}
+KERNEL_KINDS = {"stage_x": 0, "stage_y": 1, "density": 2, "potentials": 3, "aux": 4}
+
+
+class WsldaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Lattice(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+                ("dx", ct.c_double), ("dy", ct.c_double), ("dz", ct.c_double)]
+
+
+class Functional(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("B", ct.c_double), ("C", ct.c_double), ("inv_4pi_a", ct.c_double),
+                ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double)]
+
+
+class Energy(ct.Structure):
+    _fields_ = [(k, ct.c_double) for k in ("e_kin", "e_pot", "e_pair", "e_ext", "e_pair_ext", "e_total", "n_part")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2602_08982_b300.build`")
+    lib = ct.CDLL(LIB_PATH)
+    P, I, D, I64 = ct.c_void_p, ct.c_int, ct.c_double, ct.c_int64
+    DP = ct.POINTER(ct.c_double)
+    sig = {
+        "wslda_create": (I, [I, P, ct.POINTER(P)]),
+        "wslda_destroy": (None, [P]),
+        "wslda_last_error": (ct.c_char_p, [P]),
+        "wslda_lattice_supported": (I, [I, I, I, I]),
+        "wslda_add_box": (I, [P, ct.POINTER(Lattice), ct.POINTER(Functional), I64]),
+        "wslda_set_vext": (I, [P, I, P, I]),
+        "wslda_set_dext": (I, [P, I, P, I]),
+        "wslda_load_states": (I, [P, I, P, P, P, I]),
+        "wslda_start": (I, [P, I, D]),
+        "wslda_step": (I, [P, D, I]),
+        "wslda_get_states": (I, [P, I, P, I]),
+        "wslda_get_densities": (I, [P, I, P, P, P, P]),
+        "wslda_get_fields": (I, [P, I, P, P]),
+        "wslda_get_energy": (I, [P, I, ct.POINTER(Energy)]),
+        "wslda_eval_f": (I, [P, I, P]),
+        "wslda_save": (I, [P, ct.c_char_p]),
+        "wslda_load": (I, [P, ct.c_char_p]),
+        "wslda_get_time": (I, [P, DP, ct.POINTER(I64)]),
+        "wslda_memory_bytes": (I64, [P]),
+        "wslda_set_profiling": (I, [P, I]),
+        "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def lattice_supported(precision: int, nx: int, ny: int, nz: int) -> bool:
+    return bool(lib.wslda_lattice_supported(precision, nx, ny, nz))
+
+
+def _ptr(a, dtype, on_device: bool):
+    """(pointer, keep-alive) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ct.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ct.c_void_p), arr
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Context:
+    def __init__(self, precision: int = MIXED, stream: int | None = None):
+        self._h = ct.c_void_p()
+        st = lib.wslda_create(precision, ct.c_void_p(stream or 0), ct.byref(self._h))
+        if st:
+            raise WsldaError(st, "wslda_create failed")
+        self.precision = precision
+        self.boxes: list[tuple] = []
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st: int):
+        if st:
+            raise WsldaError(st, lib.wslda_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib.wslda_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ ABI
+    def add_box(self, shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, C=-1.0, inv_4pi_a=0.0, mu=0.0,
+                ec=-1.0, rho_floor=1e-12, nstates: int) -> int:
+        lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
+        fn = Functional(int(kind), float(B), float(C), float(inv_4pi_a), float(mu), float(ec), float(rho_floor))
+        r = lib.wslda_add_box(self._h, ct.byref(lat), ct.byref(fn), int(nstates))
+        if r < 0:
+            self._check(-r)
+        self.boxes.append((tuple(int(v) for v in shape), int(nstates)))
+        return r
+
+    def _M(self, box):
+        s = self.boxes[box][0]
+        return s[0] * s[1] * s[2]
+
+    def set_vext(self, box: int, vext):
+        p, keep = _ptr(vext, np.float64, _is_device(vext))
+        self._check(lib.wslda_set_vext(self._h, box, p, int(_is_device(vext))))
+
+    def set_dext(self, box: int, dext):
+        if not _is_device(dext):
+            dext = np.ascontiguousarray(dext, dtype=np.complex128)
+        p, keep = _ptr(dext, np.complex128, _is_device(dext))
+        self._check(lib.wslda_set_dext(self._h, box, p, int(_is_device(dext))))
+
+    def load_states(self, box: int, uv, w_minus=None, w_plus=None):
+        dev = _is_device(uv)
+        if not dev:
+            uv = np.ascontiguousarray(uv, dtype=np.complex128)
+        p, keep = _ptr(uv, np.complex128, dev)
+        pm, km = _ptr(w_minus, np.float64, False)
+        pp, kp = _ptr(w_plus, np.float64, False)
+        self._check(lib.wslda_load_states(self._h, box, p, pm, pp, int(dev)))
+
+    def start(self, stationary: bool, dt: float):
+        self._check(lib.wslda_start(self._h, int(bool(stationary)), float(dt)))
+
+    def step(self, dt: float, nsteps: int = 1):
+        self._check(lib.wslda_step(self._h, float(dt), int(nsteps)))
+
+    def get_states(self, box: int, out=None):
+        n = self.boxes[box][1]
+        if out is None:
+            out = np.empty((n, 2, self._M(box)), dtype=np.complex128)
+        p, keep = _ptr(out, np.complex128, _is_device(out))
+        self._check(lib.wslda_get_states(self._h, box, p, int(_is_device(out))))
+        return out
+
+    def get_densities(self, box: int, tau: bool = False, current: bool = False):
+        M = self._M(box)
+        rho = np.empty(M)
+        nu = np.empty(M, dtype=np.complex128)
+        t = np.empty(M) if tau else None
+        j = np.empty((3, M)) if current else None
+        self._check(lib.wslda_get_densities(self._h, box, rho.ctypes.data_as(ct.c_void_p),
+                                            nu.ctypes.data_as(ct.c_void_p),
+                                            t.ctypes.data_as(ct.c_void_p) if tau else None,
+                                            j.ctypes.data_as(ct.c_void_p) if current else None))
+        return (rho, nu) if not (tau or current) else (rho, nu, t, j)
+
+    def get_fields(self, box: int):
+        M = self._M(box)
+        U = np.empty(M)
+        delta = np.empty(M, dtype=np.complex128)
+        self._check(lib.wslda_get_fields(self._h, box, U.ctypes.data_as(ct.c_void_p),
+                                         delta.ctypes.data_as(ct.c_void_p)))
+        return U, delta
+
+    def get_energy(self, box: int) -> dict:
+        e = Energy()
+        self._check(lib.wslda_get_energy(self._h, box, ct.byref(e)))
+        return {k: getattr(e, k) for k, _ in Energy._fields_}
+
+    def eval_f(self, box: int):
+        n = self.boxes[box][1]
+        out = np.empty((n, 2, self._M(box)), dtype=np.complex128)
+        self._check(lib.wslda_eval_f(self._h, box, out.ctypes.data_as(ct.c_void_p)))
+        return out
+
+    def save(self, path: str):
+        self._check(lib.wslda_save(self._h, path.encode()))
+
+    def load(self, path: str):
+        self._check(lib.wslda_load(self._h, path.encode()))
+
+    def get_time(self):
+        t = ct.c_double()
+        s = ct.c_int64()
+        self._check(lib.wslda_get_time(self._h, ct.byref(t), ct.byref(s)))
+        return t.value, s.value
+
+    def memory_bytes(self) -> int:
+        return int(lib.wslda_memory_bytes(self._h))
+
+    def set_profiling(self, enable: bool):
+        self._check(lib.wslda_set_profiling(self._h, int(bool(enable))))
+
+    def get_kernel_time(self, kind) -> tuple[float, int]:
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        ms = ct.c_double()
+        n = ct.c_int64()
+        self._check(lib.wslda_get_kernel_time(self._h, k, ct.byref(ms), ct.byref(n)))
+        return ms.value, n.value
