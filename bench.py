@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the TDSLDA step (AB4AM5, Alg. 2) on B300.
+
+Metric: state-site updates per second = states x lattice sites x steps / time,
+one update being one quasiparticle state at one lattice site advanced by one
+full predictor + corrector step. The workload is a 32^3 periodic lattice in a
+harmonic trap V = 1/2 w^2 r^2 (w = 0.05) with 32768 quasiparticle states.
+
+Default run (N = 1): the mixed-precision step (complex float states and FFTs,
+double reductions) is timed with CUDA events on the library's stream over K
+steps after W warm-up steps; the plain FP64 step on the same states is timed
+the same way and reported beside it, with the relative density difference
+between the two. Per-kernel CUDA events give the stage-X kernel's duration for
+the roofline. The end-to-end number goes through the public API with pinned
+host buffers: load_states (host -> device), start, K steps each followed by a
+density read (device -> host) and a final get_states (device -> host).
+`--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TD step state-site updates/s, mixed FP32 vs plain FP64 at ≤1e-5 rel density err"
+UNIT = "state-site updates/s"
+FALLBACK_HBM_GBS = 6400.0
+FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (SM count x FP64 units x clock)
+RHO_SIGMA = 1.0 / (6 * math.pi ** 2)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--shape", default="32,32,32")
+    p.add_argument("--nstates", type=int, default=32768)
+    p.add_argument("--omega", type=float, default=0.05)
+    p.add_argument("--dt", type=float, default=0.007)
+    p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--stationary", action="store_true",
+                   help="stationary start instead of the Taylor start (short profiling runs)")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "of measured"
+    return FALLBACK_HBM_GBS, "of fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arms
+def make_box(W, prec, shape, nstates, omega, stream):
+    from paper_2602_08982_b300 import inputs
+    u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
+    ctx = W.Context(prec, stream=stream)
+    box = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=nstates)
+    ctx.set_vext(box, inputs.harmonic_trap(shape, omega))
+    return ctx, box, u
+
+
+def stage_x_algorithmic(prec, shape):
+    """Algorithmic traffic / work of one stage-X launch per state-site.
+    Bytes: reads phi, f_{k-2}, f_{k-3}, f_{k-4}; writes f_{k-1}, phi_p, c
+    (7 state passes of two complex numbers). Flops (FP64 path): forward and
+    inverse 3D FFT of both components at 5 M log2 M each, plus the pointwise
+    H, <H>_n, f, predictor, corrector partial, norm and scaling (128)."""
+    M = shape[0] * shape[1] * shape[2]
+    csize = 8 if prec == 1 else 16
+    bytes_per = 7 * 2 * csize
+    flops_per = 2 * 2 * 5 * math.log2(M) + 128
+    return bytes_per, flops_per
+
+
+def run_arm(W, torch, prec, args, shape, rank, world, dev):
+    stream = torch.cuda.current_stream()
+    ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+    ctx.start(args.stationary, args.dt)      # Taylor start: the trapped plane waves are not stationary
+    if args.warmup:
+        ctx.step(args.dt, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctx.set_profiling(True)
+    clocks = ClockSampler(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(args.dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    kt = {k: ctx.get_kernel_time(k) for k in ("stage_x", "stage_y", "density", "potentials")}
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    rho, nu = ctx.get_densities(box)
+    ctx.close()
+    M = shape[0] * shape[1] * shape[2]
+    units = float(args.nstates) * M * args.steps
+    value = world * units / (ms * 1e-3)
+    bx, fx = stage_x_algorithmic(prec, shape)
+    x_ms, x_n = kt["stage_x"]
+    x_avg = x_ms / max(x_n, 1)
+    per_launch = float(args.nstates) * M
+    if prec == 1:
+        peak, which = measured_peaks()
+        achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
+                "peak_source": which, "algorithmic_bytes_per_state_site": bx}
+    else:
+        achieved = fx * per_launch / (x_avg * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation), FP64",
+                "peak_source": "nominal FP64 rate", "algorithmic_flops_per_state_site": fx}
+    launches = sum(kt[k][1] for k in kt)
+    share = {k: kt[k][0] / ms for k in kt}
+    return dict(value=value, ms_per_step=ms / args.steps, roofline=roof, clocks=ck, launches=launches,
+                kernel_ms=kt, kernel_share=share, rho=rho, nu=nu)
+
+
+def run_e2e(W, torch, args, shape, world):
+    """Mixed path end to end through the ABI with pinned host buffers."""
+    stream = torch.cuda.current_stream()
+    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+    M = shape[0] * shape[1] * shape[2]
+    host = torch.empty((args.nstates, 2, M), dtype=torch.complex128, pin_memory=True)
+    host_np = host.numpy()
+    ctx.get_states(box, host_np)      # untimed: the job's input now lives in pinned host memory
+    ctx.close()
+    rho_h = np.empty(M)
+    nu_h = np.empty(M, dtype=np.complex128)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx.load_states(box, host_np)
+    ctx.start(False, args.dt)
+    for _ in range(args.steps):
+        ctx.step(args.dt, 1)
+        r, n = ctx.get_densities(box)
+    ctx.get_states(box, host_np)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ctx.close()
+    if world > 1:
+        t = torch.tensor([sec], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        sec = float(t.item())
+    units = float(args.nstates) * M * args.steps
+    nbytes = host.numel() * 16
+    del host
+    return {"value": world * units / sec, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / args.steps,
+            "d2h_bytes_per_step": (nbytes + args.steps * 24 * M) / args.steps,
+            "includes": "load_states from pinned host, Taylor start, K steps each with a density read, final get_states"}
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_sample(shape, omega, n):
+    """CPU-oracle system for the workload's lattice and trap, with n of its
+    uniform plane-wave states (seeded choice of momenta)."""
+    from oracle import tdslda as o
+    from paper_2602_08982_b300 import inputs
+    lat = o.Lattice(*shape)
+    seed = o.uniform_slda_seed(lat, 0.25, RHO_SIGMA)
+    fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu)
+    r = inputs.uniform01(77, lat.M)
+    idx = np.sort(np.argsort(r)[:n])
+    kx, ky, kz = (lat.kaxis(a) for a in range(3))
+    ix, rem = np.divmod(idx, lat.ny * lat.nz)
+    iy, iz = np.divmod(rem, lat.nz)
+    e = [np.exp(1j * np.outer(k[i], np.arange(nn))) for k, i, nn in ((kx, ix, lat.nx), (ky, iy, lat.ny),
+                                                                      (kz, iz, lat.nz))]
+    pw = np.einsum("ni,nj,nk->nijk", *e).reshape(n, lat.M) / np.sqrt(lat.volume)
+    Uk, Vk, _ = o.bcs_amplitudes(0.5 * (kx[ix] ** 2 + ky[iy] ** 2 + kz[iz] ** 2) - seed.mu_eff, seed.delta)
+    phi = np.stack([Uk[:, None] * pw, Vk[:, None] * pw], axis=1)
+    return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, omega)), phi, lat
+
+
+def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048):
+    """The oracle as it stands, on a bounded sample of the workload: the same
+    lattice and trap with a subset of the uniform plane-wave states, timed over
+    whole ABM steps after a stationary start."""
+    n = 64
+    while True:
+        o, sysm, phi, lat = oracle_sample(shape, omega, n)
+        st = o.start(sysm, phi, dt, stationary=True)
+        t0 = time.perf_counter()
+        st = o.ab4am5_step(sysm, st, dt)
+        one = time.perf_counter() - t0
+        if one * 4 > seconds or n >= max_states:
+            break
+        n = min(max_states, n * 2)
+    k = max(1, int(seconds / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        st = o.ab4am5_step(sysm, st, dt)
+    sec = time.perf_counter() - t0
+    return {"value": n * lat.M * k / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "n": n,
+            "sample": f"{n} of the workload's states on the same {shape[0]}x{shape[1]}x{shape[2]} trap, {k} AB4AM5 "
+                      f"steps after a stationary start, {sec:.1f} s"}
+
+
+def reference_arm(args, shape):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    # each step: one oracle AB4AM5 step over a bounded sample of the states,
+    # sized so that one step takes about a second
+    n = cpu_oracle_rate(shape, args.omega, args.dt, seconds=4.0)["n"]
+    o, sysm, phi, lat = oracle_sample(shape, args.omega, n)
+    st = o.start(sysm, phi, args.dt, stationary=True)
+    for _ in range(args.warmup):
+        st = o.ab4am5_step(sysm, st, args.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = o.ab4am5_step(sysm, st, args.dt)
+    sec = time.perf_counter() - t0
+    value = n * lat.M * args.steps / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(args, shape, "fp64 oracle (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} states of the workload per step, {args.steps} steps, {sec:.1f} s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_config(args, shape, precision):
+    return {"workload": f"TDSLDA AB4AM5 step, {shape[0]}x{shape[1]}x{shape[2]} periodic lattice, harmonic trap "
+                        f"w={args.omega}, {args.nstates} quasiparticle states",
+            "lattice": list(shape), "nstates": args.nstates, "trap_omega": args.omega, "dt": args.dt,
+            "functional": "SLDA (A=1), B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
+            "init": "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start",
+            "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    args = parse()
+    shape = tuple(int(v) for v in args.shape.split(","))
+    if args.impl == "reference":
+        reference_arm(args, shape)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2602_08982_b300 import wslda as W
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds)
+    arms = {}
+    if args.precision in ("both", "mixed"):
+        arms["mixed"] = run_arm(W, torch, W.MIXED, args, shape, rank, world, local)
+    if args.precision in ("both", "fp64"):
+        arms["fp64"] = run_arm(W, torch, W.FP64, args, shape, rank, world, local)
+    e2e = None if args.no_e2e else run_e2e(W, torch, args, shape, world)
+    main_arm = arms.get("mixed") or arms["fp64"]
+    line = {"metric": METRIC, "value": main_arm["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main_arm["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "mixed" in arms else "f64",
+            "data": "synthetic",
+            "config": workload_config(args, shape, "mixed: complex64 states and FFTs, f64 accumulation"
+                                      if "mixed" in arms else "fp64"),
+            "roofline": main_arm["roofline"], "gpu_launches": main_arm["launches"], "clocks": main_arm["clocks"],
+            "kernel_share": main_arm["kernel_share"]}
+    if "fp64" in arms and "mixed" in arms:
+        a = arms["fp64"]
+        line["fp64"] = {"value": a["value"], "ms_per_step": a["ms_per_step"], "roofline": a["roofline"],
+                        "gpu_launches": a["launches"], "clocks": a["clocks"], "kernel_share": a["kernel_share"]}
+        m = arms["mixed"]
+        line["mixed_vs_fp64"] = {
+            "rel_density_err_rho": float(np.abs(m["rho"] - a["rho"]).max() / np.abs(a["rho"]).max()),
+            "rel_density_err_nu": float(np.abs(m["nu"] - a["nu"]).max() / np.abs(a["nu"]).max()),
+            "after_steps": 3 + args.warmup + args.steps}
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

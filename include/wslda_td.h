@@ -157,6 +157,28 @@ wslda_status wslda_get_time(wslda_ctx* ctx, double* t, int64_t* steps);
 /* Device bytes held by the context. */
 int64_t wslda_memory_bytes(const wslda_ctx* ctx);
 
+/* Uniform (plane-wave) BCS solution on the lattice k-set (Sec. 5, "inittype 0";
+ * reduced 2x2 problem of Eq. HpsiEpsi). With u_k, v_k = (U_k, V_k) e^{ik.r}/sqrt(V),
+ * xi_k = k^2/2 - mu_eff, E_k = sqrt(xi_k^2 + Delta^2) over all M lattice k:
+ *  - the number equation (1/V) sum_k V_k^2 = rho_sigma fixes mu_eff = mu - U;
+ *  - kind SLDA_A1: Delta = delta0 is given; 1/g_eff = -(1/V) sum_k 1/(2E_k)
+ *    fixes C through Eq. Creg (C = rho^(1/3)/(1/g_eff + Lambda_c)), then
+ *    U = B eF(rho) - Delta^2/(3 C rho^(2/3)) and mu = U + mu_eff;
+ *  - kind BDG: the gap equation 1/(4 pi a) - Lambda_c = -(1/V) sum_k 1/(2E_k)
+ *    is solved for Delta (first root on a log grid, 1e-6..8), U = 0, mu = mu_eff.
+ * fn supplies kind, B, inv_4pi_a and ec (<= 0: zone-corner cutoff). */
+typedef struct {
+  double mu_eff, delta, mu, U, C, lam, inv_g;
+} wslda_uniform;
+wslda_status wslda_uniform_solve(const wslda_lattice* lat, const wslda_functional* fn, double rho_sigma,
+                                 double delta0, wslda_uniform* out);
+
+/* Fill a box with the positive-energy plane-wave states of a uniform solution
+ * (mu_eff, delta > 0), computed on the device. State i takes the flattened
+ * k index kidx[i] (host int64 [n]) or i when kidx is NULL (then n <= M).
+ * Weights are set to T = 0. Replaces wslda_load_states. */
+wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, double delta, const int64_t* kidx);
+
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
  * the context's stream and its duration is added to the kernel's total.
  * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction,

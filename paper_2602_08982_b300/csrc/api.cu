@@ -623,6 +623,41 @@ wslda_status wslda_load_states(wslda_ctx* c, int box, const double* uv, const do
   return WSLDA_OK;
 }
 
+wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, double delta, const int64_t* kidx) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "fill_uniform_states: bad box");
+  if (c->started) return fail(c, WSLDA_ESTATE, "fill_uniform_states after wslda_start");
+  if (!(delta > 0.0) || !std::isfinite(mu_eff)) return fail(c, WSLDA_EINVAL, "fill_uniform_states: need delta > 0");
+  if (!kidx && b->n > b->M) return fail(c, WSLDA_EINVAL, "more states than lattice momenta");
+  int64_t* kd = nullptr;
+  if (kidx && b->n > 0) {
+    for (int64_t i = 0; i < b->n; ++i)
+      if (kidx[i] < 0 || kidx[i] >= b->M) return fail(c, WSLDA_EINVAL, "k index out of range");
+    CUDA_TRY(c, cudaMalloc(&kd, size_t(b->n) * 8));
+    CUDA_TRY(c, cudaMemcpyAsync(kd, kidx, size_t(b->n) * 8, cudaMemcpyHostToDevice, c->stream));
+  }
+  cudaError_t e = launch_fill_plane_waves(b->slot[b->iphi], c->prec == WSLDA_MIXED, b->lat, mu_eff, delta, kd, b->n,
+                                          c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (kd) cudaFree(kd);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(c, WSLDA_ECUDA, std::string("fill_uniform_states: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
+  CUDA_TRY(c, cudaMemcpyAsync(b->wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(b->wp, wp.data(), wp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == WSLDA_MIXED) {
+    CUDA_TRY(c, launch_to_real<float>(b->wm, static_cast<float*>(b->wm_r), int64_t(wm.size()), c->stream));
+    CUDA_TRY(c, launch_to_real<float>(b->wp, static_cast<float*>(b->wp_r), int64_t(wp.size()), c->stream));
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(b->wm_r, b->wm, wm.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(b->wp_r, b->wp, wp.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  b->loaded = true;
+  return WSLDA_OK;
+}
+
 wslda_status wslda_start(wslda_ctx* c, int stationary, double dt) {
   CHECK_CTX(c);
   if (!(dt != 0.0) || !std::isfinite(dt)) return fail(c, WSLDA_EINVAL, "dt must be finite and non-zero");

@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "../../include/wslda_td.h"
 #include "stage.cuh"
 
 namespace wslda {
@@ -107,6 +108,10 @@ cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalD
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
                           const double* delta, const double* vext, const double* dext, const double* ekin2,
                           const double* wm, const double* wp, double dV, double* out8, cudaStream_t s);
+
+// Plane-wave states of a uniform solution (uniform.cu); dst is float2 or double2.
+cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,
+                                    const int64_t* kidx_dev, int64_t n, cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t ncomplex, int* err, cudaStream_t s);

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libwslda_td.so")
 
 FP64, MIXED = 0, 1
 SLDA_A1, BDG = 0, 1
+# B of the spin-symmetric ASLDA functional (Sec. 2.4): 2^(2/3) [0.357 - 2 A(0) 2^(-5/3)], A(0) = 1.094
+B_SLDA = 2.0 ** (2.0 / 3.0) * (0.357 - 2.0 * 1.094 * 2.0 ** (-5.0 / 3.0))
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN", 5: "EDRIFT", 6: "ETIMEOUT", 7: "ESTATE",
           8: "EUNSUPPORTED"}
 KERNEL_KINDS = {"stage_x": 0, "stage_y": 1, "density": 2, "potentials": 3, "aux": 4}
@@ -38,6 +40,10 @@ class Lattice(ct.Structure):
 class Functional(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("B", ct.c_double), ("C", ct.c_double), ("inv_4pi_a", ct.c_double),
                 ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double)]
+
+
+class Uniform(ct.Structure):
+    _fields_ = [(k, ct.c_double) for k in ("mu_eff", "delta", "mu", "U", "C", "lam", "inv_g")]
 
 
 class Energy(ct.Structure):
@@ -71,6 +77,8 @@ def _load():
         "wslda_get_time": (I, [P, DP, ct.POINTER(I64)]),
         "wslda_memory_bytes": (I64, [P]),
         "wslda_set_profiling": (I, [P, I]),
+        "wslda_uniform_solve": (I, [ct.POINTER(Lattice), ct.POINTER(Functional), D, D, ct.POINTER(Uniform)]),
+        "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
         "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
@@ -85,6 +93,18 @@ lib = _load()
 
 def lattice_supported(precision: int, nx: int, ny: int, nz: int) -> bool:
     return bool(lib.wslda_lattice_supported(precision, nx, ny, nz))
+
+
+def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4pi_a=0.0, ec=-1.0,
+                  rho_sigma=1.0 / (6 * np.pi ** 2), delta0=0.0) -> dict:
+    """Uniform plane-wave BCS solution on the lattice (wslda_uniform_solve)."""
+    lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
+    fn = Functional(int(kind), float(B), 0.0, float(inv_4pi_a), 0.0, float(ec), 1e-12)
+    out = Uniform()
+    st = lib.wslda_uniform_solve(ct.byref(lat), ct.byref(fn), float(rho_sigma), float(delta0), ct.byref(out))
+    if st:
+        raise WsldaError(st, "uniform_solve found no solution or got bad arguments")
+    return {k: getattr(out, k) for k, _ in Uniform._fields_}
 
 
 def _ptr(a, dtype, on_device: bool):
@@ -167,6 +187,10 @@ class Context:
         pm, km = _ptr(w_minus, np.float64, False)
         pp, kp = _ptr(w_plus, np.float64, False)
         self._check(lib.wslda_load_states(self._h, box, p, pm, pp, int(dev)))
+
+    def fill_uniform_states(self, box: int, mu_eff: float, delta: float, kidx=None):
+        p, keep = _ptr(kidx, np.int64, False)
+        self._check(lib.wslda_fill_uniform_states(self._h, box, float(mu_eff), float(delta), p))
 
     def start(self, stationary: bool, dt: float):
         self._check(lib.wslda_start(self._h, int(bool(stationary)), float(dt)))
