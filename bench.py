@@ -97,7 +97,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
@@ -130,6 +130,7 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream)
     ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
     ctx.start(args.stationary, args.dt)      # Taylor start: the trapped plane waves are not stationary
+    variant = ctx.get_variant(box)
     if args.warmup:
         ctx.step(args.dt, args.warmup)
     torch.cuda.synchronize()
@@ -174,6 +175,7 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
                 "peak_source": "nominal FP64 rate", "algorithmic_flops_per_state_site": fx}
     launches = sum(kt[k][1] for k in kt)
     share = {k: kt[k][0] / ms for k in kt}
+    roof["launch_variant"] = variant
     return dict(value=value, ms_per_step=ms / args.steps, roofline=roof, clocks=ck, launches=launches,
                 kernel_ms=kt, kernel_share=share, rho=rho, nu=nu)
 

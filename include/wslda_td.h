@@ -151,6 +151,11 @@ wslda_status wslda_eval_f(wslda_ctx* ctx, int box, double* f);
 wslda_status wslda_save(wslda_ctx* ctx, const char* path);
 wslda_status wslda_load(wslda_ctx* ctx, const char* path);
 
+/* Launch variant (cluster size, threads, lanes per pencil) the autotuner chose
+ * for the box's stage kernels at wslda_start, as text. Setting the environment
+ * variable WSLDA_VARIANT=<index> before creating a context forces a variant. */
+wslda_status wslda_get_variant(wslda_ctx* ctx, int box, char* desc, int len);
+
 /* Simulation time and steps taken (including start-up steps). */
 wslda_status wslda_get_time(wslda_ctx* ctx, double* t, int64_t* steps);
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -121,10 +122,46 @@ cudaError_t dalloc(wslda_ctx* c, void** p, size_t bytes) {
   return e;
 }
 
-const KernelSet* find_kernels(int prec, int nx, int ny, int nz) {
+std::vector<const KernelSet*> find_variants(int prec, int nx, int ny, int nz) {
+  std::vector<const KernelSet*> v;
   for (const KernelSet& k : registry())
-    if (k.prec == prec && k.nx == nx && k.ny == ny && k.nz == nz) return &k;
-  return nullptr;
+    if (k.prec == prec && k.nx == nx && k.ny == ny && k.nz == nz) v.push_back(&k);
+  return v;
+}
+
+const KernelSet* find_kernels(int prec, int nx, int ny, int nz) {
+  std::vector<const KernelSet*> v = find_variants(prec, nx, ny, nz);
+  if (v.empty()) return nullptr;
+  const char* env = getenv("WSLDA_VARIANT");
+  if (env) {
+    const int i = atoi(env);
+    if (i >= 0 && i < int(v.size())) return v[i];
+  }
+  return v[0];
+}
+
+int resident_clusters(const KernelSet* ks) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ks->cs * 16);
+  cfg.blockDim = dim3(ks->bt);
+  cfg.dynamicSmemBytes = ks->smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ks->cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  for (int m = 0; m < NMODES; ++m) {
+    cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks->smem));
+    if (ks->cs > 8) cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, ks->fn[MODE_X], &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return ncl;
 }
 
 int brev_host(int j, int T) {
@@ -317,10 +354,69 @@ wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
   return refresh_fields(c, b, b.iphi, 0);
 }
 
+// Autotuner: time stage X of every compiled launch variant of the box's shape
+// on (a copy of) the box's first states in the free history slots, and keep
+// the fastest. The choice is cached per shape and precision for the process.
+template <typename R>
+wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
+  static std::vector<std::pair<std::vector<int>, int>> cache;
+  std::vector<const KernelSet*> v = find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
+  if (v.size() < 2 || getenv("WSLDA_VARIANT") || b.n == 0) return WSLDA_OK;
+  const std::vector<int> key = {c->prec, b.lat.nx, b.lat.ny, b.lat.nz};
+  for (auto& e : cache)
+    if (e.first == key) {
+      b.ks = v[e.second];
+      return WSLDA_OK;
+    }
+  const int64_t nt = std::min<int64_t>(b.n, 512);
+  const size_t bytes = size_t(nt) * 2 * b.M * b.csize;
+  CUDA_TRY(c, cudaMemcpyAsync(b.ptr(b.ih[0]), b.ptr(b.iphi), bytes, cudaMemcpyDeviceToDevice, c->stream));
+  for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (size_t k = 0; k < v.size(); ++k) {
+    if (resident_clusters(v[k]) < 1) continue;
+    StageArgs<R> a = base_args<R>(b, box_dV(b));
+    a.phi = static_cast<cx<R>*>(b.ptr(b.ih[0]));
+    a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[1]));
+    a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
+    a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
+    a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+    a.dt = dt;
+    a.err = c->err_d;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+      CUDA_TRY(c, v[k]->launch[MODE_X](&a, int(nt), c->stream));
+      CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+      CUDA_TRY(c, cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms = std::min(ms, t);
+    }
+    if (getenv("WSLDA_TUNE_VERBOSE"))
+      fprintf(stderr, "[wslda autotune] %dx%dx%d prec=%d variant %zu (cluster=%d threads=%d lanes=%d,%d,%d): %.3f ms\n",
+              b.lat.nx, b.lat.ny, b.lat.nz, c->prec, k, v[k]->cs, v[k]->bt, v[k]->tx, v[k]->ty, v[k]->tz, ms);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = int(k);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b.ks = v[best];
+  cache.push_back({key, best});
+  return WSLDA_OK;
+}
+
 template <typename R>
 wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
   wslda_status st;
   if ((st = refresh_fields(c, b, b.iphi, 1))) return st;
+  if ((st = autotune_box<R>(c, b, dt))) return st;
   const size_t bytes = size_t(b.n) * 2 * b.M * b.csize;
   if (stationary) {
     for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
@@ -471,26 +567,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
                               " MiB free");
     return -WSLDA_ENOMEM;
   }
-  int ncl = 0;
-  {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ks->cs * 16);
-    cfg.blockDim = dim3(ks->bt);
-    cfg.dynamicSmemBytes = ks->smem;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = ks->cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    for (int m = 0; m < NMODES; ++m) {
-      cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks->smem));
-      if (ks->cs > 8) cudaFuncSetAttribute(ks->fn[m], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    }
-    CUDA_TRY_NEG(c, cudaOccupancyMaxActiveClusters(&ncl, ks->fn[MODE_X], &cfg));
-    if (ncl < 1) return -fail(c, WSLDA_EUNSUPPORTED, "stage kernel cannot be resident on this device");
-  }
+  if (resident_clusters(ks) < 1)
+    return -fail(c, WSLDA_EUNSUPPORTED, "stage kernel cannot be resident on this device");
 
 #define ALLOC(ptr, bytes)                                                            \
   do {                                                                               \
@@ -802,6 +880,15 @@ wslda_status wslda_eval_f(wslda_ctx* c, int box, double* f) {
   if (st) return st;
   collect_profile(c);
   return check_device_error(c);
+}
+
+wslda_status wslda_get_variant(wslda_ctx* c, int box, char* desc, int len) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !desc || len <= 0) return fail(c, WSLDA_EINVAL, "get_variant: bad arguments");
+  snprintf(desc, size_t(len), "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu", b->ks->cs,
+           b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem);
+  return WSLDA_OK;
 }
 
 wslda_status wslda_get_time(wslda_ctx* c, double* t, int64_t* steps) {

@@ -16,7 +16,7 @@ using LaunchFn = cudaError_t (*)(const void* args, int nstates, cudaStream_t s);
 struct KernelSet {
   int prec;  // 0 = double, 1 = float (mixed)
   int nx, ny, nz;
-  int cs, bt, tx, ty, tz;
+  int cs, bt, tx, ty, tz, minb;
   size_t smem;
   LaunchFn launch[NMODES];
   const void* fn[NMODES];
@@ -61,7 +61,7 @@ KernelSet make_set() {
   KernelSet k;
   k.prec = sizeof(typename G::R) == 4 ? 1 : 0;
   k.nx = G::NX; k.ny = G::NY; k.nz = G::NZ;
-  k.cs = G::CS; k.bt = G::BT; k.tx = G::TX; k.ty = G::TY; k.tz = G::TZ;
+  k.cs = G::CS; k.bt = G::BT; k.tx = G::TX; k.ty = G::TY; k.tz = G::TZ; k.minb = G::MINB;
   k.smem = G::smem_bytes;
   k.launch[MODE_X] = launch_stage<G, MODE_X>;
   k.launch[MODE_Y] = launch_stage<G, MODE_Y>;
@@ -79,9 +79,10 @@ KernelSet make_set() {
 #define WSLDA_CAT2(a, b) a##b
 #define WSLDA_CAT(a, b) WSLDA_CAT2(a, b)
 // WSLDA_INSTANCE(real type, NX, NY, NZ, cluster size, threads, lanes per x/y/z pencil)
-#define WSLDA_INSTANCE(R, NX, NY, NZ, CS, BT, TX, TY, TZ)                                   \
+// optional last argument: CTAs per SM the register budget is sized for
+#define WSLDA_INSTANCE(R, NX, NY, NZ, CS, BT, TX, TY, TZ, ...)                              \
   static ::wslda::Registrar WSLDA_CAT(wslda_reg_, __COUNTER__)(                            \
-      ::wslda::make_set<::wslda::Geometry<R, NX, NY, NZ, CS, BT, TX, TY, TZ>>());
+      ::wslda::make_set<::wslda::Geometry<R, NX, NY, NZ, CS, BT, TX, TY, TZ, ##__VA_ARGS__>>());
 
 // ---------------------------------------------------------------------------
 // Site-major kernels (densities.cu)

@@ -65,12 +65,14 @@ struct ABM {
                           a4 = -19.0 / 720.0;
 };
 
-template <typename R_, int NX_, int NY_, int NZ_, int CS_, int BT_, int TX_, int TY_, int TZ_>
+template <typename R_, int NX_, int NY_, int NZ_, int CS_, int BT_, int TX_, int TY_, int TZ_, int MINB_ = 1>
 struct Geometry {
   using R = R_;
   using C = cx<R_>;
   static constexpr int NX = NX_, NY = NY_, NZ = NZ_, CS = CS_, BT = BT_;
   static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
+  static constexpr int MINB = MINB_;        // CTAs per SM the register budget is sized for
+  static constexpr int U = sizeof(R_) == 4 ? 4 : 2;  // sites per thread per batch in the epilogues
   static constexpr int P = NX / CS;         // x-planes per CTA
   static constexpr int ZP = NZ + 1;         // odd row pitch (N even)
   static constexpr int SLAB = P * NY * ZP;  // complex elements per component
@@ -79,12 +81,25 @@ struct Geometry {
   static constexpr int NW = BT / 32;
   static constexpr int NCOL = 2 * NY * NZ / CS;  // x-pencils per CTA
   static constexpr size_t smem_bytes =
-      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + size_t(NW + 16) * sizeof(double);
+      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + size_t(NW + 16) * sizeof(double) + 16;
   static_assert(NX % CS == 0, "cluster must split x evenly");
   static_assert((2 * NY * NZ) % CS == 0, "columns must split evenly");
   static_assert(BT % 32 == 0 && BT % TX == 0 && BT % TY == 0 && BT % TZ == 0, "block");
   static_assert(CS <= 16, "cluster size");
 };
+
+// Asynchronous global -> shared copies (8 or 16 bytes), all in flight at once.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 // Sum over the threads of the CTA and the CTAs of the cluster (double, fixed order).
 template <class G>
@@ -192,7 +207,7 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
 }
 
 template <class G, int MODE>
-__global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G::R> a) {
+__global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<typename G::R> a) {
   using C = typename G::C;
   using R = typename G::R;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -216,11 +231,12 @@ __global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G
   const C* twz = tws + G::NX + G::NY;
 
   const C* in = a.phi + sbase;
-  // load the slab of both components
+  // load the slab of both components (asynchronous copies, all in flight)
   for (int i = tid; i < 2 * G::NS; i += G::BT) {
     const int comp = i / G::NS, s = i % G::NS;
-    buf[comp * G::SLAB + (s / G::NZ) * G::ZP + (s % G::NZ)] = in[comp * G::M + gs0 + s];
+    cp_async<sizeof(C)>(buf + comp * G::SLAB + (s / G::NZ) * G::ZP + (s % G::NZ), in + comp * G::M + gs0 + s);
   }
+  cp_async_wait_all();
   __syncthreads();
   local_pass<G, 2, false>(buf, twz);
   __syncthreads();
@@ -233,18 +249,31 @@ __global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G
   local_pass<G, 2, true>(buf, twz);
   __syncthreads();
   // buf now holds T phi = -1/2 lap phi of this slab (natural order).
-
+  // Epilogues: each thread handles sites s = s0 + k*BT, k < U, issuing all of
+  // a batch's global loads before using them (memory-level parallelism).
+  constexpr int U = G::U;
   const C* inu = in;
   const C* inv = in + G::M;
   auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
 
   if constexpr (MODE == MODE_EKIN) {
     R eu = 0, ev = 0;
-    for (int s = tid; s < G::NS; s += G::BT) {
-      const C u = inu[gs0 + s], v = inv[gs0 + s];
-      const C tu = buf[sidx(s)], tv = buf[G::SLAB + sidx(s)];
-      eu += u.x * tu.x + u.y * tu.y;
-      ev += v.x * tv.x + v.y * tv.y;
+    for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
+      C u[U], v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int s = s0 + k * G::BT;
+        if (s < G::NS) { u[k] = inu[gs0 + s]; v[k] = inv[gs0 + s]; }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int s = s0 + k * G::BT;
+        if (s < G::NS) {
+          const C tu = buf[sidx(s)], tv = buf[G::SLAB + sidx(s)];
+          eu += u[k].x * tu.x + u[k].y * tu.y;
+          ev += v[k].x * tv.x + v[k].y * tv.y;
+        }
+      }
     }
     const double su = cluster_sum<G>(double(eu), red, cl);
     const double sv = cluster_sum<G>(double(ev), red, cl);
@@ -254,83 +283,117 @@ __global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G
     // H phi = [T u + W u + D v, D^* u - T v - W v] (Eq. dpsidt-Hpsi, A = 1)
     double En = 0.0;
     const bool need_e = (MODE != MODE_HORNER) || a.compute_e;
-    if (need_e) {
-      R ep = 0, ec = 0;  // compensated partial sum
-      for (int s = tid; s < G::NS; s += G::BT) {
-        const int g = gs0 + s;
-        const C u = inu[g], v = inv[g];
-        const R w = a.W[g];
-        const C d = a.D[g];
-        const C hu = add(add(buf[sidx(s)], scl(u, w)), mul(d, v));
-        const C hv = sub(sub(mulc(u, d), buf[G::SLAB + sidx(s)]), scl(v, w));
-        buf[sidx(s)] = hu;
-        buf[G::SLAB + sidx(s)] = hv;
-        const R t = (u.x * hu.x + u.y * hu.y + v.x * hv.x + v.y * hv.y) - ec;
-        const R nsum = ep + t;
-        ec = (nsum - ep) - t;
-        ep = nsum;
+    R ep = 0, ec = 0;  // compensated partial sum of <phi|H|phi>
+    for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
+      C u[U], v[U], d[U];
+      R w[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int s = s0 + k * G::BT;
+        if (s < G::NS) {
+          const int g = gs0 + s;
+          u[k] = inu[g]; v[k] = inv[g]; w[k] = a.W[g]; d[k] = a.D[g];
+        }
       }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int s = s0 + k * G::BT;
+        if (s < G::NS) {
+          const C hu = add(add(buf[sidx(s)], scl(u[k], w[k])), mul(d[k], v[k]));
+          const C hv = sub(sub(mulc(u[k], d[k]), buf[G::SLAB + sidx(s)]), scl(v[k], w[k]));
+          buf[sidx(s)] = hu;
+          buf[G::SLAB + sidx(s)] = hv;
+          if (need_e) {
+            const R t = (u[k].x * hu.x + u[k].y * hu.y + v[k].x * hv.x + v[k].y * hv.y) - ec;
+            const R nsum = ep + t;
+            ec = (nsum - ep) - t;
+            ep = nsum;
+          }
+        }
+      }
+    }
+    if (need_e) {
       En = cluster_sum<G>(double(ep), red, cl) * a.dV;
       if (MODE == MODE_HORNER && rank == 0 && tid == 0) a.E[n] = En;
     } else {
       En = a.E[n];
-      for (int s = tid; s < G::NS; s += G::BT) {
-        const int g = gs0 + s;
-        const C u = inu[g], v = inv[g];
-        const R w = a.W[g];
-        const C d = a.D[g];
-        buf[sidx(s)] = add(add(buf[sidx(s)], scl(u, w)), mul(d, v));
-        buf[G::SLAB + sidx(s)] = sub(sub(mulc(u, d), buf[G::SLAB + sidx(s)]), scl(v, w));
-      }
     }
     const R Er = R(En);
     // buf now holds H phi; each thread touches only its own sites below.
     if constexpr (MODE == MODE_F) {
       C* out = a.h0 + sbase;
-      for (int s = tid; s < G::NS; s += G::BT) {
-        const int g = gs0 + s;
-        // -i (H phi - E phi)
-        out[g] = mul_mi(sub(buf[sidx(s)], scl(inu[g], Er)));
-        out[G::M + g] = mul_mi(sub(buf[G::SLAB + sidx(s)], scl(inv[g], Er)));
+      for (int e0 = tid; e0 < 2 * G::NS; e0 += G::BT * U) {
+        C ph[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * G::BT;
+          if (e < 2 * G::NS) { const int comp = e >= G::NS, s = e - comp * G::NS; ph[k] = in[comp * G::M + gs0 + s]; }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * G::BT;
+          if (e < 2 * G::NS) {
+            const int comp = e >= G::NS, s = e - comp * G::NS;
+            out[comp * G::M + gs0 + s] = mul_mi(sub(buf[comp * G::SLAB + sidx(s)], scl(ph[k], Er)));
+          }
+        }
       }
       return;
     } else {
       R np = 0, nc = 0;  // compensated norm partial
       const bool norm_out = (MODE == MODE_X || MODE == MODE_Y) || a.normalize;
       C* dst = MODE == MODE_HORNER ? a.h0 + sbase : a.phi + sbase;
-      for (int comp = 0; comp < 2; ++comp) {
-        for (int s = tid; s < G::NS; s += G::BT) {
-          const int g = comp * G::M + gs0 + s;
-          const int b = comp * G::SLAB + sidx(s);
-          const C ph = in[g];
-          const C fv = mul_mi(sub(buf[b], scl(ph, Er)));
-          C res;
-          if constexpr (MODE == MODE_X) {
-            const C f1 = a.h1[sbase + g], f2 = a.h2[sbase + g], f3 = a.h3[sbase + g];
-            const R dt = R(a.dt);
-            const C pred = add(ph, scl(add(add(scl(fv, R(ABM::b0)), scl(f1, R(ABM::b1))),
-                                           add(scl(f2, R(ABM::b2)), scl(f3, R(ABM::b3)))), dt));
-            const C corr = add(ph, scl(add(add(scl(fv, R(ABM::a1)), scl(f1, R(ABM::a2))),
-                                           add(scl(f2, R(ABM::a3)), scl(f3, R(ABM::a4)))), dt));
-            a.h0[sbase + g] = fv;
-            a.h3[sbase + g] = corr;
-            res = pred;
-          } else if constexpr (MODE == MODE_Y) {
-            const C c = a.h3[sbase + g];
-            res = add(c, scl(fv, R(ABM::a0 * a.dt)));
-          } else {  // HORNER: base + coef * (-i)^{-1}... out = base + coef (H - E) in
-            const C hv = sub(buf[b], scl(ph, Er));
-            const C cf = mk<C>(R(a.coef_re), R(a.coef_im));
-            res = add(a.h1[sbase + g], mul(cf, hv));
+      const R dt = R(a.dt);
+      for (int e0 = tid; e0 < 2 * G::NS; e0 += G::BT * U) {
+        C ph[U], x1[U], x2[U], x3[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * G::BT;
+          if (e < 2 * G::NS) {
+            const int comp = e >= G::NS, s = e - comp * G::NS;
+            const int g = comp * G::M + gs0 + s;
+            ph[k] = in[g];
+            if constexpr (MODE == MODE_X) {
+              x1[k] = a.h1[sbase + g]; x2[k] = a.h2[sbase + g]; x3[k] = a.h3[sbase + g];
+            } else if constexpr (MODE == MODE_Y) {
+              x3[k] = a.h3[sbase + g];
+            } else {
+              x1[k] = a.h1[sbase + g];
+            }
           }
-          if (norm_out) {
-            buf[b] = res;
-            const R t = (res.x * res.x + res.y * res.y) - nc;
-            const R nsum = np + t;
-            nc = (nsum - np) - t;
-            np = nsum;
-          } else {
-            dst[g] = res;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = e0 + k * G::BT;
+          if (e < 2 * G::NS) {
+            const int comp = e >= G::NS, s = e - comp * G::NS;
+            const int g = comp * G::M + gs0 + s;
+            const int b = comp * G::SLAB + sidx(s);
+            const C hm = sub(buf[b], scl(ph[k], Er));  // (H - <H>_n) phi
+            C res;
+            if constexpr (MODE == MODE_X) {
+              const C fv = mul_mi(hm);  // f(phi) = -i (H - <H>_n) phi
+              const C pred = add(ph[k], scl(add(add(scl(fv, R(ABM::b0)), scl(x1[k], R(ABM::b1))),
+                                                add(scl(x2[k], R(ABM::b2)), scl(x3[k], R(ABM::b3)))), dt));
+              const C corr = add(ph[k], scl(add(add(scl(fv, R(ABM::a1)), scl(x1[k], R(ABM::a2))),
+                                                add(scl(x2[k], R(ABM::a3)), scl(x3[k], R(ABM::a4)))), dt));
+              a.h0[sbase + g] = fv;
+              a.h3[sbase + g] = corr;
+              res = pred;
+            } else if constexpr (MODE == MODE_Y) {
+              res = add(x3[k], scl(mul_mi(hm), R(ABM::a0 * a.dt)));
+            } else {  // HORNER: out = base + coef (H - E) in
+              res = add(x1[k], mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm));
+            }
+            if (norm_out) {
+              buf[b] = res;
+              const R t = (res.x * res.x + res.y * res.y) - nc;
+              const R nsum = np + t;
+              nc = (nsum - np) - t;
+              np = nsum;
+            } else {
+              dst[g] = res;
+            }
           }
         }
       }
@@ -340,9 +403,10 @@ __global__ void __launch_bounds__(G::BT) stage_kernel(const StageArgs<typename G
           if (tid == 0) atomicOr(a.err, 1);
         }
         const R sc = R(1.0 / sqrt(nrm));
-        for (int comp = 0; comp < 2; ++comp)
-          for (int s = tid; s < G::NS; s += G::BT)
-            dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
+        for (int e = tid; e < 2 * G::NS; e += G::BT) {
+          const int comp = e >= G::NS, s = e - comp * G::NS;
+          dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
+        }
       }
     }
   }

@@ -80,6 +80,7 @@ def _load():
         "wslda_uniform_solve": (I, [ct.POINTER(Lattice), ct.POINTER(Functional), D, D, ct.POINTER(Uniform)]),
         "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
         "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
+        "wslda_get_variant": (I, [P, I, ct.c_char_p, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -248,6 +249,11 @@ class Context:
         s = ct.c_int64()
         self._check(lib.wslda_get_time(self._h, ct.byref(t), ct.byref(s)))
         return t.value, s.value
+
+    def get_variant(self, box: int) -> str:
+        buf = ct.create_string_buffer(256)
+        self._check(lib.wslda_get_variant(self._h, box, buf, 256))
+        return buf.value.decode()
 
     def memory_bytes(self) -> int:
         return int(lib.wslda_memory_bytes(self._h))
