@@ -72,7 +72,8 @@ struct Geometry {
   static constexpr int NX = NX_, NY = NY_, NZ = NZ_, CS = CS_, BT = BT_;
   static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
   static constexpr int MINB = MINB_;        // CTAs per SM the register budget is sized for
-  static constexpr int U = sizeof(R_) == 4 ? 4 : 2;  // sites per thread per batch in the epilogues
+  // sites per thread per batch in the epilogues (fewer under a tight register budget)
+  static constexpr int U = sizeof(R_) == 4 ? (MINB_ >= 3 ? 2 : 4) : 2;
   static constexpr int P = NX / CS;         // x-planes per CTA
   static constexpr int ZP = NZ + 1;         // odd row pitch (N even)
   static constexpr int SLAB = P * NY * ZP;  // complex elements per component
@@ -81,11 +82,14 @@ struct Geometry {
   static constexpr int NW = BT / 32;
   static constexpr int NCOL = 2 * NY * NZ / CS;  // x-pencils per CTA
   static constexpr size_t smem_bytes =
-      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + size_t(NW + 16) * sizeof(double) + 16;
+      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + 112 * sizeof(double) + 16;
+  // reduction scratch (doubles): warp partials A [0,32) and B [32,64), per-CTA
+  // slots of the <H>_n / kinetic sums [64, 96), of the norm [96, 112)
+  static constexpr int RED_WA = 0, RED_WB = 32, RED_E = 64, RED_N = 96;
   static_assert(NX % CS == 0, "cluster must split x evenly");
   static_assert((2 * NY * NZ) % CS == 0, "columns must split evenly");
   static_assert(BT % 32 == 0 && BT % TX == 0 && BT % TY == 0 && BT % TZ == 0, "block");
-  static_assert(CS <= 16, "cluster size");
+  static_assert(CS <= 16 && BT <= 1024, "cluster size / block size");
 };
 
 // Asynchronous global -> shared copies (8 or 16 bytes), all in flight at once.
@@ -97,17 +101,50 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+// Bulk L2 prefetch of a contiguous range (a hint: no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
+// 32-bit shared::cluster addresses of this CTA's `p` in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_dsmem(unsigned addr, float2) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_dsmem(unsigned addr, double2) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_dsmem(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_dsmem(unsigned addr, double2 v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Sum over the threads of the CTA and the CTAs of the cluster (double, fixed order).
-template <class G>
+// LAST: the caller's final reduction; the closing barrier is only arrived at
+// here and must be waited on (cluster_wait) before the CTA exits.
+template <class G, bool LAST = false>
 __device__ __forceinline__ double cluster_sum(double v, double* red, cg::cluster_group& cl) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = v;
+  if ((threadIdx.x & 31) == 0) red[G::RED_WA + w] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -119,7 +156,8 @@ __device__ __forceinline__ double cluster_sum(double v, double* red, cg::cluster
   const double* src = cl.map_shared_rank(red + G::NW, 0);
   double tot = 0.0;
   for (int r = 0; r < G::CS; ++r) tot += src[r];
-  cl.sync();
+  if constexpr (LAST) cluster_arrive();
+  else cl.sync();
   return tot;
 }
 
@@ -164,16 +202,22 @@ __device__ __forceinline__ void local_pass(typename G::C* buf, const typename G:
 }
 
 // x pencils across the cluster: forward, multiply by the kinetic symbol, inverse.
+// Element x of a column lives in CTA x / P at plane x % P; the CTA windows are
+// mapped once (mapa) and accessed with 32-bit ld/st.shared::cluster.
 template <class G>
 __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* ktab, const typename G::C* tw,
-                                       cg::cluster_group& cl) {
+                                       cg::cluster_group& cl, typename G::R& ekin_u, typename G::R& ekin_v) {
   using C = typename G::C;
   using R = typename G::R;
   constexpr int T = G::TX, N = G::NX, N1 = N / T;
   constexpr int PER = G::BT / T;
   constexpr int ITERS = (G::NCOL + PER - 1) / PER;
+  constexpr unsigned PLANE = unsigned(G::NY * G::ZP * sizeof(C));
   const int j = threadIdx.x % T;
   const int rank = cl.block_rank();
+  unsigned win[G::CS];
+#pragma unroll
+  for (int r = 0; r < G::CS; ++r) win[r] = dsmem_addr(buf, unsigned(r));
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
     const int q = rank * G::NCOL + it * PER + threadIdx.x / T;
@@ -181,26 +225,34 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
     const int qq = act ? q : rank * G::NCOL;
     const int comp = qq / (G::NY * G::NZ), yz = qq % (G::NY * G::NZ);
     const int y = yz / G::NZ, z = yz % G::NZ;
-    const int off = comp * G::SLAB + y * G::ZP + z;
+    const unsigned off = unsigned((comp * G::SLAB + y * G::ZP + z) * sizeof(C));
     C x[N1];
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      const int xg = j + T * m;
-      const C* src = cl.map_shared_rank(buf, xg / G::P);
-      x[m] = src[off + (xg % G::P) * G::NY * G::ZP];
+      const int xg = j + T * m;  // compile-time plane when T == 1
+      x[m] = ld_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, C{});
     }
     pencil_fwd<N, T>(x, j, tw);
     const R kyz = ktab[G::NX + y] + ktab[G::NX + G::NY + z];
+    // Parseval: sum_k (k^2/2M) |phi_k|^2 = <phi|T|phi> for the unnormalised FFT
+    R ek = 0;
 #pragma unroll
-    for (int m = 0; m < N1; ++m) x[m] = scl(x[m], ktab[j + T * m] + kyz);
+    for (int m = 0; m < N1; ++m) {
+      const R kk = ktab[j + T * m] + kyz;
+      ek += kk * (x[m].x * x[m].x + x[m].y * x[m].y);
+      x[m] = scl(x[m], kk);
+    }
+    if (act) {
+      if (comp == 0) ekin_u += ek;
+      else ekin_v += ek;
+    }
     pencil_inv<N, T>(x, j, tw);
     // a column is read and written only by its own lane group: no barrier here
     if (act) {
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         const int xg = j + T * m;
-        C* dst = cl.map_shared_rank(buf, xg / G::P);
-        dst[off + (xg % G::P) * G::NY * G::ZP] = x[m];
+        st_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, x[m]);
       }
     }
   }
@@ -215,7 +267,6 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   R* ktab = reinterpret_cast<R*>(buf + 2 * G::SLAB);
   C* tws = reinterpret_cast<C*>(ktab + (G::NX + G::NY + G::NZ));
   double* red = reinterpret_cast<double*>(tws + (G::NX + G::NY + G::NZ));
-  // keep the reduction scratch 8-byte aligned
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
 
   cg::cluster_group cl = cg::this_cluster();
@@ -224,6 +275,8 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   const int tid = threadIdx.x;
   const size_t sbase = size_t(n) * 2 * G::M;
   const int gs0 = rank * G::NS;  // first global site of this slab
+  constexpr int U = G::U;
+  auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
 
   for (int i = tid; i < G::NX + G::NY + G::NZ; i += G::BT) { ktab[i] = a.ktab[i]; tws[i] = a.tw[i]; }
   const C* twx = tws;
@@ -234,180 +287,176 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   // load the slab of both components (asynchronous copies, all in flight)
   for (int i = tid; i < 2 * G::NS; i += G::BT) {
     const int comp = i / G::NS, s = i % G::NS;
-    cp_async<sizeof(C)>(buf + comp * G::SLAB + (s / G::NZ) * G::ZP + (s % G::NZ), in + comp * G::M + gs0 + s);
+    cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
   }
   cp_async_wait_all();
   __syncthreads();
-  local_pass<G, 2, false>(buf, twz);
-  __syncthreads();
-  local_pass<G, 1, false>(buf, twy);
-  cl.sync();
-  x_pass<G>(buf, ktab, twx, cl);
-  cl.sync();
-  local_pass<G, 1, true>(buf, twy);
-  __syncthreads();
-  local_pass<G, 2, true>(buf, twz);
-  __syncthreads();
-  // buf now holds T phi = -1/2 lap phi of this slab (natural order).
-  // Epilogues: each thread handles sites s = s0 + k*BT, k < U, issuing all of
-  // a batch's global loads before using them (memory-level parallelism).
-  constexpr int U = G::U;
-  const C* inu = in;
-  const C* inv = in + G::M;
-  auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
 
-  if constexpr (MODE == MODE_EKIN) {
-    R eu = 0, ev = 0;
+  // <H>_n, potential part: sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v), from the slab
+  const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
+  R ep = 0, ec = 0;  // compensated partial sum
+  if (need_e) {
     for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
-      C u[U], v[U];
+      R w[U];
+      C d[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
-        if (s < G::NS) { u[k] = inu[gs0 + s]; v[k] = inv[gs0 + s]; }
+        if (s < G::NS) { w[k] = a.W[gs0 + s]; d[k] = a.D[gs0 + s]; }
       }
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
-          const C tu = buf[sidx(s)], tv = buf[G::SLAB + sidx(s)];
-          eu += u[k].x * tu.x + u[k].y * tu.y;
-          ev += v[k].x * tv.x + v[k].y * tv.y;
+          const C u = buf[sidx(s)], v = buf[G::SLAB + sidx(s)];
+          const C dv = mul(d[k], v);
+          const R t = (w[k] * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
+          const R ns = ep + t;
+          ec = (ns - ep) - t;
+          ep = ns;
         }
       }
     }
-    const double su = cluster_sum<G>(double(eu), red, cl);
-    const double sv = cluster_sum<G>(double(ev), red, cl);
-    if (rank == 0 && tid == 0) { a.out2[2 * n] = su * a.dV; a.out2[2 * n + 1] = sv * a.dV; }
+  }
+
+  __syncthreads();  // the slab is read above before the z pass overwrites it
+  local_pass<G, 2, false>(buf, twz);
+  __syncthreads();
+  local_pass<G, 1, false>(buf, twy);
+  cl.sync();
+  R eku = 0, ekv = 0;
+  x_pass<G>(buf, ktab, twx, cl, eku, ekv);
+  // publish this CTA's partial <H>_n (or kinetic sums) on the barrier that
+  // closes the x pass
+  double* slot = red + G::RED_E;
+  {
+    double v0 = MODE == MODE_EKIN ? double(eku) : double(ep) + double(eku) - double(ekv);
+    double v1 = double(ekv);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    if ((tid & 31) == 0) { red[G::RED_WA + (tid >> 5)] = v0; red[G::RED_WB + (tid >> 5)] = v1; }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int i = 0; i < G::NW; ++i) { s0 += red[G::RED_WA + i]; s1 += red[G::RED_WB + i]; }
+      double* dst = cl.map_shared_rank(slot, 0);
+      dst[rank] = s0;
+      dst[G::CS + rank] = s1;
+    }
+  }
+  cl.sync();
+  double En = 0.0, Ev = 0.0;
+  {
+    const double* src = cl.map_shared_rank(slot, 0);
+    for (int r = 0; r < G::CS; ++r) { En += src[r]; Ev += src[G::CS + r]; }
+    En *= a.dV;
+    Ev *= a.dV;
+  }
+  local_pass<G, 1, true>(buf, twy);
+  __syncthreads();
+  local_pass<G, 2, true>(buf, twz);
+  __syncthreads();
+  // buf now holds T phi = -1/2 lap phi of this slab (natural order).
+
+  if constexpr (MODE == MODE_EKIN) {
+    if (rank == 0 && tid == 0) { a.out2[2 * n] = En; a.out2[2 * n + 1] = Ev; }
+    cl.sync();  // CTA 0's slot stays readable until every CTA has read it
     return;
   } else {
-    // H phi = [T u + W u + D v, D^* u - T v - W v] (Eq. dpsidt-Hpsi, A = 1)
-    double En = 0.0;
-    const bool need_e = (MODE != MODE_HORNER) || a.compute_e;
-    R ep = 0, ec = 0;  // compensated partial sum of <phi|H|phi>
+    if (MODE == MODE_HORNER) {
+      if (a.compute_e) {
+        if (rank == 0 && tid == 0) a.E[n] = En;
+      } else {
+        En = a.E[n];
+      }
+    }
+    const R Er = R(En);
+    R np = 0, nc = 0;  // compensated norm partial
+    const bool norm_out = MODE == MODE_X || MODE == MODE_Y || (MODE == MODE_HORNER && a.normalize);
+    C* dst = (MODE == MODE_HORNER || MODE == MODE_F) ? a.h0 + sbase : a.phi + sbase;
+    const R dt = R(a.dt);
+    // one pointwise sweep: H phi on the fly, f = -i (H - <H>_n) phi, integrator
     for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
-      C u[U], v[U], d[U];
+      C u[U], v[U], d[U], x1[2][U], x2[2][U], x3[2][U];
       R w[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
           const int g = gs0 + s;
-          u[k] = inu[g]; v[k] = inv[g]; w[k] = a.W[g]; d[k] = a.D[g];
+          u[k] = in[g];
+          v[k] = in[G::M + g];
+          w[k] = a.W[g];
+          d[k] = a.D[g];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const size_t gg = sbase + c * G::M + g;
+            if constexpr (MODE == MODE_X) { x1[c][k] = a.h1[gg]; x2[c][k] = a.h2[gg]; x3[c][k] = a.h3[gg]; }
+            if constexpr (MODE == MODE_Y) x3[c][k] = a.h3[gg];
+            if constexpr (MODE == MODE_HORNER) x1[c][k] = a.h1[gg];
+          }
         }
       }
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
-          const C hu = add(add(buf[sidx(s)], scl(u[k], w[k])), mul(d[k], v[k]));
-          const C hv = sub(sub(mulc(u[k], d[k]), buf[G::SLAB + sidx(s)]), scl(v[k], w[k]));
-          buf[sidx(s)] = hu;
-          buf[G::SLAB + sidx(s)] = hv;
-          if (need_e) {
-            const R t = (u[k].x * hu.x + u[k].y * hu.y + v[k].x * hv.x + v[k].y * hv.y) - ec;
-            const R nsum = ep + t;
-            ec = (nsum - ep) - t;
-            ep = nsum;
-          }
-        }
-      }
-    }
-    if (need_e) {
-      En = cluster_sum<G>(double(ep), red, cl) * a.dV;
-      if (MODE == MODE_HORNER && rank == 0 && tid == 0) a.E[n] = En;
-    } else {
-      En = a.E[n];
-    }
-    const R Er = R(En);
-    // buf now holds H phi; each thread touches only its own sites below.
-    if constexpr (MODE == MODE_F) {
-      C* out = a.h0 + sbase;
-      for (int e0 = tid; e0 < 2 * G::NS; e0 += G::BT * U) {
-        C ph[U];
+          const int g = gs0 + s;
+          const int b = sidx(s);
+          // (H - <H>_n) phi for both components (Eq. dpsidt-Hpsi, A = 1)
+          C hm[2];
+          hm[0] = sub(add(add(buf[b], scl(u[k], w[k])), mul(d[k], v[k])), scl(u[k], Er));
+          hm[1] = sub(sub(sub(mulc(u[k], d[k]), buf[G::SLAB + b]), scl(v[k], w[k])), scl(v[k], Er));
+          const C ph[2] = {u[k], v[k]};
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * G::BT;
-          if (e < 2 * G::NS) { const int comp = e >= G::NS, s = e - comp * G::NS; ph[k] = in[comp * G::M + gs0 + s]; }
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * G::BT;
-          if (e < 2 * G::NS) {
-            const int comp = e >= G::NS, s = e - comp * G::NS;
-            out[comp * G::M + gs0 + s] = mul_mi(sub(buf[comp * G::SLAB + sidx(s)], scl(ph[k], Er)));
-          }
-        }
-      }
-      return;
-    } else {
-      R np = 0, nc = 0;  // compensated norm partial
-      const bool norm_out = (MODE == MODE_X || MODE == MODE_Y) || a.normalize;
-      C* dst = MODE == MODE_HORNER ? a.h0 + sbase : a.phi + sbase;
-      const R dt = R(a.dt);
-      for (int e0 = tid; e0 < 2 * G::NS; e0 += G::BT * U) {
-        C ph[U], x1[U], x2[U], x3[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * G::BT;
-          if (e < 2 * G::NS) {
-            const int comp = e >= G::NS, s = e - comp * G::NS;
-            const int g = comp * G::M + gs0 + s;
-            ph[k] = in[g];
-            if constexpr (MODE == MODE_X) {
-              x1[k] = a.h1[sbase + g]; x2[k] = a.h2[sbase + g]; x3[k] = a.h3[sbase + g];
-            } else if constexpr (MODE == MODE_Y) {
-              x3[k] = a.h3[sbase + g];
-            } else {
-              x1[k] = a.h1[sbase + g];
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = e0 + k * G::BT;
-          if (e < 2 * G::NS) {
-            const int comp = e >= G::NS, s = e - comp * G::NS;
-            const int g = comp * G::M + gs0 + s;
-            const int b = comp * G::SLAB + sidx(s);
-            const C hm = sub(buf[b], scl(ph[k], Er));  // (H - <H>_n) phi
+          for (int c = 0; c < 2; ++c) {
+            const size_t gg = sbase + c * G::M + g;
             C res;
             if constexpr (MODE == MODE_X) {
-              const C fv = mul_mi(hm);  // f(phi) = -i (H - <H>_n) phi
-              const C pred = add(ph[k], scl(add(add(scl(fv, R(ABM::b0)), scl(x1[k], R(ABM::b1))),
-                                                add(scl(x2[k], R(ABM::b2)), scl(x3[k], R(ABM::b3)))), dt));
-              const C corr = add(ph[k], scl(add(add(scl(fv, R(ABM::a1)), scl(x1[k], R(ABM::a2))),
-                                                add(scl(x2[k], R(ABM::a3)), scl(x3[k], R(ABM::a4)))), dt));
-              a.h0[sbase + g] = fv;
-              a.h3[sbase + g] = corr;
-              res = pred;
+              const C fv = mul_mi(hm[c]);  // f(phi) = -i (H - <H>_n) phi
+              res = add(ph[c], scl(add(add(scl(fv, R(ABM::b0)), scl(x1[c][k], R(ABM::b1))),
+                                       add(scl(x2[c][k], R(ABM::b2)), scl(x3[c][k], R(ABM::b3)))), dt));
+              const C corr = add(ph[c], scl(add(add(scl(fv, R(ABM::a1)), scl(x1[c][k], R(ABM::a2))),
+                                                add(scl(x2[c][k], R(ABM::a3)), scl(x3[c][k], R(ABM::a4)))), dt));
+              a.h0[gg] = fv;
+              a.h3[gg] = corr;
             } else if constexpr (MODE == MODE_Y) {
-              res = add(x3[k], scl(mul_mi(hm), R(ABM::a0 * a.dt)));
+              res = add(x3[c][k], scl(mul_mi(hm[c]), R(ABM::a0 * a.dt)));
+            } else if constexpr (MODE == MODE_F) {
+              res = mul_mi(hm[c]);
             } else {  // HORNER: out = base + coef (H - E) in
-              res = add(x1[k], mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm));
+              res = add(x1[c][k], mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm[c]));
             }
             if (norm_out) {
-              buf[b] = res;
+              buf[c * G::SLAB + b] = res;
               const R t = (res.x * res.x + res.y * res.y) - nc;
-              const R nsum = np + t;
-              nc = (nsum - np) - t;
-              np = nsum;
+              const R ns = np + t;
+              nc = (ns - np) - t;
+              np = ns;
             } else {
-              dst[g] = res;
+              dst[c * G::M + g] = res;
             }
           }
         }
       }
-      if (norm_out) {
-        const double nrm = cluster_sum<G>(double(np), red, cl) * a.dV;
-        if (!(nrm > 0.0) || !isfinite(nrm)) {
-          if (tid == 0) atomicOr(a.err, 1);
-        }
-        const R sc = R(1.0 / sqrt(nrm));
-        for (int e = tid; e < 2 * G::NS; e += G::BT) {
-          const int comp = e >= G::NS, s = e - comp * G::NS;
-          dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
-        }
+    }
+    if (norm_out) {
+      // the closing cluster barrier overlaps the scaled stores
+      const double nrm = cluster_sum<G, true>(double(np), red, cl) * a.dV;
+      if (!(nrm > 0.0) || !isfinite(nrm)) {
+        if (tid == 0) atomicOr(a.err, 1);
       }
+      const R sc = R(1.0 / sqrt(nrm));
+      for (int e = tid; e < 2 * G::NS; e += G::BT) {
+        const int comp = e >= G::NS, s = e - comp * G::NS;
+        dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
+      }
+      cluster_wait();
+    } else {
+      cl.sync();  // CTA 0's slot stays readable until every CTA has read it
     }
   }
 }
