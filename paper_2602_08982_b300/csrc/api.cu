@@ -47,7 +47,8 @@ struct Box {
   int iphi = 0, ih[4] = {1, 2, 3, 4};
   double *vext = nullptr, *dext = nullptr, *lam = nullptr, *rho = nullptr, *nu = nullptr, *U = nullptr,
          *delta = nullptr;
-  void *W = nullptr, *D = nullptr;      // working-precision H fields
+  void* WD = nullptr;                   // working-precision H fields {W, Re D, Im D, 0}
+  double* sc[5] = {};                   // per-slot per-state scale (deferred normalisation)
   void *ktab = nullptr, *tw = nullptr;  // per-axis kinetic symbol and twiddles
   double *wm = nullptr, *wp = nullptr;  // double weights
   void *wm_r = nullptr, *wp_r = nullptr;
@@ -241,8 +242,7 @@ void collect_profile(wslda_ctx* c) {
 template <typename R>
 StageArgs<R> base_args(const Box& b, double dV) {
   StageArgs<R> a = {};
-  a.W = static_cast<const R*>(b.W);
-  a.D = static_cast<const cx<R>*>(b.D);
+  a.WD = static_cast<const fx4<R>*>(b.WD);
   a.ktab = static_cast<const R*>(b.ktab);
   a.tw = static_cast<const cx<R>*>(b.tw);
   a.E = b.Ebuf;
@@ -268,7 +268,8 @@ template <typename R>
 wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   if (b.n > 0) {
     ProfScope ps(c, PROF_DENS);
-    CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), static_cast<const R*>(b.wm_r),
+    CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), b.sc[islot],
+                                          static_cast<const R*>(b.wm_r),
                                           static_cast<const R*>(b.wp_r), b.n, b.M, b.nchunk, b.chunk, b.part,
                                           c->stream));
   } else {
@@ -276,7 +277,7 @@ wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   }
   ProfScope ps2(c, PROF_POT);
   CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu, b.U,
-                                   b.delta, static_cast<R*>(b.W), static_cast<cx<R>*>(b.D), c->stream));
+                                   b.delta, static_cast<fx4<R>*>(b.WD), c->stream));
   return WSLDA_OK;
 }
 
@@ -293,6 +294,8 @@ wslda_status stage_x(wslda_ctx* c, Box& b, double dt) {
   a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[1]));
   a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
   a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  a.sc_in = b.sc[b.iphi];
+  a.sc_out = b.sc[b.iphi];
   a.dt = dt;
   return launch_mode<R>(c, b, MODE_X, a, PROF_X);
 }
@@ -302,6 +305,8 @@ wslda_status stage_y(wslda_ctx* c, Box& b, double dt) {
   StageArgs<R> a = base_args<R>(b, box_dV(b));
   a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
   a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  a.sc_in = b.sc[b.iphi];
+  a.sc_out = b.sc[b.iphi];
   a.dt = dt;
   return launch_mode<R>(c, b, MODE_Y, a, PROF_Y);
 }
@@ -311,6 +316,8 @@ wslda_status eval_f_into(wslda_ctx* c, Box& b, int in_slot, int out_slot) {
   StageArgs<R> a = base_args<R>(b, box_dV(b));
   a.phi = static_cast<cx<R>*>(b.ptr(in_slot));
   a.h0 = static_cast<cx<R>*>(b.ptr(out_slot));
+  a.sc_in = b.sc[in_slot];
+  a.sc_out = b.sc[out_slot];  // f is stored unscaled
   return launch_mode<R>(c, b, MODE_F, a, PROF_AUX);
 }
 
@@ -322,6 +329,9 @@ wslda_status horner(wslda_ctx* c, Box& b, int in_slot, int base_slot, int out_sl
   a.phi = static_cast<cx<R>*>(b.ptr(in_slot));
   a.h1 = static_cast<const cx<R>*>(b.ptr(base_slot));
   a.h0 = static_cast<cx<R>*>(b.ptr(out_slot));
+  a.sc_in = b.sc[in_slot];
+  a.sc_base = b.sc[base_slot];
+  a.sc_out = b.sc[out_slot];
   a.coef_re = 0.0;
   a.coef_im = coef_im;
   a.compute_e = compute_e;
@@ -371,6 +381,7 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   const int64_t nt = std::min<int64_t>(b.n, 512);
   const size_t bytes = size_t(nt) * 2 * b.M * b.csize;
   CUDA_TRY(c, cudaMemcpyAsync(b.ptr(b.ih[0]), b.ptr(b.iphi), bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(b.sc[b.ih[0]], b.sc[b.iphi], size_t(nt) * 8, cudaMemcpyDeviceToDevice, c->stream));
   for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
@@ -385,6 +396,8 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
     a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
     a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
     a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+    a.sc_in = b.sc[b.ih[0]];
+    a.sc_out = b.sc[b.ih[1]];
     a.dt = dt;
     a.err = c->err_d;
     float ms = 1e30f;
@@ -556,8 +569,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.chunk = std::max<int64_t>(1, (nstates + b.nchunk - 1) / b.nchunk);
 
   const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
-  const size_t field_bytes = size_t(M) * (8 * 9 + rsize * 3) + size_t(3) * M * 8 * b.nchunk +
-                             size_t(nstates) * (8 * 5 + rsize * 2) + 4096;
+  const size_t field_bytes = size_t(M) * (8 * 9 + rsize * 4) + size_t(3) * M * 8 * b.nchunk +
+                             size_t(nstates) * (8 * 10 + rsize * 2) + 4096;
   const size_t need = 5 * state_bytes + field_bytes;
   size_t freeb = 0, totalb = 0;
   CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
@@ -589,8 +602,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.nu, 2 * M * 8);
   ALLOC(b.U, M * 8);
   ALLOC(b.delta, 2 * M * 8);
-  ALLOC(b.W, M * rsize);
-  ALLOC(b.D, 2 * M * rsize);
+  ALLOC(b.WD, 4 * M * rsize);
+  for (int i = 0; i < 5; ++i) ALLOC(b.sc[i], std::max<int64_t>(nstates, 1) * 8);
   const int naxis = lat->nx + lat->ny + lat->nz;
   ALLOC(b.ktab, naxis * rsize);
   ALLOC(b.tw, 2 * naxis * rsize);
@@ -678,6 +691,7 @@ wslda_status wslda_load_states(wslda_ctx* c, int box, const double* uv, const do
       return fail(c, WSLDA_ECUDA, std::string("narrow: ") + cudaGetErrorString(e));
     }
   }
+  CUDA_TRY(c, launch_fill(b->sc[b->iphi], 1.0, std::max<int64_t>(b->n, 1), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (stage) cudaFree(stage);
   std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
@@ -717,6 +731,7 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, dou
   }
   cudaError_t e = launch_fill_plane_waves(b->slot[b->iphi], c->prec == WSLDA_MIXED, b->lat, mu_eff, delta, kd, b->n,
                                           c->stream);
+  if (e == cudaSuccess) e = launch_fill(b->sc[b->iphi], 1.0, std::max<int64_t>(b->n, 1), c->stream);
   cudaError_t e2 = cudaStreamSynchronize(c->stream);
   if (kd) cudaFree(kd);
   if (e != cudaSuccess || e2 != cudaSuccess)
@@ -785,9 +800,12 @@ wslda_status wslda_get_states(wslda_ctx* c, int box, double* uv, int on_device) 
   for (int64_t off = 0; off < total; off += per) {
     const int64_t cnt = std::min(per, total - off);
     double* dst = on_device ? uv + 2 * off : static_cast<double*>(stage);
+    const int64_t per_state = 2 * int64_t(b->M);
     cudaError_t e = c->prec == WSLDA_MIXED
-                        ? launch_widen<float>(static_cast<float2*>(b->slot[b->iphi]) + off, dst, cnt, c->stream)
-                        : launch_widen<double>(static_cast<double2*>(b->slot[b->iphi]) + off, dst, cnt, c->stream);
+                        ? launch_widen<float>(static_cast<float2*>(b->slot[b->iphi]) + off, dst, cnt, b->sc[b->iphi],
+                                              off, per_state, c->stream)
+                        : launch_widen<double>(static_cast<double2*>(b->slot[b->iphi]) + off, dst, cnt,
+                                               b->sc[b->iphi], off, per_state, c->stream);
     if (e != cudaSuccess) {
       if (stage) cudaFree(stage);
       return fail(c, WSLDA_ECUDA, std::string("widen: ") + cudaGetErrorString(e));
@@ -841,10 +859,12 @@ wslda_status wslda_get_energy(wslda_ctx* c, int box, wslda_energy* out) {
   if (c->prec == WSLDA_MIXED) {
     StageArgs<float> a = base_args<float>(*b, box_dV(*b));
     a.phi = static_cast<float2*>(b->ptr(b->iphi));
+    a.sc_in = b->sc[b->iphi];
     if ((st = launch_mode<float>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
   } else {
     StageArgs<double> a = base_args<double>(*b, box_dV(*b));
     a.phi = static_cast<double2*>(b->ptr(b->iphi));
+    a.sc_in = b->sc[b->iphi];
     if ((st = launch_mode<double>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
   }
   CUDA_TRY(c, launch_energy(b->M, b->n, b->fdev, b->rho, b->nu, b->delta, b->vext, b->dext, b->ekin2, b->wm, b->wp,
@@ -921,7 +941,8 @@ wslda_status wslda_get_kernel_time(wslda_ctx* c, int kind, double* total_ms, int
 }
 
 // File layout: "WSLDATD1", prec, nboxes, t, steps, dt_start, started; per box:
-// nx ny nz n iphi ih[4], then phi, h0..h3 (slot order), lam, vext, dext, wm, wp.
+// nx ny nz n iphi ih[4], then for each of the 5 slots its states and per-state
+// scale, then lam, vext, dext, wm, wp.
 wslda_status wslda_save(wslda_ctx* c, const char* path) {
   CHECK_CTX(c);
   if (!path) return fail(c, WSLDA_EINVAL, "save: null path");
@@ -946,7 +967,7 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
     int64_t bh[9] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3]};
     fwrite(bh, sizeof(bh), 1, f);
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
-    for (int i = 0; i < 5 && ok; ++i) ok = dump(b.slot[i], sb);
+    for (int i = 0; i < 5 && ok; ++i) ok = dump(b.slot[i], sb) && dump(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && dump(b.lam, size_t(b.M) * 8) && dump(b.vext, size_t(b.M) * 8) && dump(b.dext, size_t(b.M) * 16) &&
          dump(b.wm, std::max<int64_t>(b.n, 1) * 8) && dump(b.wp, std::max<int64_t>(b.n, 1) * 8);
   }
@@ -984,7 +1005,7 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
     b.iphi = int(bh[4]);
     for (int i = 0; i < 4; ++i) b.ih[i] = int(bh[5 + i]);
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
-    for (int i = 0; i < 5 && ok; ++i) ok = slurp(b.slot[i], sb);
+    for (int i = 0; i < 5 && ok; ++i) ok = slurp(b.slot[i], sb) && slurp(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && slurp(b.lam, size_t(b.M) * 8) && slurp(b.vext, size_t(b.M) * 8) && slurp(b.dext, size_t(b.M) * 16) &&
          slurp(b.wm, std::max<int64_t>(b.n, 1) * 8) && slurp(b.wp, std::max<int64_t>(b.n, 1) * 8);
     if (!ok) break;

@@ -25,24 +25,33 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __restrict__ phi, const R* __restrict__ wm,
-                                                              const R* __restrict__ wp, int64_t nstates, int M,
-                                                              int64_t chunk, double* __restrict__ part) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= M) return;
+__global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __restrict__ phi, const double* __restrict__ sc,
+                                                              const R* __restrict__ wm, const R* __restrict__ wp,
+                                                              int64_t nstates, int M, int64_t chunk,
+                                                              double* __restrict__ part) {
+  // no early exit: the float path broadcasts per-state factors with shuffles
+  const int s_raw = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = s_raw < M;
+  const int s = live ? s_raw : M - 1;
+  const int lane = threadIdx.x & 31;
   const int64_t n0 = int64_t(blockIdx.y) * chunk;
   const int64_t n1 = min(n0 + chunk, nstates);
   const int64_t stride = 2 * int64_t(M);
   double ar = 0.0, anr = 0.0, ani = 0.0;
   if constexpr (sizeof(R) == 4) {
     for (int64_t g = n0; g < n1; g += kGroup) {
+      // lane l converts the factor of state g + l once (one double op per 32 states)
+      const int64_t nl = g + lane;
+      const float s2l = nl < n1 ? float(sc[nl] * sc[nl]) : 0.f;
       float sr = 0.f, cr = 0.f, snr = 0.f, cnr = 0.f, sni = 0.f, cni = 0.f;
-      const int64_t ge = min(g + kGroup, n1);
+      const int ge = int(min(int64_t(kGroup), n1 - g));
 #pragma unroll 4
-      for (int64_t n = g; n < ge; ++n) {
+      for (int k = 0; k < ge; ++k) {
+        const int64_t n = g + k;
         const float2 u = phi[n * stride + s];
         const float2 v = phi[n * stride + M + s];
-        const float a = wm[n], b = wp[n], d = a - b;
+        const float s2 = __shfl_sync(0xffffffffu, s2l, k);  // deferred normalisation of the stored states
+        const float a = wm[n] * s2, b = wp[n] * s2, d = a - b;
         kahan(sr, cr, a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y));
         kahan(snr, cnr, d * (u.x * v.x + u.y * v.y));
         kahan(sni, cni, d * (u.y * v.x - u.x * v.y));
@@ -56,12 +65,14 @@ __global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __res
     for (int64_t n = n0; n < n1; ++n) {
       const double2 u = phi[n * stride + s];
       const double2 v = phi[n * stride + M + s];
-      const double a = wm[n], b = wp[n], d = a - b;
+      const double s2 = sc[n] * sc[n];
+      const double a = wm[n] * s2, b = wp[n] * s2, d = a - b;
       ar += a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y);
       anr += d * (u.x * v.x + u.y * v.y);
       ani += d * (u.y * v.x - u.x * v.y);
     }
   }
+  if (!live) return;
   double* p = part + int64_t(blockIdx.y) * 3 * M;
   p[s] = ar;
   p[M + s] = anr;
@@ -69,16 +80,16 @@ __global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __res
 }
 
 template <typename R>
-cudaError_t launch_density_partial(const cx<R>* phi, const R* wm, const R* wp, int64_t nstates, int M, int nchunk,
-                                   int64_t chunk, double* part, cudaStream_t s) {
+cudaError_t launch_density_partial(const cx<R>* phi, const double* sc, const R* wm, const R* wp, int64_t nstates,
+                                   int M, int nchunk, int64_t chunk, double* part, cudaStream_t s) {
   dim3 grid((M + 255) / 256, nchunk);
-  density_partial_kernel<R><<<grid, 256, 0, s>>>(phi, wm, wp, nstates, M, chunk, part);
+  density_partial_kernel<R><<<grid, 256, 0, s>>>(phi, sc, wm, wp, nstates, M, chunk, part);
   return cudaGetLastError();
 }
-template cudaError_t launch_density_partial<float>(const float2*, const float*, const float*, int64_t, int, int,
-                                                   int64_t, double*, cudaStream_t);
-template cudaError_t launch_density_partial<double>(const double2*, const double*, const double*, int64_t, int, int,
-                                                    int64_t, double*, cudaStream_t);
+template cudaError_t launch_density_partial<float>(const float2*, const double*, const float*, const float*, int64_t,
+                                                   int, int, int64_t, double*, cudaStream_t);
+template cudaError_t launch_density_partial<double>(const double2*, const double*, const double*, const double*,
+                                                    int64_t, int, int, int64_t, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Functional (Sec. 2.4) and regulator (Sec. 2.6) at one site.
@@ -134,7 +145,7 @@ constexpr int kRegulatorIters = 60;  // fixed-point iterations for the t = 0 reg
 template <typename R>
 __global__ void potentials_kernel(const double* __restrict__ part, int nchunk, int M, FunctionalDev fn,
                                   const double* __restrict__ vext, const double* __restrict__ dext, double* lam,
-                                  int init_lam, double* rho, double* nu, double* Uo, double* delta, R* W, cx<R>* D) {
+                                  int init_lam, double* rho, double* nu, double* Uo, double* delta, fx4<R>* WD) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= M) return;
   double r = 0.0, nr = 0.0, ni = 0.0;
@@ -166,26 +177,26 @@ __global__ void potentials_kernel(const double* __restrict__ part, int nchunk, i
   Uo[s] = U;
   delta[2 * s] = dr;
   delta[2 * s + 1] = di;
-  W[s] = R(U + ve - fn.mu);
-  cx<R> d;
-  d.x = R(dr + dext[2 * s]);
-  d.y = R(di + dext[2 * s + 1]);
-  D[s] = d;
+  fx4<R> f;
+  f.x = R(U + ve - fn.mu);
+  f.y = R(dr + dext[2 * s]);
+  f.z = R(di + dext[2 * s + 1]);
+  f.w = R(0);
+  WD[s] = f;
 }
 
 template <typename R>
 cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
                               const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
-                              double* delta, R* W, cx<R>* D, cudaStream_t s) {
+                              double* delta, fx4<R>* WD, cudaStream_t s) {
   potentials_kernel<R><<<(M + 127) / 128, 128, 0, s>>>(part, nchunk, M, fn, vext, dext, lam, init_lam, rho, nu, U,
-                                                       delta, W, D);
+                                                       delta, WD);
   return cudaGetLastError();
 }
 template cudaError_t launch_potentials<float>(const double*, int, int, FunctionalDev, const double*, const double*,
-                                              double*, int, double*, double*, double*, double*, float*, float2*,
-                                              cudaStream_t);
+                                              double*, int, double*, double*, double*, double*, float4*, cudaStream_t);
 template cudaError_t launch_potentials<double>(const double*, int, int, FunctionalDev, const double*, const double*,
-                                               double*, int, double*, double*, double*, double*, double*, double2*,
+                                               double*, int, double*, double*, double*, double*, double4*,
                                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
@@ -252,13 +263,20 @@ __global__ void narrow_kernel(const double* __restrict__ src, cx<R>* __restrict_
   c.y = R(b);
   dst[i] = c;
 }
+// dst = sc[state] * src, the state of element i being (first + i) / per_state
 template <typename R>
-__global__ void widen_kernel(const cx<R>* __restrict__ src, double* __restrict__ dst, int64_t n) {
+__global__ void widen_kernel(const cx<R>* __restrict__ src, double* __restrict__ dst, int64_t n, const double* sc,
+                             int64_t first, int64_t per_state) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const cx<R> c = src[i];
-  dst[2 * i] = double(c.x);
-  dst[2 * i + 1] = double(c.y);
+  const double f = sc ? sc[(first + i) / per_state] : 1.0;
+  dst[2 * i] = f * double(c.x);
+  dst[2 * i + 1] = f * double(c.y);
+}
+__global__ void fill_kernel(double* p, double v, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
 }
 template <typename R>
 __global__ void to_real_kernel(const double* __restrict__ src, R* __restrict__ dst, int64_t n) {
@@ -273,9 +291,15 @@ cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t n, int* err, cu
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t n, cudaStream_t s) {
+cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t n, const double* sc, int64_t first, int64_t per_state,
+                         cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  widen_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+  widen_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n, sc, first, per_state);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  fill_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 template <typename R>
@@ -286,8 +310,10 @@ cudaError_t launch_to_real(const double* src, R* dst, int64_t n, cudaStream_t s)
 }
 template cudaError_t launch_narrow<float>(const double*, float2*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_narrow<double>(const double*, double2*, int64_t, int*, cudaStream_t);
-template cudaError_t launch_widen<float>(const float2*, double*, int64_t, cudaStream_t);
-template cudaError_t launch_widen<double>(const double2*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_widen<float>(const float2*, double*, int64_t, const double*, int64_t, int64_t,
+                                        cudaStream_t);
+template cudaError_t launch_widen<double>(const double2*, double*, int64_t, const double*, int64_t, int64_t,
+                                         cudaStream_t);
 template cudaError_t launch_to_real<float>(const double*, float*, int64_t, cudaStream_t);
 template cudaError_t launch_to_real<double>(const double*, double*, int64_t, cudaStream_t);
 

@@ -93,9 +93,10 @@ struct FunctionalDev {
 };
 
 // Partial sums over chunks of states: part[c][0..2][M] = rho, Re nu, Im nu.
+// Stored states are scaled by sc[n] (deferred normalisation).
 template <typename R>
-cudaError_t launch_density_partial(const cx<R>* phi, const R* wm, const R* wp, int64_t nstates, int M, int nchunk,
-                                   int64_t chunk, double* part, cudaStream_t s);
+cudaError_t launch_density_partial(const cx<R>* phi, const double* sc, const R* wm, const R* wp, int64_t nstates,
+                                   int M, int nchunk, int64_t chunk, double* part, cudaStream_t s);
 
 // Sum the chunk partials, build (U, Delta) with the frozen regulator lam
 // (or first compute lam by the t = 0 fixed point when init_lam), and write
@@ -103,7 +104,7 @@ cudaError_t launch_density_partial(const cx<R>* phi, const R* wm, const R* wp, i
 template <typename R>
 cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
                               const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
-                              double* delta, R* W, cx<R>* D, cudaStream_t s);
+                              double* delta, fx4<R>* WD, cudaStream_t s);
 
 // Energy terms (Sec. 3.3) from the site fields and per-state kinetic values.
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
@@ -117,7 +118,9 @@ cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice
 template <typename R>
 cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t ncomplex, int* err, cudaStream_t s);
 template <typename R>
-cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t ncomplex, cudaStream_t s);
+cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t ncomplex, const double* sc, int64_t first,
+                         int64_t per_state, cudaStream_t s);
+cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_to_real(const double* src, R* dst, int64_t n, cudaStream_t s);
 

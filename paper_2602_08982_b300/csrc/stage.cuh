@@ -21,9 +21,12 @@
 //            Taylor series of Eq. Taylor-exp); E_n = <in|H|in> is computed and
 //            stored when requested, else read; optional normalisation.
 //   MODE_EKIN    per-state <u|T|u>, <v|T|v> for the kinetic energy.
-// Per-state reductions (<H>_n, norms) are summed per thread in the working
-// precision, then across threads and CTAs in double in a fixed order, so all
-// CTAs of the cluster obtain bit-identical values.
+// Normalisation (Alg. 2 steps 2 and 8) is deferred: states are written as
+// computed and CTA 0 of the cluster stores the per-state factor 1/sqrt(norm),
+// which every consumer (the next stage, the density reduction, read-out)
+// applies on load. Per-state reductions (<H>_n, norms) are summed per thread in
+// the working precision, then across threads and CTAs in double in a fixed
+// order, so all CTAs of the cluster obtain bit-identical values.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -34,6 +37,11 @@
 namespace wslda {
 namespace cg = cooperative_groups;
 
+template <typename R> struct fx4_of;
+template <> struct fx4_of<float> { using type = float4; };
+template <> struct fx4_of<double> { using type = double4; };
+template <typename R> using fx4 = typename fx4_of<R>::type;
+
 enum Mode : int { MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, NMODES = 5 };
 
 template <typename R>
@@ -43,12 +51,14 @@ struct StageArgs {
   const cx<R>* h1;   // X: f_{k-2}                                   HORNER: base
   const cx<R>* h2;   // X: f_{k-3}
   cx<R>* h3;         // X: f_{k-4} in, c out;  Y: c in
-  const R* W;        // [M] U + V_ext - mu
-  const cx<R>* D;    // [M] Delta + Delta_ext
+  const fx4<R>* WD;  // [M] {U + V_ext - mu, Re, Im (Delta + Delta_ext), 0}
   const R* ktab;     // [NX+NY+NZ] per-slot k_d^2 * 0.5 / M
   const cx<R>* tw;   // [NX+NY+NZ] W_N^k per axis (used where a pencil spans lanes)
   double* E;         // HORNER: per-state shift (written when compute_e)
   double* out2;      // EKIN: [n][2] <u|T|u>, <v|T|v>
+  const double* sc_in;    // [n] scale of the input states (true phi = sc_in * stored)
+  const double* sc_base;  // HORNER: [n] scale of the base states
+  double* sc_out;         // [n] scale of the written states (normalising modes), else 1
   int* err;          // error word: bit 0 non-finite norm
   double dt;
   double dV;
@@ -292,25 +302,31 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   cp_async_wait_all();
   __syncthreads();
 
-  // <H>_n, potential part: sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v), from the slab
+  // Prologue sweep over the slab: apply the input scale (deferred
+  // normalisation) and accumulate the potential part of <H>_n,
+  // sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v).
   const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
+  const R sin_ = R(a.sc_in[n]);
   R ep = 0, ec = 0;  // compensated partial sum
-  if (need_e) {
-    for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
-      R w[U];
-      C d[U];
+  for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
+    fx4<R> wd[U];
+    if (need_e) {
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
-        if (s < G::NS) { w[k] = a.W[gs0 + s]; d[k] = a.D[gs0 + s]; }
+        if (s < G::NS) wd[k] = a.WD[gs0 + s];
       }
+    }
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int s = s0 + k * G::BT;
-        if (s < G::NS) {
-          const C u = buf[sidx(s)], v = buf[G::SLAB + sidx(s)];
-          const C dv = mul(d[k], v);
-          const R t = (w[k] * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
+    for (int k = 0; k < U; ++k) {
+      const int s = s0 + k * G::BT;
+      if (s < G::NS) {
+        const C u = scl(buf[sidx(s)], sin_), v = scl(buf[G::SLAB + sidx(s)], sin_);
+        buf[sidx(s)] = u;
+        buf[G::SLAB + sidx(s)] = v;
+        if (need_e) {
+          const C dv = mul(mk<C>(wd[k].y, wd[k].z), v);
+          const R t = (wd[k].x * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
           const R ns = ep + t;
           ec = (ns - ep) - t;
           ep = ns;
@@ -378,10 +394,12 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
     const bool norm_out = MODE == MODE_X || MODE == MODE_Y || (MODE == MODE_HORNER && a.normalize);
     C* dst = (MODE == MODE_HORNER || MODE == MODE_F) ? a.h0 + sbase : a.phi + sbase;
     const R dt = R(a.dt);
-    // one pointwise sweep: H phi on the fly, f = -i (H - <H>_n) phi, integrator
+    const R sbase_ = MODE == MODE_HORNER ? R(a.sc_base[n]) : R(1);
+    // one pointwise sweep: H phi on the fly, f = -i (H - <H>_n) phi, integrator;
+    // results go straight to global memory (normalisation deferred)
     for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
-      C u[U], v[U], d[U], x1[2][U], x2[2][U], x3[2][U];
-      R w[U];
+      C u[U], v[U], x1[2][U], x2[2][U], x3[2][U];
+      fx4<R> wd[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
@@ -389,8 +407,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
           const int g = gs0 + s;
           u[k] = in[g];
           v[k] = in[G::M + g];
-          w[k] = a.W[g];
-          d[k] = a.D[g];
+          wd[k] = a.WD[g];
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
@@ -406,11 +423,14 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
         if (s < G::NS) {
           const int g = gs0 + s;
           const int b = sidx(s);
+          const C uu = scl(u[k], sin_), vv = scl(v[k], sin_);
+          const R w = wd[k].x;
+          const C d = mk<C>(wd[k].y, wd[k].z);
           // (H - <H>_n) phi for both components (Eq. dpsidt-Hpsi, A = 1)
           C hm[2];
-          hm[0] = sub(add(add(buf[b], scl(u[k], w[k])), mul(d[k], v[k])), scl(u[k], Er));
-          hm[1] = sub(sub(sub(mulc(u[k], d[k]), buf[G::SLAB + b]), scl(v[k], w[k])), scl(v[k], Er));
-          const C ph[2] = {u[k], v[k]};
+          hm[0] = sub(add(add(buf[b], scl(uu, w)), mul(d, vv)), scl(uu, Er));
+          hm[1] = sub(sub(sub(mulc(uu, d), buf[G::SLAB + b]), scl(vv, w)), scl(vv, Er));
+          const C ph[2] = {uu, vv};
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
@@ -428,35 +448,45 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
             } else if constexpr (MODE == MODE_F) {
               res = mul_mi(hm[c]);
             } else {  // HORNER: out = base + coef (H - E) in
-              res = add(x1[c][k], mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm[c]));
+              res = add(scl(x1[c][k], sbase_), mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm[c]));
             }
+            dst[c * G::M + g] = res;
             if (norm_out) {
-              buf[c * G::SLAB + b] = res;
               const R t = (res.x * res.x + res.y * res.y) - nc;
               const R ns = np + t;
               nc = (ns - np) - t;
               np = ns;
-            } else {
-              dst[c * G::M + g] = res;
             }
           }
         }
       }
     }
+    // Norm partials ride on the closing cluster barrier; CTA 0 stores the
+    // per-state factor 1/sqrt(norm) (1 for outputs that are not normalised).
     if (norm_out) {
-      // the closing cluster barrier overlaps the scaled stores
-      const double nrm = cluster_sum<G, true>(double(np), red, cl) * a.dV;
-      if (!(nrm > 0.0) || !isfinite(nrm)) {
-        if (tid == 0) atomicOr(a.err, 1);
+      double v = double(np);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) red[G::RED_WB + (tid >> 5)] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
+        double* dst_n = cl.map_shared_rank(red + G::RED_N, 0);
+        dst_n[rank] = t;
       }
-      const R sc = R(1.0 / sqrt(nrm));
-      for (int e = tid; e < 2 * G::NS; e += G::BT) {
-        const int comp = e >= G::NS, s = e - comp * G::NS;
-        dst[comp * G::M + gs0 + s] = scl(buf[comp * G::SLAB + sidx(s)], sc);
+    }
+    cl.sync();  // also keeps CTA 0's slots readable until every CTA has read them
+    if (rank == 0 && tid == 0 && a.sc_out) {
+      if (norm_out) {
+        double t = 0.0;
+        for (int r = 0; r < G::CS; ++r) t += red[G::RED_N + r];
+        const double nrm = t * a.dV;
+        if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(a.err, 1);
+        a.sc_out[n] = 1.0 / sqrt(nrm);
+      } else {
+        a.sc_out[n] = 1.0;
       }
-      cluster_wait();
-    } else {
-      cl.sync();  // CTA 0's slot stays readable until every CTA has read it
     }
   }
 }
