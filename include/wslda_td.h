@@ -184,6 +184,26 @@ wslda_status wslda_uniform_solve(const wslda_lattice* lat, const wslda_functiona
  * Weights are set to T = 0. Replaces wslda_load_states. */
 wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, double delta, const int64_t* kidx);
 
+/* Densities rho [M] and nu [M complex] of device-resident states, without any
+ * device allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc, such as code whose device memory is all
+ * owned by its own pool allocator, or code on a latency-critical path where
+ * cudaMalloc (which can synchronise the device and can fail) is not acceptable.
+ *  - uv: device pointer to [nstates][2][M] complex, float2 elements for
+ *    WSLDA_MIXED and double2 for WSLDA_FP64; w_minus / w_plus: device [nstates]
+ *    doubles or NULL (T = 0: 1 and 0); rho, nu: device outputs (nu interleaved).
+ *  - Scratch is a fixed 16 MiB device array inside the library (every GPU that
+ *    loads the library holds it until the process exits); lattices with more
+ *    than 699050 sites (3 M > 2^21 doubles) are rejected with WSLDA_ENOMEM.
+ *  - The first call on a device resolves that array's device address (a
+ *    one-time set-up); make that first call before any stream capture.
+ *  - The work is queued on `stream` (a cudaStream_t, NULL = default stream)
+ *    and the call returns without waiting. All calls share the one scratch
+ *    array, so calls that overlap on the GPU (other streams, other threads)
+ *    race and give wrong results; serialise them. */
+wslda_status wslda_densities_noalloc(int precision, const void* uv, const double* w_minus, const double* w_plus,
+                                     int64_t nstates, int nx, int ny, int nz, double* rho, double* nu, void* stream);
+
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
  * the context's stream and its duration is added to the kernel's total.
  * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction,

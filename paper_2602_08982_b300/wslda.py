@@ -81,6 +81,7 @@ def _load():
         "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
         "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
         "wslda_get_variant": (I, [P, I, ct.c_char_p, I]),
+        "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -106,6 +107,18 @@ def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4p
     if st:
         raise WsldaError(st, "uniform_solve found no solution or got bad arguments")
     return {k: getattr(out, k) for k, _ in Uniform._fields_}
+
+
+def densities_noalloc(precision: int, uv, rho, nu, shape, w_minus=None, w_plus=None, stream: int = 0):
+    """rho and nu of device states into device outputs without any device
+    allocation (wslda_densities_noalloc). All arguments are torch CUDA tensors;
+    the work is queued on `stream` and not waited for."""
+    ptr = lambda t: ct.c_void_p(t.data_ptr()) if t is not None else None
+    st = lib.wslda_densities_noalloc(int(precision), ptr(uv), ptr(w_minus), ptr(w_plus), int(uv.shape[0]),
+                                     int(shape[0]), int(shape[1]), int(shape[2]), ptr(rho), ptr(nu),
+                                     ct.c_void_p(stream))
+    if st:
+        raise WsldaError(st, "wslda_densities_noalloc failed")
 
 
 def _ptr(a, dtype, on_device: bool):
