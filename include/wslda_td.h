@@ -3,7 +3,7 @@
  *
  * The library advances every quasiparticle pair (u_n, v_n) of one or more
  * periodic 3D boxes with the modified equation of motion
- *     i d(phi_n)/dt = [H - <H>_n] phi_n                (Sec. 3.4, Eq. shorttdproblem-mod)
+ *     i d(phi_n)/dt = [H - <H>_n] phi_n                (Sec. 3.3, Eq. shorttdproblem-mod)
  * using the AB4AM5 predictor-corrector of Alg. 2, the kinetic term through
  * FFTs (Eq. derivative-spectral, A_sigma = 1 so only the Laplacian, Eq. h_sigma_A1),
  * the densities rho, nu summed over all states (Eqs. nab3D..jab3D, spin
@@ -85,7 +85,7 @@ typedef struct {
   double rho_floor;
 } wslda_functional;
 
-/* Energy terms of Sec. 3.3 for A = 1. e_total is their sum; the evolution
+/* Energy terms of Sec. 3.2 for A = 1. e_total is their sum; the evolution
  * conserves e_total - mu * n_part (Eq. E_tot). */
 typedef struct {
   double e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part;
@@ -117,7 +117,7 @@ wslda_status wslda_set_dext(wslda_ctx* ctx, int box, const double* dext, int on_
 wslda_status wslda_load_states(wslda_ctx* ctx, int box, const double* uv, const double* w_minus,
                                const double* w_plus, int on_device);
 
-/* Prepare the integrator for every box (Sec. 3.4, start-up). Computes the
+/* Prepare the integrator for every box (Sec. 3.3, start-up). Computes the
  * densities, freezes the regulator Lambda_c at its t = 0 value, then either
  * assumes a stationary state (stationary = 1: f_{k-2..k-4} = 0) or runs three
  * Taylor predictor-corrector steps of order 5 (Eq. Taylor-exp), which advance
@@ -139,7 +139,7 @@ wslda_status wslda_get_densities(wslda_ctx* ctx, int box, double* rho, double* n
  * (without Delta_ext). Host pointers. */
 wslda_status wslda_get_fields(wslda_ctx* ctx, int box, double* U, double* delta);
 
-/* Energy terms of the current states (Sec. 3.3). */
+/* Energy terms of the current states (Sec. 3.2). */
 wslda_status wslda_get_energy(wslda_ctx* ctx, int box, wslda_energy* out);
 
 /* Diagnostic: f(phi) = -i [H - <H>_n] phi (Eq. ABM-f) of the current states
@@ -162,7 +162,7 @@ wslda_status wslda_get_time(wslda_ctx* ctx, double* t, int64_t* steps);
 /* Device bytes held by the context. */
 int64_t wslda_memory_bytes(const wslda_ctx* ctx);
 
-/* Uniform (plane-wave) BCS solution on the lattice k-set (Sec. 5, "inittype 0";
+/* Uniform (plane-wave) BCS solution on the lattice k-set (Sec. 5.2.1, "inittype 0";
  * reduced 2x2 problem of Eq. HpsiEpsi). With u_k, v_k = (U_k, V_k) e^{ik.r}/sqrt(V),
  * xi_k = k^2/2 - mu_eff, E_k = sqrt(xi_k^2 + Delta^2) over all M lattice k:
  *  - the number equation (1/V) sum_k V_k^2 = rho_sigma fixes mu_eff = mu - U;

@@ -134,7 +134,7 @@ def derivative_matrix_1d(n: int, d: float, order: int) -> np.ndarray:
 
 
 def dense_laplacian(lat: Lattice) -> np.ndarray:
-    """M x M Laplacian assembled from Eq. D2 along each axis (Sec. 3.3, matrix form)."""
+    """M x M Laplacian assembled from Eq. D2 along each axis (Sec. 3.2, matrix form)."""
     Dx = derivative_matrix_1d(lat.nx, lat.dx, 2)
     Dy = derivative_matrix_1d(lat.ny, lat.dy, 2)
     Dz = derivative_matrix_1d(lat.nz, lat.dz, 2)
@@ -294,7 +294,7 @@ def kinetic_current_densities(phi, w_minus, w_plus, lat: Lattice):
 
 
 # ----------------------------------------------------------------------------
-# Hamiltonian application and ABM right-hand side (Sec. 3.4)
+# Hamiltonian application and ABM right-hand side (Sec. 3.3)
 # ----------------------------------------------------------------------------
 @dataclass
 class Fields:
@@ -381,7 +381,7 @@ class TDSystem:
         return rhs_f(phi, self.fields(phi), self.lat)
 
     def energy(self, phi) -> dict:
-        """Energy terms of Sec. 3.3 for A = 1 (reading E1: the kinetic term uses
+        """Energy terms of Sec. 3.2 for A = 1 (reading E1: the kinetic term uses
         the same Laplacian as H, via sum_n w <v|-lap|v>). The quantity the
         evolution conserves is e_total - mu * n_part (Eq. E_tot)."""
         lat, fn = self.lat, self.fn
@@ -453,7 +453,7 @@ def taylor_series(phi0, F: Fields, shift, h: float, r: int, lat: Lattice):
 
 
 def taylor_step(sys: TDSystem, phi, dt: float, r: int = 5):
-    """Predictor-corrector Taylor step (Sec. 3.4, Eq. Taylor-exp).
+    """Predictor-corrector Taylor step (Sec. 3.3, Eq. Taylor-exp).
 
     Reading T1: the series uses the shifted operator H - <H>_n of the ABM
     equations, the shift being the expectation value of that sub-step's H in
@@ -469,7 +469,7 @@ def taylor_step(sys: TDSystem, phi, dt: float, r: int = 5):
 
 
 def start(sys: TDSystem, phi0, dt: float, stationary: bool, r: int = 5) -> ABMState:
-    """ABM start-up (Sec. 3.4).
+    """ABM start-up (Sec. 3.3).
 
     stationary: reading S1, f_{k-2..k-4} = 0 and f_{k-1} = f(phi_0) (zero for an
     exact stationary state). Otherwise reading T2/T3: three Taylor steps give
@@ -495,7 +495,7 @@ def evolve(sys: TDSystem, st: ABMState, dt: float, nsteps: int) -> ABMState:
 
 
 # ----------------------------------------------------------------------------
-# Uniform systems (Sec. 5 "inittype 0"): lattice seeds and continuum checks
+# Uniform systems (Sec. 5.2.1 "inittype 0"): lattice seeds and continuum checks
 # ----------------------------------------------------------------------------
 def bcs_amplitudes(xi, delta):
     """U_k, V_k of the 2x2 problem [[xi, D], [D, -xi]] at E_k = sqrt(xi^2 + D^2) > 0."""

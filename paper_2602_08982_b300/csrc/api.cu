@@ -352,7 +352,7 @@ wslda_status taylor_series(wslda_ctx* c, Box& b, int phi_slot, int out_slot, dou
   return WSLDA_OK;
 }
 
-// Predictor-corrector Taylor step of Sec. 3.4 (order r = 5).
+// Predictor-corrector Taylor step of Sec. 3.3 (order r = 5).
 template <typename R>
 wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
   const int y = b.ih[0];

@@ -1,6 +1,6 @@
 // Site-major kernels: density reduction over states (spin-symmetric, frozen
 // weights: Eqs. nab3D.., Sec. 2.5), potentials from the SLDA / BdG functional
-// with the regularised coupling (Sec. 2.4, Eq. Creg), energy terms (Sec. 3.3),
+// with the regularised coupling (Sec. 2.4, Eq. Creg), energy terms (Sec. 3.2),
 // and precision conversions at the ABI boundary.
 #include <cuda_runtime.h>
 
@@ -200,7 +200,7 @@ template cudaError_t launch_potentials<double>(const double*, int, int, Function
                                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Energy (Sec. 3.3, A = 1): one block, fixed-order tree sums in double.
+// Energy (Sec. 3.2, A = 1): one block, fixed-order tree sums in double.
 // out8 = e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) energy_kernel(int M, int64_t nstates, FunctionalDev fn,

@@ -106,7 +106,7 @@ cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalD
                               const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
                               double* delta, fx4<R>* WD, cudaStream_t s);
 
-// Energy terms (Sec. 3.3) from the site fields and per-state kinetic values.
+// Energy terms (Sec. 3.2) from the site fields and per-state kinetic values.
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
                           const double* delta, const double* vext, const double* dext, const double* ekin2,
                           const double* wm, const double* wp, double dV, double* out8, cudaStream_t s);

@@ -1,4 +1,4 @@
-// Uniform BCS solution on the lattice k-set (Sec. 5, "inittype 0": the
+// Uniform BCS solution on the lattice k-set (Sec. 5.2.1, "inittype 0": the
 // default initial state of the toolkit) and the device kernel that writes its
 // plane-wave quasiparticle states.
 #include <cuda_runtime.h>

@@ -36,7 +36,7 @@ def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
 
 def centered_coords(shape, spacing=(1.0, 1.0, 1.0)):
     """Site coordinates x = dx (i - N/2) per axis, broadcastable to the lattice
-    (the convention of the paper's custom-initialisation example, Sec. 5)."""
+    (the convention of the paper's custom-initialisation example, Sec. 5.2.1)."""
     out = []
     for ax, (n, d) in enumerate(zip(shape, spacing)):
         c = d * (np.arange(n, dtype=np.float64) - n // 2)

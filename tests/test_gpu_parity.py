@@ -118,7 +118,7 @@ def test_mixed_elongated_vortex(W):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_uniform_seed_is_stationary_16cubed(W, prec):
     """All 4096 plane-wave states of the self-consistent uniform SLDA seed:
-    f vanishes and the states do not move (Sec. 3.4)."""
+    f vanishes and the states do not move (Sec. 3.3)."""
     case = make_case((16, 16, 16), seed=9)
     ctx, box = gpu_context(case, prec)
     f = ctx.eval_f(box)

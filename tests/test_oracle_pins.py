@@ -188,7 +188,7 @@ def test_uniform_states_orthonormal(dims):
 
 @pytest.mark.parametrize("kind", ["slda", "bdg"])
 def test_uniform_state_is_stationary(kind):
-    """Sec. 3.4: the self-consistent static solution gives f = 0 (the modified
+    """Sec. 3.3: the self-consistent static solution gives f = 0 (the modified
     equation removes the phase), so an ABM step leaves it unchanged."""
     lat = o.Lattice(6, 6, 6) if kind == "slda" else o.Lattice(8, 8, 8)
     if kind == "slda":
