@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--batched", action="store_true",
+                   help="also time the batched workload: 64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -61,6 +63,25 @@ def parse():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def stage_source_hash() -> str:
+    """git blob hash of the stage-kernel source (computed without git)."""
+    import hashlib
+    data = open(os.path.join(ROOT, "paper_2602_08982_b300", "csrc", "stage.cuh"), "rb").read()
+    return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per state-site of stage X from the committed ncu summary, if
+    that capture was taken on the current stage-kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "stage_x_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = dict(line.split("=", 1) for line in open(path).read().split() if "=" in line)
+    if kv.get("stage_cuh_blob") != stage_source_hash():
+        return None
+    return float(kv["mixed_bytes_per_state_site"])
 
 
 def measured_peaks():
@@ -164,8 +185,10 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     if prec == 1:
         peak, which = measured_peaks()
         achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
+        tb = profiled_traffic()
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
+                "traffic": None if tb is None else tb * per_launch,
+                "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
                 "peak_source": which, "algorithmic_bytes_per_state_site": bx}
     else:
         achieved = fx * per_launch / (x_avg * 1e-3) / 1e12
@@ -217,6 +240,58 @@ def run_e2e(W, torch, args, shape, world):
             "h2d_bytes_per_step": nbytes / args.steps,
             "d2h_bytes_per_step": (nbytes + args.steps * 24 * M) / args.steps,
             "includes": "load_states from pinned host, Taylor start, K steps each with a density read, final get_states"}
+
+
+def batched_boxes(max_gb=240.0, first_seed=4):
+    """Box sides for the batched workload: 64 cubic boxes drawn from
+    {12, 16, 18, 20, 24}; a draw whose five complex64 buffers exceed max_gb is
+    rejected and redrawn with the next seed."""
+    from paper_2602_08982_b300 import inputs
+    seed = first_seed
+    while True:
+        sides = inputs.draw_box_sides(64, seed)
+        if sum(n ** 6 for n in sides) * 80 / 1e9 <= max_gb:
+            return seed, sides
+        seed += 1
+
+
+def run_batched(W, torch, args):
+    from paper_2602_08982_b300 import inputs
+    seed, sides = batched_boxes()
+    inv_kfa = inputs.draw_inv_kfa(64, 1004)
+    stream = torch.cuda.current_stream()
+    ctx = W.Context(W.MIXED, stream=stream.cuda_stream)
+    units = 0.0
+    for i, (n, ik) in enumerate(zip(sides, inv_kfa)):
+        shape = (n, n, n)
+        ia = float(ik) / (4 * math.pi)
+        u = W.uniform_solve(shape, kind=W.BDG, inv_4pi_a=ia, rho_sigma=RHO_SIGMA)
+        b = ctx.add_box(shape, kind=W.BDG, inv_4pi_a=ia, mu=u["mu"], nstates=n ** 3)
+        ctx.set_dext(b, inputs.pairing_kick(shape, 5000 + i, 1e-3 * u["delta"]))
+        ctx.fill_uniform_states(b, u["mu_eff"], u["delta"])
+        units += float(n ** 3) ** 2
+    ctx.set_graph(True, 4)
+    ctx.start(False, args.dt)
+    steps = max(4, 4 * (args.steps // 4))
+    ctx.step(args.dt, 4)                      # warm-up (also captures the graphs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    value = units * steps / (ms * 1e-3)
+    peak, which = measured_peaks()
+    step_gbs = 160.0 * units / (ms / steps * 1e-3) / 1e9
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "boxes": 64,
+            "box_sides_seed": seed, "box_sides": sides, "state_sites_per_step": units,
+            "config": "64 cubic boxes 12^3..24^3 (all states), BdG 1/(kF a) uniform in [-1, 1), 1e-3 pairing "
+                      "kick per box, complex64, boxes on 4 forked streams, 4 steps per CUDA graph",
+            "step_roofline": {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                              "frac": step_gbs / peak, "peak_source": which,
+                              "algorithmic_bytes_per_state_site": 160, "scope": "whole step (10 state passes)"}}
 
 
 # ------------------------------------------------------------------ oracle (CPU)
@@ -330,6 +405,7 @@ def main():
     if args.precision in ("both", "fp64"):
         arms["fp64"] = run_arm(W, torch, W.FP64, args, shape, rank, world, local)
     e2e = None if args.no_e2e else run_e2e(W, torch, args, shape, world)
+    batched = run_batched(W, torch, args) if args.batched else None
     main_arm = arms.get("mixed") or arms["fp64"]
     line = {"metric": METRIC, "value": main_arm["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_arm["ms_per_step"], "higher_is_better": True,
@@ -350,6 +426,8 @@ def main():
             "after_steps": 3 + args.warmup + args.steps}
     if e2e:
         line["e2e"] = e2e
+    if batched:
+        line["batched"] = batched
     if cpu:
         line["cpu_baseline"] = cpu
     if rank == 0:

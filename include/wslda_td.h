@@ -142,6 +142,12 @@ wslda_status wslda_get_fields(wslda_ctx* ctx, int box, double* U, double* delta)
 /* Energy terms of the current states (Sec. 3.2). */
 wslda_status wslda_get_energy(wslda_ctx* ctx, int box, wslda_energy* out);
 
+/* Conservation diagnostics of the TD codes (Sec. 4.5.1): relative drift of
+ * E_tot - mu N (Eq. E_tot) and of N since wslda_start, for one box. Returns
+ * WSLDA_EDRIFT (sticky, like every error) when either exceeds its tolerance;
+ * de / dn (nullable) receive the drifts. */
+wslda_status wslda_check_conservation(wslda_ctx* ctx, int box, double e_tol, double n_tol, double* de, double* dn);
+
 /* Diagnostic: f(phi) = -i [H - <H>_n] phi (Eq. ABM-f) of the current states
  * with potentials from their densities, [n][2][M] complex double on the host. */
 wslda_status wslda_eval_f(wslda_ctx* ctx, int box, double* f);
@@ -150,6 +156,13 @@ wslda_status wslda_eval_f(wslda_ctx* ctx, int box, double* f);
  * time and step counter) to a file; resuming is bit-identical. */
 wslda_status wslda_save(wslda_ctx* ctx, const char* path);
 wslda_status wslda_load(wslda_ctx* ctx, const char* path);
+
+/* Batched execution of many boxes: when enabled, box i of a step runs on
+ * forked stream i mod nstreams (nstreams <= 0: 4) so that independent boxes
+ * overlap, and wslda_step replays every four steps as one captured CUDA
+ * graph (one graph per history-slot phase and dt; per-kernel profiling falls
+ * back to direct launches). Results are identical to direct execution. */
+wslda_status wslda_set_graph(wslda_ctx* ctx, int enable, int nstreams);
 
 /* Launch variant (cluster size, threads, lanes per pencil) the autotuner chose
  * for the box's stage kernels at wslda_start, as text. Setting the environment

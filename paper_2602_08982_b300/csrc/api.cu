@@ -58,6 +58,7 @@ struct Box {
   double* Ebuf = nullptr;
   double* ekin2 = nullptr;
   double* out8 = nullptr;
+  double e0 = 0.0, n0 = 0.0;  // E_tot - mu N and N of the states at wslda_start
   bool loaded = false;
   void* ptr(int i) const { return slot[i]; }
 };
@@ -66,7 +67,16 @@ struct Box {
 
 struct wslda_ctx {
   int prec = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the caller's stream
+  cudaStream_t cur = nullptr;     // stream the box-level launches go to (stream, or a forked one)
+  // batched execution: boxes spread over forked streams, four steps captured
+  // in one CUDA graph per history-slot phase (the rotation has period 4)
+  bool use_graph = false;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
+  double graph_dt = 0.0;
   std::vector<Box> boxes;
   std::string err;
   int status = WSLDA_OK;
@@ -176,8 +186,8 @@ int brev_host(int j, int T) {
 
 // Kinetic symbol per slot along one axis: slot s = j + T m holds frequency
 // m + N1 brev(j) after the forward pencil transform (identity for T = 1).
-void axis_tables(int N, int T, double d, double scale, std::vector<double>& k2, std::vector<double>& twr,
-                 std::vector<double>& twi) {
+void axis_tables(int N, int T, double d, double scale, std::vector<double>& k2, std::vector<double>& k1,
+                 std::vector<double>& twr, std::vector<double>& twi) {
   const int N1 = N / T;
   const long double L = (long double)N * d;
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -186,6 +196,8 @@ void axis_tables(int N, int T, double d, double scale, std::vector<double>& k2, 
     const int f = m + N1 * brev_host(j, T);
     const long double k = (f < N / 2) ? 2 * pi * f / L : 2 * pi * (f - N) / L;
     k2.push_back(double(k * k) * scale);
+    // first derivative symbol k / M, the Nyquist mode zeroed (Eq. derivative-spectral, odd r)
+    k1.push_back(f == N / 2 ? 0.0 : double(k) * 2.0 * scale);
     twr.push_back(double(cosl(2 * pi * s / N)));
     twi.push_back(double(-sinl(2 * pi * s / N)));
   }
@@ -214,12 +226,12 @@ struct ProfScope {
     if (c->prof) {
       a = take_event(c);
       b = take_event(c);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, c->cur);
     }
   }
   ~ProfScope() {
     if (c->prof) {
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, c->cur);
       c->pending.push_back({kind, {a, b}});
     }
   }
@@ -259,7 +271,7 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
   ProfScope ps(c, kind);
-  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), c->stream));
+  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), c->cur));
   return WSLDA_OK;
 }
 
@@ -271,13 +283,13 @@ wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
     CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), b.sc[islot],
                                           static_cast<const R*>(b.wm_r),
                                           static_cast<const R*>(b.wp_r), b.n, b.M, b.nchunk, b.chunk, b.part,
-                                          c->stream));
+                                          c->cur));
   } else {
-    CUDA_TRY(c, cudaMemsetAsync(b.part, 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(b.part, 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->cur));
   }
   ProfScope ps2(c, PROF_POT);
   CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu, b.U,
-                                   b.delta, static_cast<fx4<R>*>(b.WD), c->stream));
+                                   b.delta, static_cast<fx4<R>*>(b.WD), c->cur));
   return WSLDA_OK;
 }
 
@@ -425,10 +437,33 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   return WSLDA_OK;
 }
 
+// Energy terms of the current states into h[0..6] (fields must be current).
+template <typename R>
+wslda_status compute_energy(wslda_ctx* c, Box& b, double* h) {
+  StageArgs<R> a = base_args<R>(b, box_dV(b));
+  a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
+  a.sc_in = b.sc[b.iphi];
+  c->cur = c->stream;
+  wslda_status st = launch_mode<R>(c, b, MODE_EKIN, a, PROF_AUX);
+  if (st) return st;
+  CUDA_TRY(c, launch_energy(b.M, b.n, b.fdev, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp, box_dV(b),
+                            b.out8, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h, b.out8, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
 template <typename R>
 wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
   wslda_status st;
   if ((st = refresh_fields(c, b, b.iphi, 1))) return st;
+  {
+    // reference values of the conservation diagnostics (Sec. 4.5.1)
+    double h[8];
+    if ((st = compute_energy<R>(c, b, h))) return st;
+    b.e0 = h[5] - b.fn.mu * h[6];
+    b.n0 = h[6];
+  }
   if ((st = autotune_box<R>(c, b, dt))) return st;
   const size_t bytes = size_t(b.n) * 2 * b.M * b.csize;
   if (stationary) {
@@ -446,23 +481,93 @@ wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
 }
 
 template <typename R>
+wslda_status step_box(wslda_ctx* c, Box& b, double dt) {
+  wslda_status st;
+  if ((st = stage_x<R>(c, b, dt))) return st;
+  if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
+  if ((st = stage_y<R>(c, b, dt))) return st;
+  if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
+  // Alg. 2 steps 5-7: the slot that held c becomes the slot for the next f_{k-1}
+  const int freed = b.ih[3];
+  b.ih[3] = b.ih[2];
+  b.ih[2] = b.ih[1];
+  b.ih[1] = b.ih[0];
+  b.ih[0] = freed;
+  return WSLDA_OK;
+}
+
+// One AB4AM5 step of every box. With several boxes and batched execution on,
+// box i runs on forked stream i mod K so that independent boxes overlap.
+template <typename R>
 wslda_status step_all(wslda_ctx* c, double dt) {
   wslda_status st;
-  for (Box& b : c->boxes)
-    if ((st = stage_x<R>(c, b, dt))) return st;
-  for (Box& b : c->boxes)
-    if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
-  for (Box& b : c->boxes)
-    if ((st = stage_y<R>(c, b, dt))) return st;
-  for (Box& b : c->boxes) {
-    if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
-    // Alg. 2 steps 5-7: the slot that held c becomes the slot for the next f_{k-1}
-    const int freed = b.ih[3];
-    b.ih[3] = b.ih[2];
-    b.ih[2] = b.ih[1];
-    b.ih[1] = b.ih[0];
-    b.ih[0] = freed;
+  const bool fork = c->use_graph && c->boxes.size() > 1 && !c->side.empty();
+  if (!fork) {
+    c->cur = c->stream;
+    for (Box& b : c->boxes)
+      if ((st = step_box<R>(c, b, dt))) return st;
+    return WSLDA_OK;
   }
+  CUDA_TRY(c, cudaEventRecord(c->fork_ev, c->stream));
+  for (cudaStream_t s : c->side) CUDA_TRY(c, cudaStreamWaitEvent(s, c->fork_ev, 0));
+  for (size_t i = 0; i < c->boxes.size(); ++i) {
+    c->cur = c->side[i % c->side.size()];
+    if ((st = step_box<R>(c, c->boxes[i], dt))) {
+      c->cur = c->stream;
+      return st;
+    }
+  }
+  c->cur = c->stream;
+  for (size_t k = 0; k < c->side.size(); ++k) {
+    CUDA_TRY(c, cudaEventRecord(c->join_ev[k], c->side[k]));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
+  }
+  return WSLDA_OK;
+}
+
+void drop_graphs(wslda_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  c->graphs.clear();
+}
+
+std::vector<int> slot_phase(const wslda_ctx* c) {
+  std::vector<int> key;
+  for (const Box& b : c->boxes) {
+    key.push_back(b.iphi);
+    for (int i = 0; i < 4; ++i) key.push_back(b.ih[i]);
+  }
+  return key;
+}
+
+// Four steps captured once per slot phase and dt, replayed as one graph launch.
+template <typename R>
+wslda_status step_graph4(wslda_ctx* c, double dt) {
+  if (c->graph_dt != dt) {
+    drop_graphs(c);
+    c->graph_dt = dt;
+  }
+  const std::vector<int> key = slot_phase(c);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : c->graphs)
+    if (g.first == key) exec = g.second;
+  if (!exec) {
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    wslda_status st = WSLDA_OK;
+    for (int k = 0; k < 4 && !st; ++k) st = step_all<R>(c, dt);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(c, WSLDA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, WSLDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->graphs.push_back({key, exec});
+    // capture advanced the host-side slot rotation by four steps, back to `key`
+  }
+  CUDA_TRY(c, cudaGraphLaunch(exec, c->stream));
   return WSLDA_OK;
 }
 
@@ -501,6 +606,7 @@ wslda_status wslda_create(int precision, void* stream, wslda_ctx** out) {
   wslda_ctx* c = new wslda_ctx();
   c->prec = precision;
   c->stream = static_cast<cudaStream_t>(stream);
+  c->cur = c->stream;
   void* p = nullptr;
   cudaError_t e = dalloc(c, &p, sizeof(int));
   if (e != cudaSuccess) {
@@ -523,6 +629,10 @@ void wslda_destroy(wslda_ctx* c) {
     cudaEventDestroy(p.second.second);
   }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  drop_graphs(c);
+  for (cudaStream_t s : c->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : c->join_ev) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   delete c;
 }
 
@@ -564,12 +674,12 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.fdev.ec = fn->ec > 0 ? fn->ec : default_cutoff(*lat);
   b.fdev.rho_floor = fn->rho_floor > 0 ? fn->rho_floor : 1e-12;
   const int sites_blocks = int((M + 255) / 256);
-  b.nchunk = int(std::max<int64_t>(1, std::min<int64_t>({256, (4 * 148 + sites_blocks - 1) / sites_blocks,
+  b.nchunk = int(std::max<int64_t>(1, std::min<int64_t>({256, (16 * 148 + sites_blocks - 1) / sites_blocks,
                                                           std::max<int64_t>(1, nstates / 16)})));
   b.chunk = std::max<int64_t>(1, (nstates + b.nchunk - 1) / b.nchunk);
 
   const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
-  const size_t field_bytes = size_t(M) * (8 * 9 + rsize * 4) + size_t(3) * M * 8 * b.nchunk +
+  const size_t field_bytes = size_t(M) * (8 * 13 + rsize * 4) + size_t(4) * M * 8 * b.nchunk +
                              size_t(nstates) * (8 * 10 + rsize * 2) + 4096;
   const size_t need = 5 * state_bytes + field_bytes;
   size_t freeb = 0, totalb = 0;
@@ -605,13 +715,13 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.WD, 4 * M * rsize);
   for (int i = 0; i < 5; ++i) ALLOC(b.sc[i], std::max<int64_t>(nstates, 1) * 8);
   const int naxis = lat->nx + lat->ny + lat->nz;
-  ALLOC(b.ktab, naxis * rsize);
+  ALLOC(b.ktab, 2 * naxis * rsize);
   ALLOC(b.tw, 2 * naxis * rsize);
   ALLOC(b.wm, std::max<int64_t>(nstates, 1) * 8);
   ALLOC(b.wp, std::max<int64_t>(nstates, 1) * 8);
   ALLOC(b.wm_r, std::max<int64_t>(nstates, 1) * rsize);
   ALLOC(b.wp_r, std::max<int64_t>(nstates, 1) * rsize);
-  ALLOC(b.part, size_t(3) * M * 8 * b.nchunk);
+  ALLOC(b.part, size_t(4) * M * 8 * b.nchunk);
   ALLOC(b.Ebuf, std::max<int64_t>(nstates, 1) * 8);
   ALLOC(b.ekin2, std::max<int64_t>(nstates, 1) * 16);
   ALLOC(b.out8, 8 * 8);
@@ -620,26 +730,29 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   CUDA_TRY_NEG(c, cudaMemsetAsync(b.dext, 0, 2 * M * 8, c->stream));
 
   // kinetic symbol k_d^2 * 0.5 / M per slot (1/M folds in the unnormalised inverse FFT)
-  std::vector<double> k2, twr, twi;
+  std::vector<double> k2, k1, twr, twi;
   const double scale = 0.5 / double(M);
-  axis_tables(lat->nx, ks->tx, lat->dx, scale, k2, twr, twi);
-  axis_tables(lat->ny, ks->ty, lat->dy, scale, k2, twr, twi);
-  axis_tables(lat->nz, ks->tz, lat->dz, scale, k2, twr, twi);
+  axis_tables(lat->nx, ks->tx, lat->dx, scale, k2, k1, twr, twi);
+  axis_tables(lat->ny, ks->ty, lat->dy, scale, k2, k1, twr, twi);
+  axis_tables(lat->nz, ks->tz, lat->dz, scale, k2, k1, twr, twi);
+  k2.insert(k2.end(), k1.begin(), k1.end());
   std::vector<double> tw(2 * naxis);
   for (int i = 0; i < naxis; ++i) {
     tw[2 * i] = twr[i];
     tw[2 * i + 1] = twi[i];
   }
   void* tmp = nullptr;
-  CUDA_TRY_NEG(c, cudaMalloc(&tmp, 3 * naxis * 8));
-  cudaMemcpyAsync(tmp, k2.data(), naxis * 8, cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(static_cast<char*>(tmp) + naxis * 8, tw.data(), 2 * naxis * 8, cudaMemcpyHostToDevice, c->stream);
+  CUDA_TRY_NEG(c, cudaMalloc(&tmp, 4 * naxis * 8));
+  cudaMemcpyAsync(tmp, k2.data(), 2 * naxis * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(static_cast<char*>(tmp) + 2 * naxis * 8, tw.data(), 2 * naxis * 8, cudaMemcpyHostToDevice,
+                  c->stream);
   if (prec) {
-    launch_to_real<float>(static_cast<double*>(tmp), static_cast<float*>(b.ktab), naxis, c->stream);
-    launch_to_real<float>(static_cast<double*>(tmp) + naxis, static_cast<float*>(b.tw), 2 * naxis, c->stream);
+    launch_to_real<float>(static_cast<double*>(tmp), static_cast<float*>(b.ktab), 2 * naxis, c->stream);
+    launch_to_real<float>(static_cast<double*>(tmp) + 2 * naxis, static_cast<float*>(b.tw), 2 * naxis, c->stream);
   } else {
-    cudaMemcpyAsync(b.ktab, tmp, naxis * 8, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(b.tw, static_cast<double*>(tmp) + naxis, 2 * naxis * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(b.ktab, tmp, 2 * naxis * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(b.tw, static_cast<double*>(tmp) + 2 * naxis, 2 * naxis * 8, cudaMemcpyDeviceToDevice,
+                    c->stream);
   }
   CUDA_TRY_NEG(c, cudaStreamSynchronize(c->stream));
   cudaFree(tmp);
@@ -764,6 +877,7 @@ wslda_status wslda_start(wslda_ctx* c, int stationary, double dt) {
   }
   collect_profile(c);
   if ((st = check_device_error(c))) return st;
+  drop_graphs(c);
   c->started = true;
   c->dt_start = dt;
   c->t = stationary ? 0.0 : 3 * dt;
@@ -776,7 +890,14 @@ wslda_status wslda_step(wslda_ctx* c, double dt, int nsteps) {
   if (!c->started) return fail(c, WSLDA_ESTATE, "wslda_step before wslda_start");
   if (nsteps < 0) return fail(c, WSLDA_EINVAL, "nsteps < 0");
   if (dt != c->dt_start) return fail(c, WSLDA_EINVAL, "dt differs from the start-up dt; call wslda_start again");
-  for (int i = 0; i < nsteps; ++i) {
+  int done = 0;
+  if (c->use_graph && !c->prof) {
+    for (; done + 4 <= nsteps; done += 4) {
+      wslda_status st = c->prec == WSLDA_MIXED ? step_graph4<float>(c, dt) : step_graph4<double>(c, dt);
+      if (st) return st;
+    }
+  }
+  for (int i = done; i < nsteps; ++i) {
     wslda_status st = c->prec == WSLDA_MIXED ? step_all<float>(c, dt) : step_all<double>(c, dt);
     if (st) return st;
     if (c->prof && c->pending.size() > 4096) collect_profile(c);
@@ -822,7 +943,6 @@ wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu,
   Box* b = get_box(c, box);
   if (!b) return fail(c, WSLDA_EINVAL, "get_densities: bad box");
   if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_densities before load_states");
-  if (tau || j) return fail(c, WSLDA_EUNSUPPORTED, "tau and j are not available yet");
   if (!c->started) {
     // densities of the loaded states (regulator from the t = 0 fixed point)
     wslda_status st = refresh_fields(c, *b, b->iphi, 1);
@@ -830,6 +950,47 @@ wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu,
   }
   if (rho) CUDA_TRY(c, cudaMemcpyAsync(rho, b->rho, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream));
   if (nu) CUDA_TRY(c, cudaMemcpyAsync(nu, b->nu, size_t(b->M) * 16, cudaMemcpyDeviceToHost, c->stream));
+  if ((tau || j) && b->n > 0) {
+    // three gradient launches accumulate per-state contributions in the free
+    // history slot (between steps slot ih[0] holds nothing live), then a
+    // site-major sum over states; tau_d and j_d use the Nyquist-free gradient
+    wslda_status st;
+    c->cur = c->stream;
+    for (int dir = 0; dir < 3; ++dir) {
+      if (c->prec == WSLDA_MIXED) {
+        StageArgs<float> a = base_args<float>(*b, box_dV(*b));
+        a.phi = static_cast<float2*>(b->ptr(b->iphi));
+        a.h0 = static_cast<float2*>(b->ptr(b->ih[0]));
+        a.sc_in = b->sc[b->iphi];
+        a.wm = b->wm;
+        a.wp = b->wp;
+        a.dir = dir;
+        if ((st = launch_mode<float>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
+      } else {
+        StageArgs<double> a = base_args<double>(*b, box_dV(*b));
+        a.phi = static_cast<double2*>(b->ptr(b->iphi));
+        a.h0 = static_cast<double2*>(b->ptr(b->ih[0]));
+        a.sc_in = b->sc[b->iphi];
+        a.wm = b->wm;
+        a.wp = b->wp;
+        a.dir = dir;
+        if ((st = launch_mode<double>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
+      }
+    }
+    double* tj = nullptr;
+    CUDA_TRY(c, cudaMalloc(&tj, size_t(4) * b->M * 8));
+    cudaError_t e = c->prec == WSLDA_MIXED
+                        ? launch_sum_tauj<float>(static_cast<const float2*>(b->ptr(b->ih[0])), b->n, b->M, b->nchunk,
+                                                 b->chunk, b->part, tj, tj + b->M, c->stream)
+                        : launch_sum_tauj<double>(static_cast<const double2*>(b->ptr(b->ih[0])), b->n, b->M,
+                                                  b->nchunk, b->chunk, b->part, tj, tj + b->M, c->stream);
+    if (e == cudaSuccess && tau) e = cudaMemcpyAsync(tau, tj, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && j) e = cudaMemcpyAsync(j, tj + b->M, size_t(3) * b->M * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tj);
+    if (e != cudaSuccess) return fail(c, WSLDA_ECUDA, std::string("tau/j: ") + cudaGetErrorString(e));
+    collect_profile(c);
+  }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return WSLDA_OK;
 }
@@ -856,22 +1017,9 @@ wslda_status wslda_get_energy(wslda_ctx* c, int box, wslda_energy* out) {
   if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_energy before load_states");
   wslda_status st;
   if (!c->started && (st = refresh_fields(c, *b, b->iphi, 1))) return st;
-  if (c->prec == WSLDA_MIXED) {
-    StageArgs<float> a = base_args<float>(*b, box_dV(*b));
-    a.phi = static_cast<float2*>(b->ptr(b->iphi));
-    a.sc_in = b->sc[b->iphi];
-    if ((st = launch_mode<float>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
-  } else {
-    StageArgs<double> a = base_args<double>(*b, box_dV(*b));
-    a.phi = static_cast<double2*>(b->ptr(b->iphi));
-    a.sc_in = b->sc[b->iphi];
-    if ((st = launch_mode<double>(c, *b, MODE_EKIN, a, PROF_AUX))) return st;
-  }
-  CUDA_TRY(c, launch_energy(b->M, b->n, b->fdev, b->rho, b->nu, b->delta, b->vext, b->dext, b->ekin2, b->wm, b->wp,
-                            box_dV(*b), b->out8, c->stream));
   double h[8];
-  CUDA_TRY(c, cudaMemcpyAsync(h, b->out8, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  st = c->prec == WSLDA_MIXED ? compute_energy<float>(c, *b, h) : compute_energy<double>(c, *b, h);
+  if (st) return st;
   collect_profile(c);
   out->e_kin = h[0];
   out->e_pot = h[1];
@@ -908,6 +1056,44 @@ wslda_status wslda_get_variant(wslda_ctx* c, int box, char* desc, int len) {
   if (!b || !desc || len <= 0) return fail(c, WSLDA_EINVAL, "get_variant: bad arguments");
   snprintf(desc, size_t(len), "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu", b->ks->cs,
            b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem);
+  return WSLDA_OK;
+}
+
+wslda_status wslda_check_conservation(wslda_ctx* c, int box, double e_tol, double n_tol, double* de, double* dn) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "check_conservation: bad box");
+  if (!c->started) return fail(c, WSLDA_ESTATE, "check_conservation before wslda_start");
+  double h[8];
+  wslda_status st = c->prec == WSLDA_MIXED ? compute_energy<float>(c, *b, h) : compute_energy<double>(c, *b, h);
+  if (st) return st;
+  const double e = h[5] - b->fn.mu * h[6];
+  const double rel_e = std::fabs(e - b->e0) / std::max(std::fabs(b->e0), 1e-300);
+  const double rel_n = std::fabs(h[6] - b->n0) / std::max(std::fabs(b->n0), 1e-300);
+  if (de) *de = rel_e;
+  if (dn) *dn = rel_n;
+  if (!(rel_e <= e_tol) || !(rel_n <= n_tol))
+    return fail(c, WSLDA_EDRIFT, "conservation check: relative energy drift " + std::to_string(rel_e) +
+                                     ", particle-number drift " + std::to_string(rel_n));
+  return WSLDA_OK;
+}
+
+wslda_status wslda_set_graph(wslda_ctx* c, int enable, int nstreams) {
+  CHECK_CTX(c);
+  drop_graphs(c);
+  c->use_graph = enable != 0;
+  if (c->use_graph && c->side.empty()) {
+    const int k = std::max(1, std::min(nstreams > 0 ? nstreams : 4, 16));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    for (int i = 0; i < k; ++i) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t e = nullptr;
+      CUDA_TRY(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->side.push_back(s);
+      c->join_ev.push_back(e);
+    }
+  }
   return WSLDA_OK;
 }
 
@@ -1025,6 +1211,7 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
   }
   fclose(f);
   if (!ok) return fail(c, WSLDA_EINVAL, "load: truncated or mismatched file");
+  drop_graphs(c);
   c->t = t;
   c->steps = steps;
   c->dt_start = dts;

@@ -200,6 +200,51 @@ template cudaError_t launch_potentials<double>(const double*, int, int, Function
                                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// tau and j: sums over states of the per-state contributions (read-out only).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void sum_tauj_partial(const cx<R>* __restrict__ c, int64_t nstates, int M, int64_t chunk, double* part) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int64_t n0 = int64_t(blockIdx.y) * chunk, n1 = min(n0 + chunk, nstates);
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (int64_t n = n0; n < n1; ++n) {
+    const cx<R> p = c[n * 2 * M + s], q = c[n * 2 * M + M + s];
+    a0 += p.x;
+    a1 += p.y;
+    a2 += q.x;
+    a3 += q.y;
+  }
+  double* o = part + int64_t(blockIdx.y) * 4 * M;
+  o[s] = a0;
+  o[M + s] = a1;
+  o[2 * M + s] = a2;
+  o[3 * M + s] = a3;
+}
+__global__ void sum_tauj_final(const double* part, int nchunk, int M, double* tau, double* j) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  double a[4] = {0, 0, 0, 0};
+  for (int cidx = 0; cidx < nchunk; ++cidx)
+    for (int k = 0; k < 4; ++k) a[k] += part[int64_t(cidx) * 4 * M + int64_t(k) * M + s];
+  tau[s] = a[0];
+  j[s] = a[1];
+  j[M + s] = a[2];
+  j[2 * M + s] = a[3];
+}
+template <typename R>
+cudaError_t launch_sum_tauj(const cx<R>* contrib, int64_t nstates, int M, int nchunk, int64_t chunk, double* part,
+                            double* tau, double* j, cudaStream_t s) {
+  sum_tauj_partial<R><<<dim3((M + 255) / 256, nchunk), 256, 0, s>>>(contrib, nstates, M, chunk, part);
+  sum_tauj_final<<<(M + 255) / 256, 256, 0, s>>>(part, nchunk, M, tau, j);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sum_tauj<float>(const float2*, int64_t, int, int, int64_t, double*, double*, double*,
+                                            cudaStream_t);
+template cudaError_t launch_sum_tauj<double>(const double2*, int64_t, int, int, int64_t, double*, double*, double*,
+                                             cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Energy (Sec. 3.2, A = 1): one block, fixed-order tree sums in double.
 // out8 = e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part.
 // ---------------------------------------------------------------------------

@@ -68,11 +68,13 @@ KernelSet make_set() {
   k.launch[MODE_F] = launch_stage<G, MODE_F>;
   k.launch[MODE_HORNER] = launch_stage<G, MODE_HORNER>;
   k.launch[MODE_EKIN] = launch_stage<G, MODE_EKIN>;
+  k.launch[MODE_GRAD] = launch_stage<G, MODE_GRAD>;
   k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X>;
   k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y>;
   k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F>;
   k.fn[MODE_HORNER] = (const void*)stage_kernel<G, MODE_HORNER>;
   k.fn[MODE_EKIN] = (const void*)stage_kernel<G, MODE_EKIN>;
+  k.fn[MODE_GRAD] = (const void*)stage_kernel<G, MODE_GRAD>;
   return k;
 }
 
@@ -105,6 +107,12 @@ template <typename R>
 cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
                               const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
                               double* delta, fx4<R>* WD, cudaStream_t s);
+
+// tau and j (Eqs. nab3D..jab3D) from per-state contributions stored as
+// [n][2][M] complex {tau, j_x}, {j_y, j_z}: summed over states per site.
+template <typename R>
+cudaError_t launch_sum_tauj(const cx<R>* contrib, int64_t nstates, int M, int nchunk, int64_t chunk, double* part,
+                            double* tau, double* j, cudaStream_t s);
 
 // Energy terms (Sec. 3.2) from the site fields and per-state kinetic values.
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,

@@ -21,6 +21,9 @@
 //            Taylor series of Eq. Taylor-exp); E_n = <in|H|in> is computed and
 //            stored when requested, else read; optional normalisation.
 //   MODE_EKIN    per-state <u|T|u>, <v|T|v> for the kinetic energy.
+//   MODE_GRAD    one Cartesian derivative d_dir (symbol i k_dir, Nyquist mode
+//            zeroed) of u and v, and the per-state weighted contributions to
+//            tau and j_dir (Eqs. nab3D..jab3D), accumulated into h0.
 // Normalisation (Alg. 2 steps 2 and 8) is deferred: states are written as
 // computed and CTA 0 of the cluster stores the per-state factor 1/sqrt(norm),
 // which every consumer (the next stage, the density reduction, read-out)
@@ -42,7 +45,7 @@ template <> struct fx4_of<float> { using type = float4; };
 template <> struct fx4_of<double> { using type = double4; };
 template <typename R> using fx4 = typename fx4_of<R>::type;
 
-enum Mode : int { MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, NMODES = 5 };
+enum Mode : int { MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, NMODES = 6 };
 
 template <typename R>
 struct StageArgs {
@@ -52,7 +55,7 @@ struct StageArgs {
   const cx<R>* h2;   // X: f_{k-3}
   cx<R>* h3;         // X: f_{k-4} in, c out;  Y: c in
   const fx4<R>* WD;  // [M] {U + V_ext - mu, Re, Im (Delta + Delta_ext), 0}
-  const R* ktab;     // [NX+NY+NZ] per-slot k_d^2 * 0.5 / M
+  const R* ktab;     // [2 (NX+NY+NZ)]: per-slot k_d^2 * 0.5 / M, then k_d / M with the Nyquist mode zeroed
   const cx<R>* tw;   // [NX+NY+NZ] W_N^k per axis (used where a pencil spans lanes)
   double* E;         // HORNER: per-state shift (written when compute_e)
   double* out2;      // EKIN: [n][2] <u|T|u>, <v|T|v>
@@ -63,6 +66,9 @@ struct StageArgs {
   double dt;
   double dV;
   double coef_re, coef_im;  // HORNER coefficient
+  const double* wm;  // GRAD: frozen weights f(-E_n), f(E_n)
+  const double* wp;
+  int dir;           // GRAD: derivative direction 0, 1, 2
   int compute_e;
   int normalize;
   int nstates;
@@ -92,7 +98,7 @@ struct Geometry {
   static constexpr int NW = BT / 32;
   static constexpr int NCOL = 2 * NY * NZ / CS;  // x-pencils per CTA
   static constexpr size_t smem_bytes =
-      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (sizeof(R) + sizeof(C)) + 112 * sizeof(double) + 16;
+      size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (2 * sizeof(R) + sizeof(C)) + 112 * sizeof(double) + 16;
   // reduction scratch (doubles): warp partials A [0,32) and B [32,64), per-CTA
   // slots of the <H>_n / kinetic sums [64, 96), of the norm [96, 112)
   static constexpr int RED_WA = 0, RED_WB = 32, RED_E = 64, RED_N = 96;
@@ -214,9 +220,10 @@ __device__ __forceinline__ void local_pass(typename G::C* buf, const typename G:
 // x pencils across the cluster: forward, multiply by the kinetic symbol, inverse.
 // Element x of a column lives in CTA x / P at plane x % P; the CTA windows are
 // mapped once (mapa) and accessed with 32-bit ld/st.shared::cluster.
-template <class G>
+template <class G, bool GRAD = false>
 __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* ktab, const typename G::C* tw,
-                                       cg::cluster_group& cl, typename G::R& ekin_u, typename G::R& ekin_v) {
+                                       cg::cluster_group& cl, typename G::R& ekin_u, typename G::R& ekin_v,
+                                       int dir = 0) {
   using C = typename G::C;
   using R = typename G::R;
   constexpr int T = G::TX, N = G::NX, N1 = N / T;
@@ -243,6 +250,16 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
       x[m] = ld_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, C{});
     }
     pencil_fwd<N, T>(x, j, tw);
+    if constexpr (GRAD) {
+      // symbol i k_dir / M (Nyquist mode zeroed), from the second half of ktab
+      constexpr int K1 = G::NX + G::NY + G::NZ;
+      const R kyz1 = dir == 1 ? ktab[K1 + G::NX + y] : ktab[K1 + G::NX + G::NY + z];
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const R kk = dir == 0 ? ktab[K1 + j + T * m] : kyz1;
+        x[m] = mk<C>(-kk * x[m].y, kk * x[m].x);
+      }
+    } else {
     const R kyz = ktab[G::NX + y] + ktab[G::NX + G::NY + z];
     // Parseval: sum_k (k^2/2M) |phi_k|^2 = <phi|T|phi> for the unnormalised FFT
     R ek = 0;
@@ -255,6 +272,7 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
     if (act) {
       if (comp == 0) ekin_u += ek;
       else ekin_v += ek;
+    }
     }
     pencil_inv<N, T>(x, j, tw);
     // a column is read and written only by its own lane group: no barrier here
@@ -275,7 +293,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   extern __shared__ __align__(16) unsigned char smem[];
   C* buf = reinterpret_cast<C*>(smem);
   R* ktab = reinterpret_cast<R*>(buf + 2 * G::SLAB);
-  C* tws = reinterpret_cast<C*>(ktab + (G::NX + G::NY + G::NZ));
+  C* tws = reinterpret_cast<C*>(ktab + 2 * (G::NX + G::NY + G::NZ));
   double* red = reinterpret_cast<double*>(tws + (G::NX + G::NY + G::NZ));
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
 
@@ -288,7 +306,12 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   constexpr int U = G::U;
   auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
 
-  for (int i = tid; i < G::NX + G::NY + G::NZ; i += G::BT) { ktab[i] = a.ktab[i]; tws[i] = a.tw[i]; }
+  constexpr int NAX = G::NX + G::NY + G::NZ;
+  for (int i = tid; i < NAX; i += G::BT) {
+    ktab[i] = a.ktab[i];
+    ktab[NAX + i] = a.ktab[NAX + i];
+    tws[i] = a.tw[i];
+  }
   const C* twx = tws;
   const C* twy = tws + G::NX;
   const C* twz = tws + G::NX + G::NY;
@@ -341,7 +364,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   local_pass<G, 1, false>(buf, twy);
   cl.sync();
   R eku = 0, ekv = 0;
-  x_pass<G>(buf, ktab, twx, cl, eku, ekv);
+  x_pass<G, MODE == MODE_GRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
   // publish this CTA's partial <H>_n (or kinetic sums) on the barrier that
   // closes the x pass
   double* slot = red + G::RED_E;
@@ -380,6 +403,26 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   if constexpr (MODE == MODE_EKIN) {
     if (rank == 0 && tid == 0) { a.out2[2 * n] = En; a.out2[2 * n + 1] = Ev; }
     cl.sync();  // CTA 0's slot stays readable until every CTA has read it
+    return;
+  } else if constexpr (MODE == MODE_GRAD) {
+    // buf holds d_dir u, d_dir v. Per site: tau_dir = w-|dv|^2 + w+|du|^2,
+    // j_dir = w- Im(v dv^*) - w+ Im(u du^*); stored as [tau, j_x] and
+    // [j_y, j_z] in components 0 and 1 of h0, tau summed over the directions.
+    const R wmn = R(a.wm[n]), wpn = R(a.wp[n]);
+    C* out = a.h0 + sbase;
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const int g = gs0 + s;
+      const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
+      const C du = buf[sidx(s)], dv = buf[G::SLAB + sidx(s)];
+      const R tau = wmn * (dv.x * dv.x + dv.y * dv.y) + wpn * (du.x * du.x + du.y * du.y);
+      const R jd = wmn * (vv.y * dv.x - vv.x * dv.y) - wpn * (uu.y * du.x - uu.x * du.y);
+      C o0 = a.dir == 0 ? mk<C>(R(0), jd) : out[g];
+      o0.x += tau;
+      out[g] = o0;
+      if (a.dir == 1) out[G::M + g] = mk<C>(jd, R(0));
+      if (a.dir == 2) { C o1 = out[G::M + g]; o1.y = jd; out[G::M + g] = o1; }
+    }
+    cl.sync();
     return;
   } else {
     if (MODE == MODE_HORNER) {

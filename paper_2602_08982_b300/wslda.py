@@ -81,6 +81,8 @@ def _load():
         "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
         "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
         "wslda_get_variant": (I, [P, I, ct.c_char_p, I]),
+        "wslda_set_graph": (I, [P, I, I]),
+        "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -262,6 +264,15 @@ class Context:
         s = ct.c_int64()
         self._check(lib.wslda_get_time(self._h, ct.byref(t), ct.byref(s)))
         return t.value, s.value
+
+    def check_conservation(self, box: int, e_tol: float, n_tol: float):
+        de, dn = ct.c_double(), ct.c_double()
+        self._check(lib.wslda_check_conservation(self._h, box, float(e_tol), float(n_tol), ct.byref(de),
+                                                 ct.byref(dn)))
+        return de.value, dn.value
+
+    def set_graph(self, enable: bool, nstreams: int = 4):
+        self._check(lib.wslda_set_graph(self._h, int(bool(enable)), int(nstreams)))
 
     def get_variant(self, box: int) -> str:
         buf = ct.create_string_buffer(256)

@@ -158,6 +158,24 @@ def test_c1_config_16cubed_20_steps(W, c1_reference, prec):
     assert all(v < TOL[prec] for v in errs.values()), errs
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape,spacing,n", [((8, 12, 16), (1.0, 0.9, 1.1), 301), ((32, 32, 32), (1, 1, 1), 129)])
+def test_tau_and_current_match_oracle(W, prec, shape, spacing, n):
+    """tau and j (Eqs. nab3D..jab3D) with Nyquist-free spectral gradients, after
+    a few steps so that j is non-zero (trap + pairing kick + thermal weights)."""
+    case = make_case(shape, spacing, nstates=n, trap=0.1, kick=0.05, seed=12, thermal=True)
+    ctx, box = gpu_context(case, prec)
+    ctx.start(False, 0.01)
+    ctx.step(0.01, 2)
+    rho, nu, tau, j = ctx.get_densities(box, tau=True, current=True)
+    ctx.close()
+    ref_in = case.phi if prec == 0 else case.phi.astype(np.complex64).astype(np.complex128)
+    sysm, st = oracle_evolve(case, 0.01, 5, False, phi0=ref_in)
+    tau_r, j_r = o.kinetic_current_densities(st.phi, case.wm, case.wp, case.lat)
+    assert rel(tau, tau_r) < TOL[prec]
+    assert np.abs(j - j_r).max() / np.abs(j_r).max() < TOL[prec] * (10 if prec == 1 else 1)
+
+
 def test_save_load_resume_is_bit_identical(W, tmp_path):
     case = make_case((8, 8, 8), trap=0.1, kick=0.05, seed=10)
     a, box = gpu_context(case, 0)
@@ -174,6 +192,25 @@ def test_save_load_resume_is_bit_identical(W, tmp_path):
     got = b.get_states(box)
     b.close()
     assert np.array_equal(ref, got)
+
+
+def test_conservation_diagnostics(W):
+    """Energy (E_tot - mu N) and N drift checks of the TD codes (Sec. 4.5.1):
+    small for a trapped evolution, and a zero tolerance trips WSLDA_EDRIFT
+    (host-side fault injection, no GPU fault), which then sticks."""
+    case = make_case((8, 8, 8), trap=0.1, seed=13)
+    ctx, box = gpu_context(case, 0)
+    ctx.start(False, 0.005)
+    ctx.step(0.005, 20)
+    de, dn = ctx.check_conservation(box, 1e-6, 1e-6)
+    assert de < 1e-6 and dn < 1e-6
+    with pytest.raises(W.WsldaError) as e:
+        ctx.check_conservation(box, 0.0, 0.0)
+    assert e.value.status == 5
+    with pytest.raises(W.WsldaError) as e:
+        ctx.step(0.005, 1)
+    assert e.value.status == 7
+    ctx.close()
 
 
 def test_errors_are_status_codes(W):
