@@ -77,6 +77,8 @@ struct wslda_ctx {
   std::vector<cudaEvent_t> join_ev;
   std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
   double graph_dt = 0.0;
+  cudaStream_t cap = nullptr;      // context-owned stream the graphs are captured and replayed on
+  cudaEvent_t cap_in = nullptr, cap_out = nullptr;
   std::vector<Box> boxes;
   std::string err;
   int status = WSLDA_OK;
@@ -540,6 +542,9 @@ std::vector<int> slot_phase(const wslda_ctx* c) {
 }
 
 // Four steps captured once per slot phase and dt, replayed as one graph launch.
+// Capture and replay happen on a context-owned stream (the caller's stream may
+// be the legacy default stream, which cannot be captured), ordered after and
+// before the caller's stream with events.
 template <typename R>
 wslda_status step_graph4(wslda_ctx* c, double dt) {
   if (c->graph_dt != dt) {
@@ -550,12 +555,16 @@ wslda_status step_graph4(wslda_ctx* c, double dt) {
   cudaGraphExec_t exec = nullptr;
   for (auto& g : c->graphs)
     if (g.first == key) exec = g.second;
+  cudaStream_t user = c->stream;
   if (!exec) {
-    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->cap;
     wslda_status st = WSLDA_OK;
     for (int k = 0; k < 4 && !st; ++k) st = step_all<R>(c, dt);
+    c->stream = user;
+    c->cur = user;
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
     if (st) {
       if (graph) cudaGraphDestroy(graph);
       return st;
@@ -567,7 +576,11 @@ wslda_status step_graph4(wslda_ctx* c, double dt) {
     c->graphs.push_back({key, exec});
     // capture advanced the host-side slot rotation by four steps, back to `key`
   }
-  CUDA_TRY(c, cudaGraphLaunch(exec, c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->cap_in, user));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->cap, c->cap_in, 0));
+  CUDA_TRY(c, cudaGraphLaunch(exec, c->cap));
+  CUDA_TRY(c, cudaEventRecord(c->cap_out, c->cap));
+  CUDA_TRY(c, cudaStreamWaitEvent(user, c->cap_out, 0));
   return WSLDA_OK;
 }
 
@@ -633,6 +646,9 @@ void wslda_destroy(wslda_ctx* c) {
   for (cudaStream_t s : c->side) cudaStreamDestroy(s);
   for (cudaEvent_t e : c->join_ev) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap_in) cudaEventDestroy(c->cap_in);
+  if (c->cap_out) cudaEventDestroy(c->cap_out);
   delete c;
 }
 
@@ -1084,6 +1100,9 @@ wslda_status wslda_set_graph(wslda_ctx* c, int enable, int nstreams) {
   c->use_graph = enable != 0;
   if (c->use_graph && c->side.empty()) {
     const int k = std::max(1, std::min(nstreams > 0 ? nstreams : 4, 16));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cap_in, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cap_out, cudaEventDisableTiming));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
     for (int i = 0; i < k; ++i) {
       cudaStream_t s = nullptr;
