@@ -161,10 +161,12 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     clocks = ClockSampler(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    l0 = ctx.launch_count()
     e0.record(stream)
     ctx.step(args.dt, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
     kt = {k: ctx.get_kernel_time(k) for k in ("stage_x", "stage_y", "density", "potentials")}
@@ -196,7 +198,6 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation), FP64",
                 "peak_source": "nominal FP64 rate", "algorithmic_flops_per_state_site": fx}
-    launches = sum(kt[k][1] for k in kt)
     share = {k: kt[k][0] / ms for k in kt}
     roof["launch_variant"] = variant
     return dict(value=value, ms_per_step=ms / args.steps, roofline=roof, clocks=ck, launches=launches,
@@ -276,16 +277,19 @@ def run_batched(W, torch, args):
     ctx.step(args.dt, 4)                      # warm-up (also captures the graphs)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
     e0.record(stream)
     ctx.step(args.dt, steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
     ms = e0.elapsed_time(e1)
     ctx.close()
     value = units * steps / (ms * 1e-3)
     peak, which = measured_peaks()
     step_gbs = 160.0 * units / (ms / steps * 1e-3) / 1e9
     return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "boxes": 64,
+            "gpu_launches": launches,
             "box_sides_seed": seed, "box_sides": sides, "state_sites_per_step": units,
             "config": "64 cubic boxes 12^3..24^3 (all states), BdG 1/(kF a) uniform in [-1, 1), 1e-3 pairing "
                       "kick per box, complex64, boxes on 4 forked streams, 4 steps per CUDA graph",

@@ -224,6 +224,10 @@ wslda_status wslda_densities_noalloc(int precision, const void* uv, const double
 wslda_status wslda_set_profiling(wslda_ctx* ctx, int enable);
 wslda_status wslda_get_kernel_time(wslda_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 
+/* Number of kernels the context has launched so far (a graph replay counts
+ * the kernels it contains). */
+int64_t wslda_launch_count(const wslda_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ struct Box {
   int nchunk = 1;
   int64_t chunk = 1;
   double* Ebuf = nullptr;
+  double* npart = nullptr;  // [n][16] per-CTA norm partials
   double* ekin2 = nullptr;
   double* out8 = nullptr;
   double e0 = 0.0, n0 = 0.0;  // E_tot - mu N and N of the states at wslda_start
@@ -76,6 +77,7 @@ struct wslda_ctx {
   cudaEvent_t fork_ev = nullptr;
   std::vector<cudaEvent_t> join_ev;
   std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> graphs;
+  std::vector<int64_t> graph_kernels;  // kernels per graph (launch accounting)
   double graph_dt = 0.0;
   cudaStream_t cap = nullptr;      // context-owned stream the graphs are captured and replayed on
   cudaEvent_t cap_in = nullptr, cap_out = nullptr;
@@ -94,6 +96,7 @@ struct wslda_ctx {
   std::vector<cudaEvent_t> evpool;
   double prof_ms[NPROF] = {};
   int64_t prof_n[NPROF] = {};
+  int64_t launches = 0;  // kernels this context has launched
 };
 
 namespace {
@@ -260,6 +263,7 @@ StageArgs<R> base_args(const Box& b, double dV) {
   a.ktab = static_cast<const R*>(b.ktab);
   a.tw = static_cast<const cx<R>*>(b.tw);
   a.E = b.Ebuf;
+  a.npart = b.npart;
   a.out2 = b.ekin2;
   a.dV = dV;
   a.nstates = int(b.n);
@@ -268,12 +272,20 @@ StageArgs<R> base_args(const Box& b, double dV) {
 
 double box_dV(const Box& b) { return b.lat.dx * b.lat.dy * b.lat.dz; }
 
+// A stage launch; normalising modes are followed by the kernel that turns the
+// per-CTA norm partials into the per-state factor (same profiling scope).
 template <typename R>
 wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int kind) {
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
   ProfScope ps(c, kind);
   CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), c->cur));
+  c->launches += 1;
+  const bool norm_out = mode == MODE_X || mode == MODE_Y || (mode == MODE_HORNER && a.normalize);
+  if (norm_out) {
+    CUDA_TRY(c, launch_finalize_norm(a.npart, b.ks->cs, b.n, box_dV(b), a.sc_out, c->err_d, c->cur));
+    c->launches += 1;
+  }
   return WSLDA_OK;
 }
 
@@ -282,6 +294,7 @@ template <typename R>
 wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   if (b.n > 0) {
     ProfScope ps(c, PROF_DENS);
+    c->launches += 1;
     CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), b.sc[islot],
                                           static_cast<const R*>(b.wm_r),
                                           static_cast<const R*>(b.wp_r), b.n, b.M, b.nchunk, b.chunk, b.part,
@@ -290,6 +303,7 @@ wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
     CUDA_TRY(c, cudaMemsetAsync(b.part, 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->cur));
   }
   ProfScope ps2(c, PROF_POT);
+  c->launches += 1;
   CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu, b.U,
                                    b.delta, static_cast<fx4<R>*>(b.WD), c->cur));
   return WSLDA_OK;
@@ -530,6 +544,7 @@ wslda_status step_all(wslda_ctx* c, double dt) {
 void drop_graphs(wslda_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   c->graphs.clear();
+  c->graph_kernels.clear();
 }
 
 std::vector<int> slot_phase(const wslda_ctx* c) {
@@ -553,16 +568,23 @@ wslda_status step_graph4(wslda_ctx* c, double dt) {
   }
   const std::vector<int> key = slot_phase(c);
   cudaGraphExec_t exec = nullptr;
-  for (auto& g : c->graphs)
-    if (g.first == key) exec = g.second;
+  int64_t kernels = 0;
+  for (size_t i = 0; i < c->graphs.size(); ++i)
+    if (c->graphs[i].first == key) {
+      exec = c->graphs[i].second;
+      kernels = c->graph_kernels[i];
+    }
   cudaStream_t user = c->stream;
   if (!exec) {
     CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = c->launches;
     c->stream = c->cap;
     wslda_status st = WSLDA_OK;
     for (int k = 0; k < 4 && !st; ++k) st = step_all<R>(c, dt);
     c->stream = user;
     c->cur = user;
+    kernels = c->launches - l0;  // captured, not yet executed
+    c->launches = l0;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
     if (st) {
@@ -574,11 +596,13 @@ wslda_status step_graph4(wslda_ctx* c, double dt) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(c, WSLDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     c->graphs.push_back({key, exec});
+    c->graph_kernels.push_back(kernels);
     // capture advanced the host-side slot rotation by four steps, back to `key`
   }
   CUDA_TRY(c, cudaEventRecord(c->cap_in, user));
   CUDA_TRY(c, cudaStreamWaitEvent(c->cap, c->cap_in, 0));
   CUDA_TRY(c, cudaGraphLaunch(exec, c->cap));
+  c->launches += kernels;
   CUDA_TRY(c, cudaEventRecord(c->cap_out, c->cap));
   CUDA_TRY(c, cudaStreamWaitEvent(user, c->cap_out, 0));
   return WSLDA_OK;
@@ -696,7 +720,7 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
 
   const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
   const size_t field_bytes = size_t(M) * (8 * 13 + rsize * 4) + size_t(4) * M * 8 * b.nchunk +
-                             size_t(nstates) * (8 * 10 + rsize * 2) + 4096;
+                             size_t(nstates) * (8 * 26 + rsize * 2) + 4096;
   const size_t need = 5 * state_bytes + field_bytes;
   size_t freeb = 0, totalb = 0;
   CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
@@ -739,6 +763,7 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.wp_r, std::max<int64_t>(nstates, 1) * rsize);
   ALLOC(b.part, size_t(4) * M * 8 * b.nchunk);
   ALLOC(b.Ebuf, std::max<int64_t>(nstates, 1) * 8);
+  ALLOC(b.npart, std::max<int64_t>(nstates, 1) * 16 * 8);
   ALLOC(b.ekin2, std::max<int64_t>(nstates, 1) * 16);
   ALLOC(b.out8, 8 * 8);
 #undef ALLOC
@@ -1135,6 +1160,8 @@ wslda_status wslda_set_profiling(wslda_ctx* c, int enable) {
   }
   return WSLDA_OK;
 }
+
+int64_t wslda_launch_count(const wslda_ctx* c) { return c ? c->launches : 0; }
 
 wslda_status wslda_get_kernel_time(wslda_ctx* c, int kind, double* total_ms, int64_t* launches) {
   CHECK_CTX(c);

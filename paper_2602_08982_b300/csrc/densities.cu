@@ -245,6 +245,25 @@ template cudaError_t launch_sum_tauj<double>(const double2*, int64_t, int, int, 
                                              cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// Deferred normalisation: per-state factor 1/sqrt(dV sum of the CTA partials).
+// ---------------------------------------------------------------------------
+__global__ void finalize_norm_kernel(const double* npart, int cs, int64_t n, double dV, double* sc, int* err) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = 0.0;
+  for (int r = 0; r < cs; ++r) t += npart[i * 16 + r];
+  const double nrm = t * dV;
+  if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(err, 1);
+  sc[i] = 1.0 / sqrt(nrm);
+}
+cudaError_t launch_finalize_norm(const double* npart, int cs, int64_t n, double dV, double* sc, int* err,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  finalize_norm_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(npart, cs, n, dV, sc, err);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Energy (Sec. 3.2, A = 1): one block, fixed-order tree sums in double.
 // out8 = e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part.
 // ---------------------------------------------------------------------------

@@ -114,6 +114,10 @@ template <typename R>
 cudaError_t launch_sum_tauj(const cx<R>* contrib, int64_t nstates, int M, int nchunk, int64_t chunk, double* part,
                             double* tau, double* j, cudaStream_t s);
 
+// Deferred normalisation: sc[i] = 1/sqrt(dV sum_{r<cs} npart[16 i + r]).
+cudaError_t launch_finalize_norm(const double* npart, int cs, int64_t n, double dV, double* sc, int* err,
+                                 cudaStream_t s);
+
 // Energy terms (Sec. 3.2) from the site fields and per-state kinetic values.
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
                           const double* delta, const double* vext, const double* dext, const double* ekin2,

@@ -25,9 +25,10 @@
 //            zeroed) of u and v, and the per-state weighted contributions to
 //            tau and j_dir (Eqs. nab3D..jab3D), accumulated into h0.
 // Normalisation (Alg. 2 steps 2 and 8) is deferred: states are written as
-// computed and CTA 0 of the cluster stores the per-state factor 1/sqrt(norm),
-// which every consumer (the next stage, the density reduction, read-out)
-// applies on load. Per-state reductions (<H>_n, norms) are summed per thread in
+// computed, each CTA stores its partial norm, a small kernel turns the partials
+// into the per-state factor 1/sqrt(norm), and every consumer (the next stage,
+// the density reduction, read-out) applies that factor on load. The only
+// cluster barriers are the two around the x pass; CTAs exit without waiting. Per-state reductions (<H>_n, norms) are summed per thread in
 // the working precision, then across threads and CTAs in double in a fixed
 // order, so all CTAs of the cluster obtain bit-identical values.
 #pragma once
@@ -61,7 +62,8 @@ struct StageArgs {
   double* out2;      // EKIN: [n][2] <u|T|u>, <v|T|v>
   const double* sc_in;    // [n] scale of the input states (true phi = sc_in * stored)
   const double* sc_base;  // HORNER: [n] scale of the base states
-  double* sc_out;         // [n] scale of the written states (normalising modes), else 1
+  double* sc_out;         // [n] scale of the written states: 1 for outputs that are not normalised
+  double* npart;          // [n][16] per-CTA norm partials of normalised outputs (finalised by a separate kernel)
   int* err;          // error word: bit 0 non-finite norm
   double dt;
   double dV;
@@ -100,7 +102,7 @@ struct Geometry {
   static constexpr size_t smem_bytes =
       size_t(2) * SLAB * sizeof(C) + size_t(NX + NY + NZ) * (2 * sizeof(R) + sizeof(C)) + 112 * sizeof(double) + 16;
   // reduction scratch (doubles): warp partials A [0,32) and B [32,64), per-CTA
-  // slots of the <H>_n / kinetic sums [64, 96), of the norm [96, 112)
+  // slots of the <H>_n / kinetic sums [64, 96)
   static constexpr int RED_WA = 0, RED_WB = 32, RED_E = 64, RED_N = 96;
   static_assert(NX % CS == 0, "cluster must split x evenly");
   static_assert((2 * NY * NZ) % CS == 0, "columns must split evenly");
@@ -121,8 +123,6 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 // 32-bit shared::cluster addresses of this CTA's `p` in CTA `rank` of the cluster.
 __device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
@@ -141,6 +141,26 @@ __device__ __forceinline__ double2 ld_dsmem(unsigned addr, double2) {
   asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
   return v;
 }
+template <unsigned OFF>
+__device__ __forceinline__ float2 ld_dsmem_off(unsigned addr, float2) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(OFF) : "memory");
+  return v;
+}
+template <unsigned OFF>
+__device__ __forceinline__ double2 ld_dsmem_off(unsigned addr, double2) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2+%3];" : "=d"(v.x), "=d"(v.y) : "r"(addr), "n"(OFF) : "memory");
+  return v;
+}
+template <unsigned OFF>
+__device__ __forceinline__ void st_dsmem_off(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0+%1], {%2, %3};" ::"r"(addr), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
+}
+template <unsigned OFF>
+__device__ __forceinline__ void st_dsmem_off(unsigned addr, double2 v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0+%1], {%2, %3};" ::"r"(addr), "n"(OFF), "d"(v.x), "d"(v.y) : "memory");
+}
 __device__ __forceinline__ void st_dsmem(unsigned addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
@@ -150,31 +170,6 @@ __device__ __forceinline__ void st_dsmem(unsigned addr, double2 v) {
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Sum over the threads of the CTA and the CTAs of the cluster (double, fixed order).
-// LAST: the caller's final reduction; the closing barrier is only arrived at
-// here and must be waited on (cluster_wait) before the CTA exits.
-template <class G, bool LAST = false>
-__device__ __forceinline__ double cluster_sum(double v, double* red, cg::cluster_group& cl) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[G::RED_WA + w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < G::NW; ++i) s += red[i];
-    double* dst = cl.map_shared_rank(red + G::NW, 0);
-    dst[cl.block_rank()] = s;
-  }
-  cl.sync();
-  const double* src = cl.map_shared_rank(red + G::NW, 0);
-  double tot = 0.0;
-  for (int r = 0; r < G::CS; ++r) tot += src[r];
-  if constexpr (LAST) cluster_arrive();
-  else cl.sync();
-  return tot;
 }
 
 // Local pencils along z (rows) or y, forward or inverse, over both components.
@@ -244,10 +239,21 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
     const int y = yz / G::NZ, z = yz % G::NZ;
     const unsigned off = unsigned((comp * G::SLAB + y * G::ZP + z) * sizeof(C));
     C x[N1];
+    if constexpr (T == 1) {
+      // one base address per CTA of the cluster, plane offsets as immediates
+      unsigned base[G::CS];
 #pragma unroll
-    for (int m = 0; m < N1; ++m) {
-      const int xg = j + T * m;  // compile-time plane when T == 1
-      x[m] = ld_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, C{});
+      for (int r = 0; r < G::CS; ++r) base[r] = win[r] + off;
+      static_for<0, N1>([&](auto mm) {
+        constexpr int m = decltype(mm)::value;
+        x[m] = ld_dsmem_off<unsigned(m % G::P) * PLANE>(base[m / G::P], C{});
+      });
+    } else {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const int xg = j + T * m;
+        x[m] = ld_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, C{});
+      }
     }
     pencil_fwd<N, T>(x, j, tw);
     if constexpr (GRAD) {
@@ -277,10 +283,20 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
     pencil_inv<N, T>(x, j, tw);
     // a column is read and written only by its own lane group: no barrier here
     if (act) {
+      if constexpr (T == 1) {
+        unsigned base[G::CS];
 #pragma unroll
-      for (int m = 0; m < N1; ++m) {
-        const int xg = j + T * m;
-        st_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, x[m]);
+        for (int r = 0; r < G::CS; ++r) base[r] = win[r] + off;
+        static_for<0, N1>([&](auto mm) {
+          constexpr int m = decltype(mm)::value;
+          st_dsmem_off<unsigned(m % G::P) * PLANE>(base[m / G::P], x[m]);
+        });
+      } else {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+          const int xg = j + T * m;
+          st_dsmem(win[xg / G::P] + off + unsigned(xg % G::P) * PLANE, x[m]);
+        }
       }
     }
   }
@@ -325,15 +341,16 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   cp_async_wait_all();
   __syncthreads();
 
-  // Prologue sweep over the slab: apply the input scale (deferred
-  // normalisation) and accumulate the potential part of <H>_n,
-  // sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v).
+  // Prologue sweep over the slab: the potential part of <H>_n,
+  // sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v), of the scaled input (the slab
+  // itself stays unscaled; the FFT is linear, so the scale is applied to its
+  // results instead).
   const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
   const R sin_ = R(a.sc_in[n]);
   R ep = 0, ec = 0;  // compensated partial sum
-  for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
+  for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * U) {
     fx4<R> wd[U];
-    if (need_e) {
+    {
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int s = s0 + k * G::BT;
@@ -343,33 +360,31 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int s = s0 + k * G::BT;
-      if (s < G::NS) {
+      if (s < G::NS && need_e) {
         const C u = scl(buf[sidx(s)], sin_), v = scl(buf[G::SLAB + sidx(s)], sin_);
-        buf[sidx(s)] = u;
-        buf[G::SLAB + sidx(s)] = v;
-        if (need_e) {
-          const C dv = mul(mk<C>(wd[k].y, wd[k].z), v);
-          const R t = (wd[k].x * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
-          const R ns = ep + t;
-          ec = (ns - ep) - t;
-          ep = ns;
-        }
+        const C dv = mul(mk<C>(wd[k].y, wd[k].z), v);
+        const R t = (wd[k].x * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
+        const R ns = ep + t;
+        ec = (ns - ep) - t;
+        ep = ns;
       }
     }
   }
 
   __syncthreads();  // the slab is read above before the z pass overwrites it
+  const R sin2 = sin_ * sin_;
   local_pass<G, 2, false>(buf, twz);
   __syncthreads();
   local_pass<G, 1, false>(buf, twy);
   cl.sync();
   R eku = 0, ekv = 0;
   x_pass<G, MODE == MODE_GRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
-  // publish this CTA's partial <H>_n (or kinetic sums) on the barrier that
-  // closes the x pass
+  // Publish this CTA's partial <H>_n (or kinetic sums) into the slots of every
+  // CTA of the cluster on the barrier that closes the x pass; afterwards each
+  // CTA reads only its own shared memory, so no CTA has to outlive another.
   double* slot = red + G::RED_E;
   {
-    double v0 = MODE == MODE_EKIN ? double(eku) : double(ep) + double(eku) - double(ekv);
+    double v0 = MODE == MODE_EKIN ? double(eku) : double(ep) + (double(eku) - double(ekv)) * double(sin2);
     double v1 = double(ekv);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -378,22 +393,20 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
     }
     if ((tid & 31) == 0) { red[G::RED_WA + (tid >> 5)] = v0; red[G::RED_WB + (tid >> 5)] = v1; }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < G::CS) {
       double s0 = 0.0, s1 = 0.0;
       for (int i = 0; i < G::NW; ++i) { s0 += red[G::RED_WA + i]; s1 += red[G::RED_WB + i]; }
-      double* dst = cl.map_shared_rank(slot, 0);
+      double* dst = cl.map_shared_rank(slot, tid);
       dst[rank] = s0;
       dst[G::CS + rank] = s1;
     }
   }
   cl.sync();
   double En = 0.0, Ev = 0.0;
-  {
-    const double* src = cl.map_shared_rank(slot, 0);
-    for (int r = 0; r < G::CS; ++r) { En += src[r]; Ev += src[G::CS + r]; }
-    En *= a.dV;
-    Ev *= a.dV;
-  }
+  for (int r = 0; r < G::CS; ++r) { En += slot[r]; Ev += slot[G::CS + r]; }
+  En *= a.dV;
+  Ev *= a.dV;
+  if (MODE == MODE_EKIN) { En *= double(sin2); Ev *= double(sin2); }
   local_pass<G, 1, true>(buf, twy);
   __syncthreads();
   local_pass<G, 2, true>(buf, twz);
@@ -402,7 +415,6 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
 
   if constexpr (MODE == MODE_EKIN) {
     if (rank == 0 && tid == 0) { a.out2[2 * n] = En; a.out2[2 * n + 1] = Ev; }
-    cl.sync();  // CTA 0's slot stays readable until every CTA has read it
     return;
   } else if constexpr (MODE == MODE_GRAD) {
     // buf holds d_dir u, d_dir v. Per site: tau_dir = w-|dv|^2 + w+|du|^2,
@@ -413,7 +425,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
     for (int s = tid; s < G::NS; s += G::BT) {
       const int g = gs0 + s;
       const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
-      const C du = buf[sidx(s)], dv = buf[G::SLAB + sidx(s)];
+      const C du = scl(buf[sidx(s)], sin_), dv = scl(buf[G::SLAB + sidx(s)], sin_);
       const R tau = wmn * (dv.x * dv.x + dv.y * dv.y) + wpn * (du.x * du.x + du.y * du.y);
       const R jd = wmn * (vv.y * dv.x - vv.x * dv.y) - wpn * (uu.y * du.x - uu.x * du.y);
       C o0 = a.dir == 0 ? mk<C>(R(0), jd) : out[g];
@@ -422,7 +434,6 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
       if (a.dir == 1) out[G::M + g] = mk<C>(jd, R(0));
       if (a.dir == 2) { C o1 = out[G::M + g]; o1.y = jd; out[G::M + g] = o1; }
     }
-    cl.sync();
     return;
   } else {
     if (MODE == MODE_HORNER) {
@@ -471,8 +482,8 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
           const C d = mk<C>(wd[k].y, wd[k].z);
           // (H - <H>_n) phi for both components (Eq. dpsidt-Hpsi, A = 1)
           C hm[2];
-          hm[0] = sub(add(add(buf[b], scl(uu, w)), mul(d, vv)), scl(uu, Er));
-          hm[1] = sub(sub(sub(mulc(uu, d), buf[G::SLAB + b]), scl(vv, w)), scl(vv, Er));
+          hm[0] = sub(add(add(scl(buf[b], sin_), scl(uu, w)), mul(d, vv)), scl(uu, Er));
+          hm[1] = sub(sub(sub(mulc(uu, d), scl(buf[G::SLAB + b], sin_)), scl(vv, w)), scl(vv, Er));
           const C ph[2] = {uu, vv};
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
@@ -504,8 +515,8 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
         }
       }
     }
-    // Norm partials ride on the closing cluster barrier; CTA 0 stores the
-    // per-state factor 1/sqrt(norm) (1 for outputs that are not normalised).
+    // Norm partials go to global memory (finalised into 1/sqrt(norm) by a
+    // separate kernel); outputs that are not normalised get the factor 1.
     if (norm_out) {
       double v = double(np);
 #pragma unroll
@@ -515,21 +526,10 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
       if (tid == 0) {
         double t = 0.0;
         for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
-        double* dst_n = cl.map_shared_rank(red + G::RED_N, 0);
-        dst_n[rank] = t;
+        a.npart[size_t(n) * 16 + rank] = t;
       }
-    }
-    cl.sync();  // also keeps CTA 0's slots readable until every CTA has read them
-    if (rank == 0 && tid == 0 && a.sc_out) {
-      if (norm_out) {
-        double t = 0.0;
-        for (int r = 0; r < G::CS; ++r) t += red[G::RED_N + r];
-        const double nrm = t * a.dV;
-        if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(a.err, 1);
-        a.sc_out[n] = 1.0 / sqrt(nrm);
-      } else {
-        a.sc_out[n] = 1.0;
-      }
+    } else if (rank == 0 && tid == 0 && a.sc_out) {
+      a.sc_out[n] = 1.0;
     }
   }
 }

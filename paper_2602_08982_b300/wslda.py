@@ -76,6 +76,7 @@ def _load():
         "wslda_load": (I, [P, ct.c_char_p]),
         "wslda_get_time": (I, [P, DP, ct.POINTER(I64)]),
         "wslda_memory_bytes": (I64, [P]),
+        "wslda_launch_count": (I64, [P]),
         "wslda_set_profiling": (I, [P, I]),
         "wslda_uniform_solve": (I, [ct.POINTER(Lattice), ct.POINTER(Functional), D, D, ct.POINTER(Uniform)]),
         "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
@@ -278,6 +279,9 @@ class Context:
         buf = ct.create_string_buffer(256)
         self._check(lib.wslda_get_variant(self._h, box, buf, 256))
         return buf.value.decode()
+
+    def launch_count(self) -> int:
+        return int(lib.wslda_launch_count(self._h))
 
     def memory_bytes(self) -> int:
         return int(lib.wslda_memory_bytes(self._h))
