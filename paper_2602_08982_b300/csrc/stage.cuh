@@ -348,19 +348,19 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
   const R sin_ = R(a.sc_in[n]);
   R ep = 0, ec = 0;  // compensated partial sum
-  for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * U) {
-    fx4<R> wd[U];
-    {
+  // all of a thread's field loads in one round trip (registers are free here)
+  constexpr int UP = (G::NS + G::BT - 1) / G::BT < 16 ? (G::NS + G::BT - 1) / G::BT : 16;
+  for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * UP) {
+    fx4<R> wd[UP];
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int s = s0 + k * G::BT;
-        if (s < G::NS) wd[k] = a.WD[gs0 + s];
-      }
+    for (int k = 0; k < UP; ++k) {
+      const int s = s0 + k * G::BT;
+      if (s < G::NS) wd[k] = a.WD[gs0 + s];
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) {
+    for (int k = 0; k < UP; ++k) {
       const int s = s0 + k * G::BT;
-      if (s < G::NS && need_e) {
+      if (s < G::NS) {
         const C u = scl(buf[sidx(s)], sin_), v = scl(buf[G::SLAB + sidx(s)], sin_);
         const C dv = mul(mk<C>(wd[k].y, wd[k].z), v);
         const R t = (wd[k].x * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
@@ -402,6 +402,14 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
     }
   }
   cl.sync();
+  // The epilogue's DRAM inputs (history slabs) start moving into L2 now, a
+  // few microseconds before they are read.
+  if (tid < 2) {
+    const size_t off = sbase + size_t(tid) * G::M + gs0;
+    constexpr unsigned nb = unsigned(G::NS * sizeof(C));
+    if constexpr (MODE == MODE_X) { prefetch_l2(a.h1 + off, nb); prefetch_l2(a.h2 + off, nb); prefetch_l2(a.h3 + off, nb); }
+    if constexpr (MODE == MODE_Y) prefetch_l2(a.h3 + off, nb);
+  }
   double En = 0.0, Ev = 0.0;
   for (int r = 0; r < G::CS; ++r) { En += slot[r]; Ev += slot[G::CS + r]; }
   En *= a.dV;
