@@ -65,6 +65,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values of x (every rank gets it); x itself on one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank, and the job takes as long as its slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def stage_source_hash() -> str:
     """git blob hash of the stage-kernel source (computed without git)."""
     import hashlib
@@ -170,16 +186,14 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
     kt = {k: ctx.get_kernel_time(k) for k in ("stage_x", "stage_y", "density", "potentials")}
+    ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     rho, nu = ctx.get_densities(box)
     ctx.close()
     M = shape[0] * shape[1] * shape[2]
     units = float(args.nstates) * M * args.steps
-    value = world * units / (ms * 1e-3)
+    value = job_rate(units, world, ms * 1e-3)
     bx, fx = stage_x_algorithmic(prec, shape)
     x_ms, x_n = kt["stage_x"]
     x_avg = x_ms / max(x_n, 1)
@@ -230,14 +244,11 @@ def run_e2e(W, torch, args, shape, world):
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     ctx.close()
-    if world > 1:
-        t = torch.tensor([sec], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = max_over_ranks(sec, world, "cuda")
     units = float(args.nstates) * M * args.steps
     nbytes = host.numel() * 16
     del host
-    return {"value": world * units / sec, "unit": UNIT,
+    return {"value": job_rate(units, world, sec), "unit": UNIT,
             "h2d_bytes_per_step": nbytes / args.steps,
             "d2h_bytes_per_step": (nbytes + args.steps * 24 * M) / args.steps,
             "includes": "load_states from pinned host, Taylor start, K steps each with a density read, final get_states"}
@@ -324,7 +335,8 @@ def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048):
     """The oracle as it stands, on a bounded sample of the workload: the same
     lattice and trap with a subset of the uniform plane-wave states, timed over
     whole ABM steps after a stationary start."""
-    n = 64
+    max_states = min(max_states, shape[0] * shape[1] * shape[2])
+    n = min(64, max_states)
     while True:
         o, sysm, phi, lat = oracle_sample(shape, omega, n)
         st = o.start(sysm, phi, dt, stationary=True)
@@ -354,7 +366,7 @@ def reference_arm(args, shape):
             return
     # each step: one oracle AB4AM5 step over a bounded sample of the states,
     # sized so that one step takes about a second
-    n = cpu_oracle_rate(shape, args.omega, args.dt, seconds=4.0)["n"]
+    n = cpu_oracle_rate(shape, args.omega, args.dt, seconds=args.cpu_seconds / 4)["n"]
     o, sysm, phi, lat = oracle_sample(shape, args.omega, n)
     st = o.start(sysm, phi, args.dt, stationary=True)
     for _ in range(args.warmup):
