@@ -1,0 +1,133 @@
+"""Plain FP64 CPU oracle of the static self-consistent solver (Alg. 1, Sec. 3.2).
+
+TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference leg may import or run anything in this package; the
+product path never does, and this module never imports the product.
+
+The static problem (Eq. HpsiEpsi) is solved as the fixed point K[p] = p of the
+map of Alg. 1 over the potentials p = (U, Delta) (the potential-based
+formulation the toolkit uses by default), iterated with linear mixing
+p <- m K[p] + (1 - m) p and stopped by the energy criterion of Eq. E-conv.
+One application of K, with no blocking, symmetry reduction or reordering:
+
+  1. build the 2M x 2M matrix of Eq. HpsiEpsi from the input potentials
+     (W = U + V_ext - mu, D = Delta + Delta_ext; Laplacian of Eq. D2);
+  2. diagonalise it (numpy.linalg.eigh, one library step) and keep the M
+     eigenpairs with E_n > 0, normalised as sum_r dV (|u|^2 + |v|^2) = 1;
+  3. densities rho_sigma, nu of those states (T = 0 weights);
+  4. potentials (U, Delta) from the densities, the regulator Lambda_c
+     recomputed from the input mean field (reading S1).
+
+Readings (the same on the CUDA side):
+  S1  Lambda_c of Eq. Creg is evaluated every iteration at V = U_in + V_ext
+      with the input mean field of that iteration (it is frozen only during
+      time evolution, reading R2 of the TD oracle).
+  S2  The energy scale of Eq. E-conv is the Fermi energy of the reference
+      uniform system (1/2 for k_F = 1); every energy term listed in Sec. 3.2
+      that the functional has (kinetic, potential, pairing, external
+      potential, external pairing) and their total must change by less than
+      eps_energy times that scale between two consecutive iterations.
+  S3  With a particle-number target, mu follows Eq. update-mu once per
+      iteration, outside the linear mixing; N counts one spin species,
+      N_sigma = int rho_sigma.
+  S4  The first iteration has no predecessor, so convergence is tested from
+      the second iteration on; the returned states are the eigenstates of
+      the last matrix diagonalised, and the returned potentials are its input.
+
+Pins (tests/test_oracle_scf.py): uniform BdG and SLDA fixed points equal the
+lattice seeds solved from the number and gap equations alone, the BdG
+spectrum is +/- symmetric, a converged trapped solution is a fixed point of K
+and is stationary under the TD right-hand side, the mixing parameter does not
+move the fixed point, and the mu update reaches the requested N.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+from . import tdslda as o
+
+ENERGY_TERMS = ("e_kin", "e_pot", "e_pair", "e_ext", "e_pair_ext", "e_total")
+
+
+@dataclass
+class MapOutput:
+    phi: np.ndarray       # [M, 2, M] eigenstates with E_n > 0, ascending E
+    E: np.ndarray         # [M] their quasiparticle energies
+    evals: np.ndarray     # [2M] full spectrum of the matrix
+    rho: np.ndarray       # rho_sigma
+    nu: np.ndarray
+    U: np.ndarray         # output potentials K[p]
+    delta: np.ndarray
+    lam: np.ndarray       # regulator used (reading S1)
+    energy: dict
+
+
+def map_K(lat: o.Lattice, fn: o.Functional, vext, U_in, delta_in, dext=None) -> MapOutput:
+    """One application of the map K of Alg. 1 (steps 1-5)."""
+    # step 1: the matrix of Eq. HpsiEpsi at the input potentials
+    D = delta_in if dext is None else delta_in + dext
+    H = o.dense_bdg(o.Fields(W=U_in + vext - fn.mu, D=D), lat)
+    # step 2: diagonalise, keep E > 0 (M of the 2M eigenvalues for this problem)
+    evals, vecs = np.linalg.eigh(H)
+    M = lat.M
+    keep = np.argsort(evals)[M:]
+    E = evals[keep]
+    phi = vecs[:, keep].T.reshape(M, 2, M) / np.sqrt(lat.dV)
+    # step 3: densities (T = 0)
+    wm, wp = np.ones(M), np.zeros(M)
+    rho, nu = o.densities(phi, wm, wp)
+    # step 4: potentials, regulator at the input mean field (reading S1)
+    lam = o.lambda_c(fn.mu - U_in - vext, fn.cutoff(lat))
+    U_out, delta_out, _ = o.potentials(rho, nu, lam, fn)
+    sysm = o.TDSystem(lat, fn, vext=vext, dext=dext, lam=lam)
+    energy = sysm.energy(phi)
+    return MapOutput(phi=phi, E=E, evals=evals, rho=rho, nu=nu, U=U_out, delta=delta_out, lam=lam, energy=energy)
+
+
+@dataclass
+class SCFResult:
+    phi: np.ndarray
+    E: np.ndarray
+    U: np.ndarray          # input potentials of the last map application
+    delta: np.ndarray
+    mu: float
+    iters: int
+    converged: bool
+    last: MapOutput
+    history: list = field(default_factory=list)    # energy dict per iteration
+
+
+def static_solve(lat: o.Lattice, fn: o.Functional, vext, U0, delta0, mixing: float = 0.5,
+                 eps_energy: float = 1e-6, e_ref: float = 0.5, max_iters: int = 200,
+                 n_target: float | None = None, a_mu: float = 0.0, eps_npart: float = 1e-6,
+                 dext=None) -> SCFResult:
+    """Linear mixing of the potentials (Sec. 3.2, 'Linear mixing') until the
+    energy criterion of Eq. E-conv holds (and Eq. N-conv with a target N)."""
+    U = np.array(U0, dtype=np.float64)
+    delta = np.array(delta0, dtype=np.complex128)
+    mu = fn.mu
+    hist = []
+    out = None
+    converged = False
+    it = 0
+    for it in range(1, max_iters + 1):
+        out = map_K(lat, replace(fn, mu=mu), vext, U, delta, dext)
+        hist.append(out.energy)
+        n_sigma = lat.dV * np.sum(out.rho)
+        n_ok = n_target is None or abs(n_target - n_sigma) < eps_npart
+        if it >= 2:
+            prev = hist[-2]
+            change = max(abs(out.energy[k] - prev[k]) / e_ref for k in ENERGY_TERMS)
+            if change < eps_energy and n_ok:
+                converged = True
+                break
+        if it == max_iters:
+            break
+        if n_target is not None and a_mu != 0.0:
+            mu = mu + (a_mu / n_target) * (n_target - n_sigma)          # Eq. update-mu
+        U = mixing * out.U + (1.0 - mixing) * U
+        delta = mixing * out.delta + (1.0 - mixing) * delta
+    return SCFResult(phi=out.phi, E=out.E, U=U, delta=delta, mu=mu, iters=it, converged=converged,
+                     last=out, history=hist)
