@@ -197,6 +197,48 @@ wslda_status wslda_uniform_solve(const wslda_lattice* lat, const wslda_functiona
  * Weights are set to T = 0. Replaces wslda_load_states. */
 wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, double delta, const int64_t* kidx);
 
+/* Static self-consistent solve (Alg. 1, Sec. 3.2) of a trapped, spin-symmetric
+ * T = 0 system, whose positive-energy eigenstates then become the box's states
+ * (ready for wslda_start). Iteration i applies the map K of Alg. 1 to the
+ * potentials p = (U, Delta): the matrix of Eq. HpsiEpsi built from p (Laplacian
+ * of Eq. D2, W = U + V_ext - mu) is diagonalised, the densities of its M
+ * positive-energy eigenstates give K[p] through the functional, with the
+ * regulator Lambda_c of Eq. Creg evaluated at the input mean field; then
+ * p <- m K[p] + (1 - m) p (linear mixing). The iteration stops when, from the
+ * second iteration on, every energy term of Sec. 3.2 and the total change by
+ * less than eps_energy * e_ref between consecutive iterations (Eq. E-conv) and,
+ * with a particle-number target, |N_req - N_sigma| < eps_npart (Eq. N-conv);
+ * with a target, mu follows Eq. update-mu once per iteration, unmixed.
+ *  - Requirements: the box holds nstates = M states; V_ext, U0 and delta0 are
+ *    real and symmetric under the reflections i -> N - i (mod N) of every axis
+ *    (a potential centred on site N/2); Delta_ext is zero. The problem is then
+ *    real and splits into the 8 reflection-parity blocks, each diagonalised in
+ *    double precision; otherwise WSLDA_EINVAL.
+ *  - U0, delta0: initial potentials, host [M] doubles (Delta real).
+ *  - qp_energies: host [M] output (nullable): the quasiparticle energy of each
+ *    returned state, in state order.
+ *  - On return the box's states are the eigenstates of the last matrix
+ *    diagonalised (normalised, T = 0 weights) and its functional's mu is the
+ *    final mu. The mixed path rounds the states to complex float.
+ *  - out->iters, converged, mu, max_rel_change (last iteration's largest
+ *    |change| / e_ref), n_sigma and the energy terms of the last iteration. */
+typedef struct {
+  double mixing;     /* m of the linear mixing, 0 < m <= 1 */
+  double eps_energy; /* Eq. E-conv threshold */
+  double e_ref;      /* energy scale of Eq. E-conv; <= 0: 1/2 (Fermi energy at k_F = 1) */
+  int max_iters;     /* >= 1 */
+  double n_target;   /* Eq. update-mu target N_sigma; <= 0: fixed mu */
+  double a_mu;       /* Eq. update-mu step size */
+  double eps_npart;  /* Eq. N-conv tolerance */
+} wslda_scf_params;
+typedef struct {
+  int iters, converged;
+  double mu, max_rel_change, n_sigma;
+  wslda_energy energy;
+} wslda_scf_result;
+wslda_status wslda_static_solve(wslda_ctx* ctx, int box, const double* U0, const double* delta0,
+                                const wslda_scf_params* params, double* qp_energies, wslda_scf_result* out);
+
 /* Densities rho [M] and nu [M complex] of device-resident states, without any
  * device allocation. The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc, such as code whose device memory is all

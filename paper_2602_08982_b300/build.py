@@ -2,7 +2,8 @@
 
 Every .cu file under csrc/ is compiled with nvcc in parallel and linked into
 paper_2602_08982_b300/_lib/libwslda_td.so with the CUDA runtime linked
-statically, so the library has no dependency on a particular libcudart.
+statically, so the library has no dependency on a particular libcudart;
+the static solver links the toolkit's cuSOLVER (dense symmetric eigensolver).
 Objects are rebuilt only when a source or header is newer than the object.
 """
 from __future__ import annotations
@@ -56,7 +57,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=jobs or min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs]
+        cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs, "-lcusolver"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

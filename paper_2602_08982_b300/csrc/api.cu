@@ -905,6 +905,70 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, dou
   return WSLDA_OK;
 }
 
+namespace {
+// max |x[i] - x[mirror(i)]| over the reflections i -> N - i (mod N) of each axis
+double mirror_asymmetry(const double* x, int stride, const wslda_lattice& l) {
+  double worst = 0.0;
+  for (int ix = 0; ix < l.nx; ++ix)
+    for (int iy = 0; iy < l.ny; ++iy)
+      for (int iz = 0; iz < l.nz; ++iz) {
+        const int s = (ix * l.ny + iy) * l.nz + iz;
+        const int rx = (l.nx - ix) % l.nx, ry = (l.ny - iy) % l.ny, rz = (l.nz - iz) % l.nz;
+        const int m[3] = {(rx * l.ny + iy) * l.nz + iz, (ix * l.ny + ry) * l.nz + iz, (ix * l.ny + iy) * l.nz + rz};
+        for (int k = 0; k < 3; ++k) worst = std::max(worst, std::fabs(x[size_t(s) * stride] - x[size_t(m[k]) * stride]));
+      }
+  return worst;
+}
+double max_abs(const double* x, size_t n) {
+  double m = 0.0;
+  for (size_t i = 0; i < n; ++i) m = std::max(m, std::fabs(x[i]));
+  return m;
+}
+}  // namespace
+
+wslda_status wslda_static_solve(wslda_ctx* c, int box, const double* U0, const double* delta0,
+                                const wslda_scf_params* p, double* qp_energies, wslda_scf_result* out) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !U0 || !delta0 || !p || !out) return fail(c, WSLDA_EINVAL, "static_solve: bad box or null pointer");
+  if (c->started) return fail(c, WSLDA_ESTATE, "static_solve after wslda_start");
+  if (b->n != b->M) return fail(c, WSLDA_EINVAL, "static_solve: the box must hold nstates = M states");
+  if (!(p->mixing > 0.0 && p->mixing <= 1.0) || p->max_iters < 1 || !(p->eps_energy >= 0.0) ||
+      !std::isfinite(p->e_ref) || !std::isfinite(p->n_target) || !std::isfinite(p->a_mu) ||
+      (p->n_target > 0 && !(p->eps_npart > 0.0)))
+    return fail(c, WSLDA_EINVAL, "static_solve: bad parameters");
+  const size_t M = size_t(b->M);
+  std::vector<double> v(M), d(2 * M);
+  CUDA_TRY(c, cudaMemcpyAsync(v.data(), b->vext, M * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d.data(), b->dext, 2 * M * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (max_abs(d.data(), d.size()) != 0.0)
+    return fail(c, WSLDA_EINVAL, "static_solve: an external pairing field is not supported");
+  for (size_t i = 0; i < M; ++i)
+    if (!std::isfinite(U0[i]) || !std::isfinite(delta0[i])) return fail(c, WSLDA_ENAN, "static_solve: non-finite input");
+  const double* arrs[3] = {v.data(), U0, delta0};
+  for (const double* x : arrs)
+    if (mirror_asymmetry(x, 1, b->lat) > 1e-12 * std::max(1.0, max_abs(x, M)))
+      return fail(c, WSLDA_EINVAL, "static_solve: V_ext, U0 and delta0 must be symmetric about site N/2 on every axis");
+  ScfBox view{b->lat, b->fdev, b->M, c->prec, b->slot[b->iphi], b->sc[b->iphi], b->vext, b->dext, b->rho, b->nu,
+              b->delta, b->ekin2, b->wm, b->wp, b->out8, c->stream};
+  std::string err;
+  const wslda_status st = static_solve(view, U0, delta0, *p, qp_energies, out, err);
+  if (st != WSLDA_OK) return fail(c, st, "static_solve: " + err);
+  b->fn.mu = out->mu;
+  b->fdev.mu = out->mu;
+  if (c->prec == WSLDA_MIXED) {
+    CUDA_TRY(c, launch_to_real<float>(b->wm, static_cast<float*>(b->wm_r), b->n, c->stream));
+    CUDA_TRY(c, launch_to_real<float>(b->wp, static_cast<float*>(b->wp_r), b->n, c->stream));
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(b->wm_r, b->wm, size_t(b->n) * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(b->wp_r, b->wp, size_t(b->n) * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  b->loaded = true;
+  return WSLDA_OK;
+}
+
 wslda_status wslda_start(wslda_ctx* c, int stationary, double dt) {
   CHECK_CTX(c);
   if (!(dt != 0.0) || !std::isfinite(dt)) return fail(c, WSLDA_EINVAL, "dt must be finite and non-zero");

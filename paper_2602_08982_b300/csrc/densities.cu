@@ -4,6 +4,7 @@
 // and precision conversions at the ABI boundary.
 #include <cuda_runtime.h>
 
+#include "functional.cuh"
 #include "internal.cuh"
 
 namespace wslda {
@@ -90,55 +91,6 @@ template cudaError_t launch_density_partial<float>(const float2*, const double*,
                                                    int, int, int64_t, double*, cudaStream_t);
 template cudaError_t launch_density_partial<double>(const double2*, const double*, const double*, const double*,
                                                     int64_t, int, int, int64_t, double*, cudaStream_t);
-
-// ---------------------------------------------------------------------------
-// Functional (Sec. 2.4) and regulator (Sec. 2.6) at one site.
-// ---------------------------------------------------------------------------
-__device__ double regulator(double mu_minus_V, double ec) {
-  // Lambda_c = (1/2 pi^2) PV int_0^kc k^2 dk / (k^2 - k0^2), A = 1:
-  // k0^2 = 2 (mu - V), kc^2 = 2 (E_c + mu - V).
-  const double k0sq = 2.0 * mu_minus_V;
-  const double kcsq = 2.0 * (ec + mu_minus_V);
-  if (!(kcsq > 0.0)) return 0.0;
-  const double kc = sqrt(kcsq);
-  const double pref = kc / (2.0 * M_PI * M_PI);
-  if (k0sq > 0.0) {
-    const double k0 = sqrt(k0sq);
-    return pref * (1.0 - (k0 / (2.0 * kc)) * log((kc + k0) / (kc - k0)));
-  }
-  if (k0sq < 0.0) {
-    const double kap = sqrt(-k0sq);
-    return pref * (1.0 - (kap / kc) * atan2(kc, kap));
-  }
-  return pref;
-}
-
-__device__ __forceinline__ double fermi_energy(double rho_total) {
-  const double c = cbrt(3.0 * M_PI * M_PI * rho_total);
-  return 0.5 * c * c;
-}
-
-// (U, Delta) at one site from rho_sigma, nu and the regulator value lam.
-__device__ void site_potentials(const FunctionalDev& fn, double rho_s, double nr, double ni, double lam, double& U,
-                                double& dr, double& di) {
-  double inv_g;
-  double rho = 2.0 * rho_s;
-  if (fn.kind == 0) {
-    rho = fmax(rho, fn.rho_floor);
-    inv_g = cbrt(rho) / fn.C - lam;
-  } else {
-    inv_g = fn.inv_4pi_a - lam;
-  }
-  const double g = 1.0 / inv_g;
-  dr = -g * nr;
-  di = -g * ni;
-  if (fn.kind == 0) {
-    const double r13 = cbrt(rho);
-    U = fn.B * fermi_energy(rho) - (dr * dr + di * di) / (3.0 * fn.C * r13 * r13);
-  } else {
-    U = 0.0;
-  }
-}
 
 constexpr int kRegulatorIters = 60;  // fixed-point iterations for the t = 0 regulator
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/wslda_td.h"
@@ -126,6 +127,22 @@ cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double
 // Plane-wave states of a uniform solution (uniform.cu); dst is float2 or double2.
 cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,
                                     const int64_t* kidx_dev, int64_t n, cudaStream_t s);
+
+// Static self-consistent solve (scf.cu): the box buffers it reads and writes.
+struct ScfBox {
+  wslda_lattice lat;
+  FunctionalDev fn;
+  int M;
+  int prec;
+  void* states;  // [M][2][M] complex slot receiving the eigenstates
+  double* sc;    // that slot's per-state scale, set to 1
+  const double* vext;
+  const double* dext;  // zero
+  double *rho, *nu, *delta, *ekin2, *wm, *wp, *out8;
+  cudaStream_t s;
+};
+wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, const wslda_scf_params& p,
+                          double* qpE, wslda_scf_result* res, std::string& err);
 
 template <typename R>
 cudaError_t launch_narrow(const double* src, cx<R>* dst, int64_t ncomplex, int* err, cudaStream_t s);

@@ -1,0 +1,542 @@
+// Static self-consistent solver (Alg. 1, Sec. 3.2) for trapped, spin-symmetric
+// T = 0 systems with real potentials that are symmetric under the reflections
+// i -> N - i (mod N) of each axis (a trap centred on site N/2).
+//
+// The Laplacian of Eq. D2 depends on i - j only and is even in it, so it
+// commutes with the reflections; so do the diagonal fields. In the basis of
+// even and odd combinations per axis,
+//   even: e_0 = d_0, e_{N/2} = d_{N/2}, e_a = (d_a + d_{N-a})/sqrt2  (N/2+1)
+//   odd : o_a = (d_a - d_{N-a})/sqrt2, 0 < a < N/2                  (N/2-1)
+// the 2M x 2M matrix of Eq. HpsiEpsi splits into 8 real symmetric blocks
+// [[h, D], [D, -h]] of size 2 m_b (m_b = product of the per-axis sizes), with
+// h = -L_b/2 + W: the block Laplacian is the Kronecker sum of the per-axis
+// parity blocks of Eq. D2, and W, D are the field values at the block's
+// representative sites. The (u, v) -> (-v, u) symmetry maps E to -E inside
+// each block, so each block holds m_b positive eigenvalues, and the 8 blocks
+// together hold the M positive-energy states.
+//
+// One iteration (map K of Alg. 1, then linear mixing) on the device:
+//   build_block   block matrix from (U_in, Delta_in, V_ext, mu)
+//   cusolverDnDsyevd (library eigensolver, double precision)
+//   block_density rho_sigma, nu at the representative sites (fundamental domain)
+//   block_kinetic <u|T|u>, <v|T|v> of each positive-energy state
+//   scf_fields    densities on the whole lattice, regulator at the input mean
+//                 field, output potentials K[p]
+//   energy terms  (the energy kernel of the time-dependent path)
+//   scf_mix       p <- m K[p] + (1 - m) p
+// and at the end unfold_states writes the eigenstates into the box.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "functional.cuh"
+#include "internal.cuh"
+
+namespace wslda {
+namespace {
+
+struct BlockGeom {
+  int m;                    // sites in the block
+  int mx, my, mz;           // per-axis block sizes
+  int px, py, pz;           // per-axis parity, 0 even, 1 odd
+  int nx, ny, nz;           // lattice
+  const double *Dx, *Dy, *Dz;  // per-axis parity blocks of Eq. D2, row-major
+};
+
+// Lattice coordinate of block index a along an axis: even blocks start at
+// site 0, odd blocks at site 1.
+__device__ __forceinline__ int lattice_site(const BlockGeom& g, int a, int b, int c) {
+  return ((a + g.px) * g.ny + (b + g.py)) * g.nz + (c + g.pz);
+}
+
+__device__ __forceinline__ void decode(const BlockGeom& g, int r, int& a, int& b, int& c) {
+  c = r % g.mz;
+  const int t = r / g.mz;
+  b = t % g.my;
+  a = t / g.my;
+}
+
+__global__ void build_block(BlockGeom g, const double* __restrict__ U, const double* __restrict__ D,
+                            const double* __restrict__ vext, double mu, double* __restrict__ H) {
+  const int64_t n2 = 2 * int64_t(g.m);
+  const int64_t total = n2 * n2;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int col = int(idx / n2), row = int(idx - int64_t(col) * n2);  // column-major
+    const int ru = row >= g.m, cu = col >= g.m;
+    const int r = row - ru * g.m, c = col - cu * g.m;
+    double v = 0.0;
+    if (ru == cu) {
+      int a, b, cc, a2, b2, c2;
+      decode(g, r, a, b, cc);
+      decode(g, c, a2, b2, c2);
+      double L = 0.0;
+      if (b == b2 && cc == c2) L += g.Dx[a * g.mx + a2];
+      if (a == a2 && cc == c2) L += g.Dy[b * g.my + b2];
+      if (a == a2 && b == b2) L += g.Dz[cc * g.mz + c2];
+      double h = -0.5 * L;
+      if (r == c) {
+        const int s = lattice_site(g, a, b, cc);
+        h += U[s] + vext[s] - mu;
+      }
+      v = ru ? -h : h;
+    } else if (r == c) {
+      int a, b, cc;
+      decode(g, r, a, b, cc);
+      v = D[lattice_site(g, a, b, cc)];
+    }
+    H[idx] = v;
+  }
+}
+
+// Weight of a representative site in the density: 1/2 per axis whose
+// coordinate is not a fixed point of the reflection (the basis vector is
+// spread over two sites there).
+__device__ __forceinline__ double orbit_weight(int i, int n) { return (i == 0 || 2 * i == n) ? 1.0 : 0.5; }
+
+// Thread = block row r; sums over the m positive-energy columns.
+__global__ void block_density(BlockGeom g, const double* __restrict__ Z, double inv_dV, double* __restrict__ frho,
+                              double* __restrict__ fnu) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.m) return;
+  const int64_t n2 = 2 * int64_t(g.m);
+  double sr = 0.0, sn = 0.0;
+  for (int j = g.m; j < 2 * g.m; ++j) {
+    const double* col = Z + int64_t(j) * n2;
+    const double cu = col[r], cv = col[g.m + r];
+    sr += cv * cv;
+    sn += cu * cv;
+  }
+  int a, b, c;
+  decode(g, r, a, b, c);
+  const int ix = a + g.px, iy = b + g.py, iz = c + g.pz;
+  const int hy = g.ny / 2 + 1, hz = g.nz / 2 + 1;
+  const double w = orbit_weight(ix, g.nx) * orbit_weight(iy, g.ny) * orbit_weight(iz, g.nz) * inv_dV;
+  const int f = (ix * hy + iy) * hz + iz;
+  frho[f] += w * sr;
+  fnu[f] += w * sn;
+}
+
+// CTA = one positive-energy state (column m + blockIdx.x). The column is
+// staged in shared memory, L_b is applied through its Kronecker structure,
+// and <u|-L/2|u>, <v|-L/2|v> are written as ekin2[2 j], ekin2[2 j + 1].
+__global__ void __launch_bounds__(256) block_kinetic(BlockGeom g, const double* __restrict__ Z,
+                                                     double* __restrict__ ekin2) {
+  extern __shared__ double col[];
+  __shared__ double red[2][8];
+  const int j = blockIdx.x;
+  const int64_t n2 = 2 * int64_t(g.m);
+  const double* src = Z + (int64_t(g.m) + j) * n2;
+  for (int i = threadIdx.x; i < 2 * g.m; i += blockDim.x) col[i] = src[i];
+  __syncthreads();
+  double tu = 0.0, tv = 0.0;
+  for (int r = threadIdx.x; r < g.m; r += blockDim.x) {
+    int a, b, c;
+    decode(g, r, a, b, c);
+    double lu = 0.0, lv = 0.0;
+    for (int k = 0; k < g.mx; ++k) {
+      const double d = g.Dx[a * g.mx + k];
+      const int q = (k * g.my + b) * g.mz + c;
+      lu += d * col[q];
+      lv += d * col[g.m + q];
+    }
+    for (int k = 0; k < g.my; ++k) {
+      const double d = g.Dy[b * g.my + k];
+      const int q = (a * g.my + k) * g.mz + c;
+      lu += d * col[q];
+      lv += d * col[g.m + q];
+    }
+    for (int k = 0; k < g.mz; ++k) {
+      const double d = g.Dz[c * g.mz + k];
+      const int q = (a * g.my + b) * g.mz + k;
+      lu += d * col[q];
+      lv += d * col[g.m + q];
+    }
+    tu += col[r] * lu;
+    tv += col[g.m + r] * lv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tu += __shfl_xor_sync(0xffffffffu, tu, o);
+    tv += __shfl_xor_sync(0xffffffffu, tv, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = tu;
+    red[1][w] = tv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double su = 0.0, sv = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+      su += red[0][i];
+      sv += red[1][i];
+    }
+    ekin2[2 * j] = -0.5 * su;
+    ekin2[2 * j + 1] = -0.5 * sv;
+  }
+}
+
+__device__ __forceinline__ int fold(int i, int n) { return i <= n / 2 ? i : n - i; }
+
+// Densities on the whole lattice from the fundamental domain, regulator at
+// the input mean field, output potentials K[p].
+__global__ void scf_fields(int nx, int ny, int nz, const double* __restrict__ frho, const double* __restrict__ fnu,
+                           const double* __restrict__ Uin, const double* __restrict__ vext, FunctionalDev fn,
+                           double* __restrict__ rho, double* __restrict__ nu, double* __restrict__ Uout,
+                           double* __restrict__ delta) {
+  const int M = nx * ny * nz;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int iz = s % nz, iy = (s / nz) % ny, ix = s / (ny * nz);
+  const int f = (fold(ix, nx) * (ny / 2 + 1) + fold(iy, ny)) * (nz / 2 + 1) + fold(iz, nz);
+  const double r = frho[f], n = fnu[f];
+  const double lam = regulator(fn.mu - Uin[s] - vext[s], fn.ec);
+  double U, dr, di;
+  site_potentials(fn, r, n, 0.0, lam, U, dr, di);
+  rho[s] = r;
+  nu[2 * s] = n;
+  nu[2 * s + 1] = 0.0;
+  Uout[s] = U;
+  delta[2 * s] = dr;
+  delta[2 * s + 1] = di;
+}
+
+__global__ void scf_mix(int M, double m, const double* __restrict__ Uout, const double* __restrict__ delta_out,
+                        double* __restrict__ Uin, double* __restrict__ Din) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  Uin[s] = m * Uout[s] + (1.0 - m) * Uin[s];
+  Din[s] = m * delta_out[2 * s] + (1.0 - m) * Din[s];
+}
+
+// Block index and basis-vector value of lattice coordinate i along an axis of
+// parity p; false where the odd basis vanishes (the two fixed points).
+__device__ __forceinline__ bool axis_basis(int i, int n, int p, int& a, double& f) {
+  const int j = fold(i, n);
+  const bool fixed = (j == 0 || 2 * j == n);
+  if (p == 0) {
+    a = j;
+    f = fixed ? 1.0 : M_SQRT1_2;
+    return true;
+  }
+  if (fixed) return false;
+  a = j - 1;
+  f = i > n / 2 ? -M_SQRT1_2 : M_SQRT1_2;
+  return true;
+}
+
+// Thread = (state j, lattice site s): the block eigenvector expanded on the
+// lattice, scaled to sum_r dV (|u|^2 + |v|^2) = 1.
+template <typename C>
+__global__ void unfold_states(BlockGeom g, const double* __restrict__ Z, double inv_sqrt_dV, C* __restrict__ out) {
+  const int64_t M = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(g.m) * M) return;
+  const int j = int(idx / M);
+  const int s = int(idx - int64_t(j) * M);
+  const int iz = s % g.nz, iy = (s / g.nz) % g.ny, ix = s / (g.ny * g.nz);
+  int a, b, c;
+  double fx, fy, fz;
+  double u = 0.0, v = 0.0;
+  if (axis_basis(ix, g.nx, g.px, a, fx) && axis_basis(iy, g.ny, g.py, b, fy) && axis_basis(iz, g.nz, g.pz, c, fz)) {
+    const double* col = Z + (int64_t(g.m) + j) * 2 * g.m;
+    const int r = (a * g.my + b) * g.mz + c;
+    const double f = fx * fy * fz * inv_sqrt_dV;
+    u = col[r] * f;
+    v = col[g.m + r] * f;
+  }
+  C cu, cv;
+  cu.x = u;
+  cu.y = 0;
+  cv.x = v;
+  cv.y = 0;
+  out[(2 * int64_t(j)) * M + s] = cu;
+  out[(2 * int64_t(j) + 1) * M + s] = cv;
+}
+
+// Eq. D2 of one axis as the spectral second derivative: D_ij = (1/N) sum_l
+// (-k_l^2) cos(k_l (i - j) d), the Nyquist mode kept, then its even and odd
+// parity blocks B^T D B (even block first, both row-major).
+std::vector<double> parity_blocks(int n, double d) {
+  std::vector<double> D(size_t(n) * n);
+  const double L = n * d;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < n; ++l) {
+        const int q = l < n / 2 ? l : l - n;
+        const double k = 2.0 * M_PI * q / L;
+        const long ph = (long(l) * long(((i - j) % n + n) % n)) % n;  // exact phase reduction
+        s += -k * k * std::cos(2.0 * M_PI * double(ph) / n);
+      }
+      D[size_t(i) * n + j] = s / n;
+    }
+  const int ne = n / 2 + 1, no = n / 2 - 1;
+  // basis vectors as (site, coefficient) pairs
+  auto even = [&](int a, int& s0, int& s1, double& c) {
+    s0 = a;
+    s1 = (n - a) % n;
+    c = (a == 0 || 2 * a == n) ? 1.0 : M_SQRT1_2;
+  };
+  std::vector<double> out(size_t(ne) * ne + size_t(no) * no);
+  for (int a = 0; a < ne; ++a)
+    for (int b = 0; b < ne; ++b) {
+      int a0, a1, b0, b1;
+      double ca, cb;
+      even(a, a0, a1, ca);
+      even(b, b0, b1, cb);
+      double v = 0.0;
+      // <e_a| D |e_b>, each basis vector touching one site (fixed points) or two
+      const int na = (a0 == a1) ? 1 : 2, nb = (b0 == b1) ? 1 : 2;
+      for (int x = 0; x < na; ++x)
+        for (int y = 0; y < nb; ++y) v += ca * cb * D[size_t(x ? a1 : a0) * n + (y ? b1 : b0)];
+      out[size_t(a) * ne + b] = v;
+    }
+  double* odd = out.data() + size_t(ne) * ne;
+  for (int a = 0; a < no; ++a)
+    for (int b = 0; b < no; ++b) {
+      const int i0 = a + 1, i1 = n - a - 1, j0 = b + 1, j1 = n - b - 1;
+      const double v = 0.5 * (D[size_t(i0) * n + j0] - D[size_t(i0) * n + j1] - D[size_t(i1) * n + j0] +
+                              D[size_t(i1) * n + j1]);
+      odd[size_t(a) * no + b] = v;
+    }
+  return out;
+}
+
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return e;
+  }
+};
+
+struct SolverHandle {
+  cusolverDnHandle_t h = nullptr;
+  ~SolverHandle() {
+    if (h) cusolverDnDestroy(h);
+  }
+};
+
+}  // namespace
+
+wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, const wslda_scf_params& p,
+                          double* qpE, wslda_scf_result* res, std::string& err) {
+  const int nx = b.lat.nx, ny = b.lat.ny, nz = b.lat.nz;
+  const int M = b.M;
+  const double dV = b.lat.dx * b.lat.dy * b.lat.dz;
+  cudaStream_t s = b.s;
+#define SCF_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return WSLDA_ECUDA;                                     \
+    }                                                         \
+  } while (0)
+
+  // per-axis parity blocks of Eq. D2
+  const int ns[3] = {nx, ny, nz};
+  const double ds[3] = {b.lat.dx, b.lat.dy, b.lat.dz};
+  std::vector<double> tab;
+  size_t off[3][2];
+  int sz[3][2];
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<double> t = parity_blocks(ns[ax], ds[ax]);
+    sz[ax][0] = ns[ax] / 2 + 1;
+    sz[ax][1] = ns[ax] / 2 - 1;
+    off[ax][0] = tab.size();
+    off[ax][1] = tab.size() + size_t(sz[ax][0]) * sz[ax][0];
+    tab.insert(tab.end(), t.begin(), t.end());
+  }
+  Scratch sc;
+  double* dtab;
+  SCF_CUDA(sc.get(&dtab, tab.size()));
+  SCF_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s));
+
+  // the 8 parity blocks, each with its own matrix / eigenvector buffer
+  struct Blk {
+    BlockGeom g;
+    double *Z, *W;
+    int64_t first;  // index of its first state
+  };
+  std::vector<Blk> blks;
+  int64_t first = 0;
+  for (int px = 0; px < 2; ++px)
+    for (int py = 0; py < 2; ++py)
+      for (int pz = 0; pz < 2; ++pz) {
+        BlockGeom g{};
+        g.mx = sz[0][px];
+        g.my = sz[1][py];
+        g.mz = sz[2][pz];
+        g.m = g.mx * g.my * g.mz;
+        if (g.m == 0) continue;
+        g.px = px;
+        g.py = py;
+        g.pz = pz;
+        g.nx = nx;
+        g.ny = ny;
+        g.nz = nz;
+        g.Dx = dtab + off[0][px];
+        g.Dy = dtab + off[1][py];
+        g.Dz = dtab + off[2][pz];
+        Blk k{g, nullptr, nullptr, first};
+        SCF_CUDA(sc.get(&k.Z, size_t(2 * g.m) * size_t(2 * g.m)));
+        SCF_CUDA(sc.get(&k.W, size_t(2 * g.m)));
+        blks.push_back(k);
+        first += g.m;
+      }
+  if (first != M) {
+    err = "parity blocks do not cover the lattice";
+    return WSLDA_EINVAL;
+  }
+
+  SolverHandle sh;
+  if (cusolverDnCreate(&sh.h) != CUSOLVER_STATUS_SUCCESS) {
+    err = "cusolverDnCreate failed";
+    return WSLDA_ECUDA;
+  }
+  cusolverDnSetStream(sh.h, s);
+  int lwork = 0;
+  for (const Blk& k : blks) {
+    int lw = 0;
+    if (cusolverDnDsyevd_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, 2 * k.g.m, k.Z,
+                                    2 * k.g.m, k.W, &lw) != CUSOLVER_STATUS_SUCCESS) {
+      err = "cusolverDnDsyevd_bufferSize failed";
+      return WSLDA_ECUDA;
+    }
+    lwork = std::max(lwork, lw);
+  }
+  double *work, *Uin, *Din, *Uout, *frho, *fnu;
+  int* info;
+  const int nf = (nx / 2 + 1) * (ny / 2 + 1) * (nz / 2 + 1);
+  SCF_CUDA(sc.get(&work, size_t(lwork)));
+  SCF_CUDA(sc.get(&info, blks.size()));
+  SCF_CUDA(sc.get(&Uin, M));
+  SCF_CUDA(sc.get(&Din, M));
+  SCF_CUDA(sc.get(&Uout, M));
+  SCF_CUDA(sc.get(&frho, nf));
+  SCF_CUDA(sc.get(&fnu, nf));
+  SCF_CUDA(cudaMemcpyAsync(Uin, U0, size_t(M) * 8, cudaMemcpyHostToDevice, s));
+  SCF_CUDA(cudaMemcpyAsync(Din, D0, size_t(M) * 8, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<double> ones(M, 1.0), zeros(M, 0.0);
+    SCF_CUDA(cudaMemcpyAsync(b.wm, ones.data(), size_t(M) * 8, cudaMemcpyHostToDevice, s));
+    SCF_CUDA(cudaMemcpyAsync(b.wp, zeros.data(), size_t(M) * 8, cudaMemcpyHostToDevice, s));
+    SCF_CUDA(cudaStreamSynchronize(s));
+  }
+  int max_smem = 0;
+  for (const Blk& k : blks) max_smem = std::max(max_smem, int(2 * k.g.m * sizeof(double)));
+  SCF_CUDA(cudaFuncSetAttribute(block_kinetic, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+
+  FunctionalDev fn = b.fn;
+  const double e_ref = p.e_ref > 0 ? p.e_ref : 0.5;
+  const bool fixed_n = p.n_target > 0;
+  double prev[6] = {0, 0, 0, 0, 0, 0};
+  double cur[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double change = 0.0;
+  int it = 0;
+  bool converged = false;
+  std::vector<std::vector<double>> evals(blks.size());
+  for (it = 1; it <= p.max_iters; ++it) {
+    SCF_CUDA(cudaMemsetAsync(frho, 0, size_t(nf) * 8, s));
+    SCF_CUDA(cudaMemsetAsync(fnu, 0, size_t(nf) * 8, s));
+    for (size_t bi = 0; bi < blks.size(); ++bi) {
+      const Blk& k = blks[bi];
+      const int n2 = 2 * k.g.m;
+      const int64_t tot = int64_t(n2) * n2;
+      const unsigned grid = unsigned(std::min<int64_t>((tot + 255) / 256, 148 * 16));
+      build_block<<<grid, 256, 0, s>>>(k.g, Uin, Din, b.vext, fn.mu, k.Z);
+      SCF_CUDA(cudaGetLastError());
+      if (cusolverDnDsyevd(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n2, k.Z, n2, k.W, work, lwork,
+                           info + bi) != CUSOLVER_STATUS_SUCCESS) {
+        err = "cusolverDnDsyevd failed";
+        return WSLDA_ECUDA;
+      }
+      block_density<<<(k.g.m + 127) / 128, 128, 0, s>>>(k.g, k.Z, 1.0 / dV, frho, fnu);
+      block_kinetic<<<k.g.m, 256, 2 * k.g.m * sizeof(double), s>>>(k.g, k.Z, b.ekin2 + 2 * k.first);
+      SCF_CUDA(cudaGetLastError());
+    }
+    scf_fields<<<(M + 127) / 128, 128, 0, s>>>(nx, ny, nz, frho, fnu, Uin, b.vext, fn, b.rho, b.nu, Uout, b.delta);
+    SCF_CUDA(cudaGetLastError());
+    SCF_CUDA(launch_energy(M, M, fn, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp, dV, b.out8, s));
+    std::vector<int> hinfo(blks.size());
+    SCF_CUDA(cudaMemcpyAsync(cur, b.out8, 7 * 8, cudaMemcpyDeviceToHost, s));
+    SCF_CUDA(cudaMemcpyAsync(hinfo.data(), info, blks.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    for (size_t bi = 0; bi < blks.size(); ++bi) {
+      evals[bi].resize(2 * size_t(blks[bi].g.m));
+      SCF_CUDA(cudaMemcpyAsync(evals[bi].data(), blks[bi].W, evals[bi].size() * 8, cudaMemcpyDeviceToHost, s));
+    }
+    SCF_CUDA(cudaStreamSynchronize(s));
+    for (size_t bi = 0; bi < blks.size(); ++bi) {
+      if (hinfo[bi] != 0) {
+        err = "cusolverDnDsyevd did not converge (info " + std::to_string(hinfo[bi]) + ")";
+        return WSLDA_ECUDA;
+      }
+      const int m = blks[bi].g.m;
+      if (!(evals[bi][m - 1] < 0.0 && evals[bi][m] > 0.0)) {
+        err = "a parity block has a zero quasiparticle energy (its spectrum does not split into m + m)";
+        return WSLDA_EUNSUPPORTED;
+      }
+    }
+    for (int k = 0; k < 7; ++k)
+      if (!std::isfinite(cur[k])) {
+        err = "non-finite energy in the static iteration";
+        return WSLDA_ENAN;
+      }
+    const double n_sigma = 0.5 * cur[6];
+    const bool n_ok = !fixed_n || std::fabs(p.n_target - n_sigma) < p.eps_npart;
+    if (it >= 2) {
+      change = 0.0;
+      for (int k = 0; k < 6; ++k) change = std::max(change, std::fabs(cur[k] - prev[k]) / e_ref);
+      if (change < p.eps_energy && n_ok) {
+        converged = true;
+        break;
+      }
+    }
+    for (int k = 0; k < 6; ++k) prev[k] = cur[k];
+    if (it == p.max_iters) break;
+    if (fixed_n && p.a_mu != 0.0) fn.mu += (p.a_mu / p.n_target) * (p.n_target - n_sigma);  // Eq. update-mu
+    scf_mix<<<(M + 127) / 128, 128, 0, s>>>(M, p.mixing, Uout, b.delta, Uin, Din);
+    SCF_CUDA(cudaGetLastError());
+  }
+  if (it > p.max_iters) it = p.max_iters;
+
+  // the eigenstates of the last matrix become the box's states
+  const double isq = 1.0 / std::sqrt(dV);
+  for (const Blk& k : blks) {
+    const int64_t tot = int64_t(k.g.m) * M;
+    const unsigned grid = unsigned((tot + 255) / 256);
+    if (b.prec == WSLDA_MIXED)
+      unfold_states<float2><<<grid, 256, 0, s>>>(k.g, k.Z, isq, static_cast<float2*>(b.states) + 2 * k.first * M);
+    else
+      unfold_states<double2><<<grid, 256, 0, s>>>(k.g, k.Z, isq, static_cast<double2*>(b.states) + 2 * k.first * M);
+    SCF_CUDA(cudaGetLastError());
+  }
+  SCF_CUDA(launch_fill(b.sc, 1.0, M, s));
+  SCF_CUDA(cudaStreamSynchronize(s));
+  if (qpE)
+    for (size_t bi = 0; bi < blks.size(); ++bi)
+      for (int j = 0; j < blks[bi].g.m; ++j) qpE[blks[bi].first + j] = evals[bi][blks[bi].g.m + j];
+  res->iters = it;
+  res->converged = converged ? 1 : 0;
+  res->mu = fn.mu;
+  res->max_rel_change = change;
+  res->n_sigma = 0.5 * cur[6];
+  res->energy = {cur[0], cur[1], cur[2], cur[3], cur[4], cur[5], cur[6]};
+#undef SCF_CUDA
+  return WSLDA_OK;
+}
+
+}  // namespace wslda

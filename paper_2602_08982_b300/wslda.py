@@ -50,6 +50,17 @@ class Energy(ct.Structure):
     _fields_ = [(k, ct.c_double) for k in ("e_kin", "e_pot", "e_pair", "e_ext", "e_pair_ext", "e_total", "n_part")]
 
 
+class ScfParams(ct.Structure):
+    _fields_ = [("mixing", ct.c_double), ("eps_energy", ct.c_double), ("e_ref", ct.c_double),
+                ("max_iters", ct.c_int), ("n_target", ct.c_double), ("a_mu", ct.c_double),
+                ("eps_npart", ct.c_double)]
+
+
+class ScfResult(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("converged", ct.c_int), ("mu", ct.c_double), ("max_rel_change", ct.c_double),
+                ("n_sigma", ct.c_double), ("energy", Energy)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2602_08982_b300.build`")
@@ -85,6 +96,7 @@ def _load():
         "wslda_set_graph": (I, [P, I, I]),
         "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
+        "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +220,28 @@ class Context:
     def fill_uniform_states(self, box: int, mu_eff: float, delta: float, kidx=None):
         p, keep = _ptr(kidx, np.int64, False)
         self._check(lib.wslda_fill_uniform_states(self._h, box, float(mu_eff), float(delta), p))
+
+    def static_solve(self, box: int, U0, delta0, *, mixing: float = 0.5, eps_energy: float = 1e-6,
+                     e_ref: float = 0.5, max_iters: int = 200, n_target: float = 0.0, a_mu: float = 0.0,
+                     eps_npart: float = 1e-6):
+        """Static self-consistent solve (Alg. 1); the box's states become the
+        positive-energy eigenstates. Returns (result dict, quasiparticle energies)."""
+        M = self._M(box)
+        U0 = np.ascontiguousarray(U0, dtype=np.float64)
+        d0 = np.ascontiguousarray(delta0, dtype=np.float64)
+        if U0.size != M or d0.size != M:
+            raise ValueError("U0 and delta0 need M real values")
+        E = np.empty(M)
+        prm = ScfParams(float(mixing), float(eps_energy), float(e_ref), int(max_iters), float(n_target),
+                        float(a_mu), float(eps_npart))
+        out = ScfResult()
+        self._check(lib.wslda_static_solve(self._h, box, U0.ctypes.data_as(ct.c_void_p),
+                                           d0.ctypes.data_as(ct.c_void_p), ct.byref(prm),
+                                           E.ctypes.data_as(ct.c_void_p), ct.byref(out)))
+        res = {k: getattr(out, k) for k, _ in ScfResult._fields_ if k != "energy"}
+        res["converged"] = bool(res["converged"])
+        res["energy"] = {k: getattr(out.energy, k) for k, _ in Energy._fields_}
+        return res, E
 
     def start(self, stationary: bool, dt: float):
         self._check(lib.wslda_start(self._h, int(bool(stationary)), float(dt)))
