@@ -208,7 +208,11 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, d
  * second iteration on, every energy term of Sec. 3.2 and the total change by
  * less than eps_energy * e_ref between consecutive iterations (Eq. E-conv) and,
  * with a particle-number target, |N_req - N_sigma| < eps_npart (Eq. N-conv);
- * with a target, mu follows Eq. update-mu once per iteration, unmixed.
+ * with a target, Eq. update-mu is one more step of K and mu is mixed with the
+ * potentials. method 1 replaces the linear mixing by modified Broyden mixing
+ * (Sec. 3.2; D. D. Johnson, Phys. Rev. B 38, 12807 (1988), weights 1 and w_0,
+ * the last broyden_memory iterations) of the vector (U, Delta, mu), with
+ * alpha = mixing; its first iteration mixes linearly.
  *  - Requirements: the box holds nstates = M states; V_ext, U0 and delta0 are
  *    real and symmetric under the reflections i -> N - i (mod N) of every axis
  *    (a potential centred on site N/2); Delta_ext is zero. The problem is then
@@ -230,6 +234,9 @@ typedef struct {
   double n_target;   /* Eq. update-mu target N_sigma; <= 0: fixed mu */
   double a_mu;       /* Eq. update-mu step size */
   double eps_npart;  /* Eq. N-conv tolerance */
+  int method;        /* 0 linear mixing, 1 modified Broyden mixing */
+  int broyden_memory;   /* iterations kept, 1..8; <= 0: 7 */
+  double broyden_w0;    /* regularisation weight w_0; <= 0: 0.01 */
 } wslda_scf_params;
 typedef struct {
   int iters, converged;

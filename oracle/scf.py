@@ -27,12 +27,19 @@ Readings (the same on the CUDA side):
       that the functional has (kinetic, potential, pairing, external
       potential, external pairing) and their total must change by less than
       eps_energy times that scale between two consecutive iterations.
-  S3  With a particle-number target, mu follows Eq. update-mu once per
-      iteration, outside the linear mixing; N counts one spin species,
-      N_sigma = int rho_sigma.
+  S3  With a particle-number target, Eq. update-mu is one more step of the
+      map (as Sec. 3.2 puts it), so mu_out joins the mixed vector: linear
+      mixing gives mu <- m mu_out + (1 - m) mu, and Broyden mixing carries mu
+      as one more component. N counts one spin species, N_sigma = int rho_sigma.
   S4  The first iteration has no predecessor, so convergence is tested from
       the second iteration on; the returned states are the eigenstates of
       the last matrix diagonalised, and the returned potentials are its input.
+  S5  The Broyden option (Sec. 3.2 lists it beside linear mixing) is the
+      modified Broyden mixing of D. D. Johnson, Phys. Rev. B 38, 12807 (1988),
+      in the form used for nuclear DFT by A. Baran et al., Phys. Rev. C 78,
+      014318 (2008): all weights 1, w_0 = 0.01, the last 7 iterations kept, on
+      the vector p = (U, Re Delta) (real problems). The first iteration mixes
+      linearly.
 
 Pins (tests/test_oracle_scf.py): uniform BdG and SLDA fixed points equal the
 lattice seeds solved from the number and gap equations alone, the BdG
@@ -99,15 +106,51 @@ class SCFResult:
     history: list = field(default_factory=list)    # energy dict per iteration
 
 
+class Broyden:
+    """Modified Broyden mixing (reading S5). With p_n the input and
+    F_n = K[p_n] - p_n the residual of iteration n, each step stores
+    dF = (F_n - F_{n-1}) / |F_n - F_{n-1}|, u = alpha dF + (p_n - p_{n-1}) / |F_n - F_{n-1}|
+    and proposes p_{n+1} = p_n + alpha F_n - sum_j gamma_j u_j with
+    gamma = c (w0^2 I + A)^{-1}, A_ij = dF_i . dF_j, c_i = dF_i . F_n."""
+
+    def __init__(self, alpha: float, memory: int = 7, w0: float = 0.01):
+        self.alpha, self.memory, self.w0 = alpha, memory, w0
+        self.dF, self.u = [], []
+        self.prev = None
+
+    def next(self, p, F):
+        if self.prev is not None:
+            p0, F0 = self.prev
+            d = F - F0
+            nrm = np.sqrt(d @ d)
+            self.dF.append(d / nrm)
+            self.u.append(self.alpha * d / nrm + (p - p0) / nrm)
+            self.dF, self.u = self.dF[-self.memory:], self.u[-self.memory:]
+        self.prev = (p.copy(), F.copy())
+        step = p + self.alpha * F
+        if self.dF:
+            k = len(self.dF)
+            A = np.array([[self.dF[i] @ self.dF[j] for j in range(k)] for i in range(k)])
+            beta = np.linalg.inv(self.w0 ** 2 * np.eye(k) + A)
+            c = np.array([self.dF[i] @ F for i in range(k)])
+            gamma = c @ beta
+            step = step - sum(gamma[j] * self.u[j] for j in range(k))
+        return step
+
+
 def static_solve(lat: o.Lattice, fn: o.Functional, vext, U0, delta0, mixing: float = 0.5,
                  eps_energy: float = 1e-6, e_ref: float = 0.5, max_iters: int = 200,
                  n_target: float | None = None, a_mu: float = 0.0, eps_npart: float = 1e-6,
-                 dext=None) -> SCFResult:
-    """Linear mixing of the potentials (Sec. 3.2, 'Linear mixing') until the
-    energy criterion of Eq. E-conv holds (and Eq. N-conv with a target N)."""
+                 dext=None, method: str = "linear", broyden_memory: int = 7,
+                 broyden_w0: float = 0.01) -> SCFResult:
+    """Linear mixing (Sec. 3.2, 'Linear mixing') or modified Broyden mixing
+    (reading S5) of the potentials until the energy criterion of Eq. E-conv
+    holds (and Eq. N-conv with a target N). The Broyden option requires real
+    potentials."""
     U = np.array(U0, dtype=np.float64)
     delta = np.array(delta0, dtype=np.complex128)
     mu = fn.mu
+    mixer = Broyden(mixing, broyden_memory, broyden_w0) if method == "broyden" else None
     hist = []
     out = None
     converged = False
@@ -125,9 +168,16 @@ def static_solve(lat: o.Lattice, fn: o.Functional, vext, U0, delta0, mixing: flo
                 break
         if it == max_iters:
             break
-        if n_target is not None and a_mu != 0.0:
-            mu = mu + (a_mu / n_target) * (n_target - n_sigma)          # Eq. update-mu
-        U = mixing * out.U + (1.0 - mixing) * U
-        delta = mixing * out.delta + (1.0 - mixing) * delta
+        # Eq. update-mu is a step of the map: mu_out joins the mixed vector (reading S3)
+        mu_out = mu + (a_mu / n_target) * (n_target - n_sigma) if n_target is not None else mu
+        if mixer is None:
+            U = mixing * out.U + (1.0 - mixing) * U
+            delta = mixing * out.delta + (1.0 - mixing) * delta
+            mu = mixing * mu_out + (1.0 - mixing) * mu
+        else:
+            p = np.concatenate([U, delta.real, [mu]])
+            F = np.concatenate([out.U, out.delta.real, [mu_out]]) - p
+            p = mixer.next(p, F)
+            U, delta, mu = p[:lat.M], p[lat.M:2 * lat.M] + 0j, float(p[-1])
     return SCFResult(phi=out.phi, E=out.E, U=U, delta=delta, mu=mu, iters=it, converged=converged,
                      last=out, history=hist)

@@ -23,7 +23,8 @@
 //   scf_fields    densities on the whole lattice, regulator at the input mean
 //                 field, output potentials K[p]
 //   energy terms  (the energy kernel of the time-dependent path)
-//   scf_mix       p <- m K[p] + (1 - m) p
+//   scf_mix       p <- m K[p] + (1 - m) p, or the modified Broyden update
+//                 (broyden_* kernels, multi_dot, a k x k solve on the host)
 // and at the end unfold_states writes the eigenstates into the box.
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
@@ -211,6 +212,79 @@ __global__ void scf_mix(int M, double m, const double* __restrict__ Uout, const 
   if (s >= M) return;
   Uin[s] = m * Uout[s] + (1.0 - m) * Uin[s];
   Din[s] = m * delta_out[2 * s] + (1.0 - m) * Din[s];
+}
+
+// Modified Broyden mixing on the vector x = (U, Re Delta, mu) of length 2M + 1.
+// Residual F = K[x] - x; the mu component comes from the host.
+__global__ void broyden_residual(int M, const double* __restrict__ Uout, const double* __restrict__ delta_out,
+                                 double mu, double mu_out, double* __restrict__ x, double* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) F[i] = Uout[i] - x[i];
+  else if (i < 2 * M) F[i] = delta_out[2 * (i - M)] - x[i];
+  else if (i == 2 * M) {
+    x[i] = mu;
+    F[i] = mu_out - mu;
+  }
+}
+
+// dF <- F - F_prev, u <- x - x_prev
+__global__ void broyden_diff(int n, const double* __restrict__ F, const double* __restrict__ Fp,
+                             const double* __restrict__ x, const double* __restrict__ xp, double* __restrict__ dF,
+                             double* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dF[i] = F[i] - Fp[i];
+  u[i] = x[i] - xp[i];
+}
+
+// dF <- dF / |dF|, u <- alpha dF / |dF| + u / |dF|
+__global__ void broyden_scale(int n, double inv_norm, double alpha, double* __restrict__ dF, double* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = dF[i] * inv_norm;
+  dF[i] = d;
+  u[i] = alpha * d + u[i] * inv_norm;
+}
+
+constexpr int kMaxDots = 17;
+constexpr int kDotBlocks = 64;
+struct DotList {
+  const double* a[kMaxDots];
+  const double* b[kMaxDots];
+  int count;
+};
+
+// partial[d][block] = sum over the block's elements of a_d . b_d; the host adds
+// the partials in block order.
+__global__ void __launch_bounds__(256) multi_dot(DotList L, int n, double* __restrict__ partial) {
+  __shared__ double red[8];
+  for (int d = 0; d < L.count; ++d) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += L.a[d][i] * L.b[d][i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+      partial[d * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// x <- x + alpha F - sum_j gamma_j u_j (j in chronological order)
+struct GammaList {
+  const double* u[8];
+  double g[8];
+  int count;
+};
+__global__ void broyden_update(int n, double alpha, const double* __restrict__ F, GammaList G, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double corr = 0.0;
+  for (int j = 0; j < G.count; ++j) corr += G.g[j] * G.u[j][i];
+  x[i] = x[i] + alpha * F[i] - corr;
 }
 
 // Block index and basis-vector value of lattice coordinate i along an axis of
@@ -423,8 +497,12 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
   const int nf = (nx / 2 + 1) * (ny / 2 + 1) * (nz / 2 + 1);
   SCF_CUDA(sc.get(&work, size_t(lwork)));
   SCF_CUDA(sc.get(&info, blks.size()));
-  SCF_CUDA(sc.get(&Uin, M));
-  SCF_CUDA(sc.get(&Din, M));
+  // x = (U_in, Delta_in, mu): the mixed vector; mu lives on the host between iterations
+  const int nvec = 2 * M + 1;
+  double* xvec;
+  SCF_CUDA(sc.get(&xvec, size_t(nvec)));
+  Uin = xvec;
+  Din = xvec + M;
   SCF_CUDA(sc.get(&Uout, M));
   SCF_CUDA(sc.get(&frho, nf));
   SCF_CUDA(sc.get(&fnu, nf));
@@ -439,6 +517,37 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
   int max_smem = 0;
   for (const Blk& k : blks) max_smem = std::max(max_smem, int(2 * k.g.m * sizeof(double)));
   SCF_CUDA(cudaFuncSetAttribute(block_kinetic, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+
+  // modified Broyden state: ring of (dF, u) pairs, previous x and F, dot partials
+  const bool broyden = p.method == 1;
+  const int mem = p.broyden_memory > 0 ? std::min(p.broyden_memory, 8) : 7;
+  const double w0 = p.broyden_w0 > 0 ? p.broyden_w0 : 0.01;
+  double *bF = nullptr, *bxp = nullptr, *bFp = nullptr, *bdF = nullptr, *bu = nullptr, *bpart = nullptr;
+  if (broyden) {
+    SCF_CUDA(sc.get(&bF, size_t(nvec)));
+    SCF_CUDA(sc.get(&bxp, size_t(nvec)));
+    SCF_CUDA(sc.get(&bFp, size_t(nvec)));
+    SCF_CUDA(sc.get(&bdF, size_t(mem) * nvec));
+    SCF_CUDA(sc.get(&bu, size_t(mem) * nvec));
+    SCF_CUDA(sc.get(&bpart, size_t(kMaxDots) * kDotBlocks));
+  }
+  int bcount = 0, bhead = 0;       // stored pairs, next ring slot
+  bool bprev = false;              // previous (x, F) present
+  std::vector<std::vector<double>> A(mem, std::vector<double>(mem, 0.0));  // dF_i . dF_j by ring slot
+  auto dots = [&](const DotList& L, std::vector<double>& outv) -> cudaError_t {
+    multi_dot<<<kDotBlocks, 256, 0, s>>>(L, nvec, bpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<double> h(size_t(L.count) * kDotBlocks);
+    e = cudaMemcpyAsync(h.data(), bpart, h.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    outv.assign(L.count, 0.0);
+    for (int d = 0; d < L.count; ++d)
+      for (int k = 0; k < kDotBlocks; ++k) outv[d] += h[size_t(d) * kDotBlocks + k];
+    return e;
+  };
+  const unsigned vgrid = unsigned((nvec + 255) / 256);
 
   FunctionalDev fn = b.fn;
   const double e_ref = p.e_ref > 0 ? p.e_ref : 0.5;
@@ -507,9 +616,88 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
     }
     for (int k = 0; k < 6; ++k) prev[k] = cur[k];
     if (it == p.max_iters) break;
-    if (fixed_n && p.a_mu != 0.0) fn.mu += (p.a_mu / p.n_target) * (p.n_target - n_sigma);  // Eq. update-mu
-    scf_mix<<<(M + 127) / 128, 128, 0, s>>>(M, p.mixing, Uout, b.delta, Uin, Din);
+    // Eq. update-mu is a step of the map; mu_out is mixed with the potentials
+    const double mu_out = fixed_n ? fn.mu + (p.a_mu / p.n_target) * (p.n_target - n_sigma) : fn.mu;
+    if (!broyden) {
+      scf_mix<<<(M + 127) / 128, 128, 0, s>>>(M, p.mixing, Uout, b.delta, Uin, Din);
+      SCF_CUDA(cudaGetLastError());
+      fn.mu = p.mixing * mu_out + (1.0 - p.mixing) * fn.mu;
+      continue;
+    }
+    broyden_residual<<<vgrid, 256, 0, s>>>(M, Uout, b.delta, fn.mu, mu_out, xvec, bF);
     SCF_CUDA(cudaGetLastError());
+    if (bprev) {
+      const int slot = bhead;
+      double* dF = bdF + size_t(slot) * nvec;
+      double* u = bu + size_t(slot) * nvec;
+      broyden_diff<<<vgrid, 256, 0, s>>>(nvec, bF, bFp, xvec, bxp, dF, u);
+      SCF_CUDA(cudaGetLastError());
+      DotList L{};
+      L.a[0] = dF;
+      L.b[0] = dF;
+      L.count = 1;
+      std::vector<double> nn;
+      SCF_CUDA(dots(L, nn));
+      if (!(nn[0] > 0.0)) {
+        err = "Broyden mixing: two consecutive residuals are equal";
+        return WSLDA_ENAN;
+      }
+      const double inv = 1.0 / std::sqrt(nn[0]);
+      broyden_scale<<<vgrid, 256, 0, s>>>(nvec, inv, p.mixing, dF, u);
+      SCF_CUDA(cudaGetLastError());
+      bhead = (bhead + 1) % mem;
+      bcount = std::min(bcount + 1, mem);
+    }
+    // chronological ring slots of the stored pairs
+    std::vector<int> order(bcount);
+    for (int j = 0; j < bcount; ++j) order[j] = ((bhead - bcount + j) % mem + mem) % mem;
+    GammaList G{};
+    G.count = bcount;
+    if (bcount > 0) {
+      const int newest = order[bcount - 1];
+      DotList L{};
+      for (int j = 0; j < bcount; ++j) {  // new row of A, then c_j = dF_j . F
+        L.a[j] = bdF + size_t(newest) * nvec;
+        L.b[j] = bdF + size_t(order[j]) * nvec;
+        L.a[bcount + j] = bdF + size_t(order[j]) * nvec;
+        L.b[bcount + j] = bF;
+      }
+      L.count = 2 * bcount;
+      std::vector<double> dv;
+      SCF_CUDA(dots(L, dv));
+      for (int j = 0; j < bcount; ++j) A[newest][order[j]] = A[order[j]][newest] = dv[j];
+      // gamma = (w0^2 I + A)^{-1} c, by Gaussian elimination with partial pivoting
+      const int k = bcount;
+      std::vector<double> m(size_t(k) * (k + 1));
+      for (int i = 0; i < k; ++i) {
+        for (int j = 0; j < k; ++j) m[size_t(i) * (k + 1) + j] = A[order[i]][order[j]] + (i == j ? w0 * w0 : 0.0);
+        m[size_t(i) * (k + 1) + k] = dv[k + i];
+      }
+      for (int c = 0; c < k; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < k; ++r)
+          if (std::fabs(m[size_t(r) * (k + 1) + c]) > std::fabs(m[size_t(piv) * (k + 1) + c])) piv = r;
+        if (piv != c)
+          for (int j = 0; j <= k; ++j) std::swap(m[size_t(c) * (k + 1) + j], m[size_t(piv) * (k + 1) + j]);
+        for (int r = c + 1; r < k; ++r) {
+          const double f = m[size_t(r) * (k + 1) + c] / m[size_t(c) * (k + 1) + c];
+          for (int j = c; j <= k; ++j) m[size_t(r) * (k + 1) + j] -= f * m[size_t(c) * (k + 1) + j];
+        }
+      }
+      for (int r = k - 1; r >= 0; --r) {
+        double v = m[size_t(r) * (k + 1) + k];
+        for (int j = r + 1; j < k; ++j) v -= m[size_t(r) * (k + 1) + j] * G.g[j];
+        G.g[r] = v / m[size_t(r) * (k + 1) + r];
+      }
+      for (int j = 0; j < k; ++j) G.u[j] = bu + size_t(order[j]) * nvec;
+    }
+    SCF_CUDA(cudaMemcpyAsync(bxp, xvec, size_t(nvec) * 8, cudaMemcpyDeviceToDevice, s));
+    SCF_CUDA(cudaMemcpyAsync(bFp, bF, size_t(nvec) * 8, cudaMemcpyDeviceToDevice, s));
+    bprev = true;
+    broyden_update<<<vgrid, 256, 0, s>>>(nvec, p.mixing, bF, G, xvec);
+    SCF_CUDA(cudaGetLastError());
+    SCF_CUDA(cudaMemcpyAsync(&fn.mu, xvec + 2 * M, 8, cudaMemcpyDeviceToHost, s));
+    SCF_CUDA(cudaStreamSynchronize(s));
   }
   if (it > p.max_iters) it = p.max_iters;
 

@@ -109,3 +109,27 @@ def test_converged_trap_states_are_stationary_under_the_td_rhs(trapped):
     f = o.rhs_f(r.phi, F, lat)
     assert np.abs(f).max() < 1e-9 * np.abs(Hphi).max()
     assert np.abs(o.expectation(r.phi, Hphi, lat) - r.E).max() < 1e-9 * r.E.max()
+
+
+def test_broyden_reaches_the_linear_mixing_fixed_point_faster(trapped):
+    lat, fn, v, res = trapped
+    sd, _ = _bdg(lat, 1.0)
+    rb = scf.static_solve(lat, fn, v, np.zeros(lat.M), np.full(lat.M, sd.delta), mixing=0.5, eps_energy=1e-11,
+                          max_iters=300, method="broyden")
+    assert rb.converged and rb.iters < res[1.0].iters // 3
+    scale = np.abs(res[1.0].delta).max()
+    assert np.abs(rb.delta - res[1.0].delta).max() < 1e-8 * scale
+    assert np.abs(np.sort(rb.E) - np.sort(res[1.0].E)).max() < 1e-9 * rb.E.max()
+
+
+def test_broyden_with_mu_update_reaches_the_slda_seed():
+    lat = o.Lattice(6, 6, 6)
+    sd = o.uniform_slda_seed(lat, 0.25, RHO_S)
+    fn = o.Functional("slda", B=o.B_SLDA, C=sd.C, mu=sd.mu + 0.05)
+    n_req = RHO_S * lat.volume
+    r = scf.static_solve(lat, fn, np.zeros(lat.M), np.full(lat.M, 0.9 * sd.U), np.full(lat.M, 0.9 * sd.delta),
+                         eps_energy=1e-9, max_iters=100, n_target=n_req, a_mu=0.5, eps_npart=1e-8,
+                         method="broyden")
+    assert r.converged and r.iters < 40
+    assert abs(r.mu - sd.mu) < 1e-8
+    assert np.abs(r.U - sd.U).max() < 1e-8 and np.abs(r.delta - sd.delta).max() < 1e-8
