@@ -153,7 +153,8 @@ wslda_status wslda_check_conservation(wslda_ctx* ctx, int box, double e_tol, dou
 wslda_status wslda_eval_f(wslda_ctx* ctx, int box, double* f);
 
 /* Save / restore the full integrator state (states, history, regulator,
- * time and step counter) to a file; resuming is bit-identical. */
+ * time and step counter, and the stage-kernel launch variant) to a file;
+ * resuming is bit-identical when the loading library has that variant. */
 wslda_status wslda_save(wslda_ctx* ctx, const char* path);
 wslda_status wslda_load(wslda_ctx* ctx, const char* path);
 

@@ -16,25 +16,25 @@ One application of K, with no blocking, symmetry reduction or reordering:
      eigenpairs with E_n > 0, normalised as sum_r dV (|u|^2 + |v|^2) = 1;
   3. densities rho_sigma, nu of those states (T = 0 weights);
   4. potentials (U, Delta) from the densities, the regulator Lambda_c
-     recomputed from the input mean field (reading S1).
+     recomputed from the input mean field (reading K1).
 
 Readings (the same on the CUDA side):
-  S1  Lambda_c of Eq. Creg is evaluated every iteration at V = U_in + V_ext
+  K1  Lambda_c of Eq. Creg is evaluated every iteration at V = U_in + V_ext
       with the input mean field of that iteration (it is frozen only during
       time evolution, reading R2 of the TD oracle).
-  S2  The energy scale of Eq. E-conv is the Fermi energy of the reference
+  K2  The energy scale of Eq. E-conv is the Fermi energy of the reference
       uniform system (1/2 for k_F = 1); every energy term listed in Sec. 3.2
       that the functional has (kinetic, potential, pairing, external
       potential, external pairing) and their total must change by less than
       eps_energy times that scale between two consecutive iterations.
-  S3  With a particle-number target, Eq. update-mu is one more step of the
+  K3  With a particle-number target, Eq. update-mu is one more step of the
       map (as Sec. 3.2 puts it), so mu_out joins the mixed vector: linear
       mixing gives mu <- m mu_out + (1 - m) mu, and Broyden mixing carries mu
       as one more component. N counts one spin species, N_sigma = int rho_sigma.
-  S4  The first iteration has no predecessor, so convergence is tested from
+  K4  The first iteration has no predecessor, so convergence is tested from
       the second iteration on; the returned states are the eigenstates of
       the last matrix diagonalised, and the returned potentials are its input.
-  S5  The Broyden option (Sec. 3.2 lists it beside linear mixing) is the
+  K5  The Broyden option (Sec. 3.2 lists it beside linear mixing) is the
       modified Broyden mixing of D. D. Johnson, Phys. Rev. B 38, 12807 (1988),
       in the form used for nuclear DFT by A. Baran et al., Phys. Rev. C 78,
       014318 (2008): all weights 1, w_0 = 0.01, the last 7 iterations kept, on
@@ -67,7 +67,7 @@ class MapOutput:
     nu: np.ndarray
     U: np.ndarray         # output potentials K[p]
     delta: np.ndarray
-    lam: np.ndarray       # regulator used (reading S1)
+    lam: np.ndarray       # regulator used (reading K1)
     energy: dict
 
 
@@ -85,7 +85,7 @@ def map_K(lat: o.Lattice, fn: o.Functional, vext, U_in, delta_in, dext=None) -> 
     # step 3: densities (T = 0)
     wm, wp = np.ones(M), np.zeros(M)
     rho, nu = o.densities(phi, wm, wp)
-    # step 4: potentials, regulator at the input mean field (reading S1)
+    # step 4: potentials, regulator at the input mean field (reading K1)
     lam = o.lambda_c(fn.mu - U_in - vext, fn.cutoff(lat))
     U_out, delta_out, _ = o.potentials(rho, nu, lam, fn)
     sysm = o.TDSystem(lat, fn, vext=vext, dext=dext, lam=lam)
@@ -107,7 +107,7 @@ class SCFResult:
 
 
 class Broyden:
-    """Modified Broyden mixing (reading S5). With p_n the input and
+    """Modified Broyden mixing (reading K5). With p_n the input and
     F_n = K[p_n] - p_n the residual of iteration n, each step stores
     dF = (F_n - F_{n-1}) / |F_n - F_{n-1}|, u = alpha dF + (p_n - p_{n-1}) / |F_n - F_{n-1}|
     and proposes p_{n+1} = p_n + alpha F_n - sum_j gamma_j u_j with
@@ -144,7 +144,7 @@ def static_solve(lat: o.Lattice, fn: o.Functional, vext, U0, delta0, mixing: flo
                  dext=None, method: str = "linear", broyden_memory: int = 7,
                  broyden_w0: float = 0.01) -> SCFResult:
     """Linear mixing (Sec. 3.2, 'Linear mixing') or modified Broyden mixing
-    (reading S5) of the potentials until the energy criterion of Eq. E-conv
+    (reading K5) of the potentials until the energy criterion of Eq. E-conv
     holds (and Eq. N-conv with a target N). The Broyden option requires real
     potentials."""
     U = np.array(U0, dtype=np.float64)
@@ -168,7 +168,7 @@ def static_solve(lat: o.Lattice, fn: o.Functional, vext, U0, delta0, mixing: flo
                 break
         if it == max_iters:
             break
-        # Eq. update-mu is a step of the map: mu_out joins the mixed vector (reading S3)
+        # Eq. update-mu is a step of the map: mu_out joins the mixed vector (reading K3)
         mu_out = mu + (a_mu / n_target) * (n_target - n_sigma) if n_target is not None else mu
         if mixer is None:
             U = mixing * out.U + (1.0 - mixing) * U

@@ -42,6 +42,7 @@ struct Box {
   int64_t n = 0;
   int M = 0;
   const KernelSet* ks = nullptr;
+  int ncl = 0;           // persistent stage launches: clusters (0 = one cluster per state)
   size_t csize = 0;      // bytes per complex element (8 or 16)
   void* slot[5] = {};    // state buffers [n][2][M]
   int iphi = 0, ih[4] = {1, 2, 3, 4};
@@ -279,7 +280,7 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
   ProfScope ps(c, kind);
-  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), c->cur));
+  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), b.ncl, c->cur));
   c->launches += 1;
   const bool norm_out = mode == MODE_X || mode == MODE_Y || (mode == MODE_HORNER && a.normalize);
   if (norm_out) {
@@ -397,13 +398,25 @@ wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
 // the fastest. The choice is cached per shape and precision for the process.
 template <typename R>
 wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
-  static std::vector<std::pair<std::vector<int>, int>> cache;
+  // cache: (precision, shape, states) -> (variant, persistent clusters)
+  static std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> cache;
+  if (b.n == 0) return WSLDA_OK;
+  // WSLDA_VARIANT=<i> fixes the variant, WSLDA_PERSIST=0/1 the launch form
+  const char* forced = getenv("WSLDA_VARIANT");
+  const char* pers = getenv("WSLDA_PERSIST");
+  const int pmode = pers ? (atoi(pers) ? 1 : 0) : -1;
   std::vector<const KernelSet*> v = find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
-  if (v.size() < 2 || getenv("WSLDA_VARIANT") || b.n == 0) return WSLDA_OK;
-  const std::vector<int> key = {c->prec, b.lat.nx, b.lat.ny, b.lat.nz};
+  if (forced) v.assign(1, b.ks);
+  if (v.size() == 1 && pmode >= 0) {
+    b.ncl = pmode ? resident_clusters(b.ks) : 0;
+    return WSLDA_OK;
+  }
+  const std::vector<int64_t> key = {c->prec, b.lat.nx, b.lat.ny, b.lat.nz, std::min<int64_t>(b.n, 512),
+                                    forced ? 1 : 0, pmode};
   for (auto& e : cache)
     if (e.first == key) {
-      b.ks = v[e.second];
+      b.ks = v[e.second.first];
+      b.ncl = e.second.second;
       return WSLDA_OK;
     }
   const int64_t nt = std::min<int64_t>(b.n, 512);
@@ -414,42 +427,52 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
   CUDA_TRY(c, cudaEventCreate(&e1));
-  int best = 0;
+  int best = 0, best_ncl = 0;
   float best_ms = 1e30f;
   for (size_t k = 0; k < v.size(); ++k) {
-    if (resident_clusters(v[k]) < 1) continue;
-    StageArgs<R> a = base_args<R>(b, box_dV(b));
-    a.phi = static_cast<cx<R>*>(b.ptr(b.ih[0]));
-    a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[1]));
-    a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
-    a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
-    a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
-    a.sc_in = b.sc[b.ih[0]];
-    a.sc_out = b.sc[b.ih[1]];
-    a.dt = dt;
-    a.err = c->err_d;
-    float ms = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
-      CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-      CUDA_TRY(c, v[k]->launch[MODE_X](&a, int(nt), c->stream));
-      CUDA_TRY(c, cudaEventRecord(e1, c->stream));
-      CUDA_TRY(c, cudaEventSynchronize(e1));
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      if (rep > 0) ms = std::min(ms, t);
-    }
-    if (getenv("WSLDA_TUNE_VERBOSE"))
-      fprintf(stderr, "[wslda autotune] %dx%dx%d prec=%d variant %zu (cluster=%d threads=%d lanes=%d,%d,%d): %.3f ms\n",
-              b.lat.nx, b.lat.ny, b.lat.nz, c->prec, k, v[k]->cs, v[k]->bt, v[k]->tx, v[k]->ty, v[k]->tz, ms);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = int(k);
+    const int res = resident_clusters(v[k]);
+    if (res < 1) continue;
+    for (int mode = 0; mode < 2; ++mode) {
+      if (pmode >= 0 && mode != pmode) continue;
+      const int ncl = mode ? res : 0;
+      StageArgs<R> a = base_args<R>(b, box_dV(b));
+      a.phi = static_cast<cx<R>*>(b.ptr(b.ih[0]));
+      a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[1]));
+      a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
+      a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
+      a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+      a.sc_in = b.sc[b.ih[0]];
+      a.sc_out = b.sc[b.ih[1]];
+      a.dt = dt;
+      a.err = c->err_d;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+        CUDA_TRY(c, v[k]->launch[MODE_X](&a, int(nt), ncl, c->stream));
+        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms = std::min(ms, t);
+      }
+      if (getenv("WSLDA_TUNE_VERBOSE"))
+        fprintf(stderr,
+                "[wslda autotune] %dx%dx%d prec=%d variant %zu (cluster=%d threads=%d lanes=%d,%d,%d) "
+                "clusters=%s: %.3f ms\n",
+                b.lat.nx, b.lat.ny, b.lat.nz, c->prec, k, v[k]->cs, v[k]->bt, v[k]->tx, v[k]->ty, v[k]->tz,
+                ncl ? std::to_string(ncl).c_str() : "per-state", ms);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = int(k);
+        best_ncl = ncl;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b.ks = v[best];
-  cache.push_back({key, best});
+  b.ncl = best_ncl;
+  cache.push_back({key, {best, best_ncl}});
   return WSLDA_OK;
 }
 
@@ -713,9 +736,7 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.fdev.mu = fn->mu;
   b.fdev.ec = fn->ec > 0 ? fn->ec : default_cutoff(*lat);
   b.fdev.rho_floor = fn->rho_floor > 0 ? fn->rho_floor : 1e-12;
-  const int sites_blocks = int((M + 255) / 256);
-  b.nchunk = int(std::max<int64_t>(1, std::min<int64_t>({256, (16 * 148 + sites_blocks - 1) / sites_blocks,
-                                                          std::max<int64_t>(1, nstates / 16)})));
+  b.nchunk = density_chunks(int(M), nstates, prec == WSLDA_MIXED);
   b.chunk = std::max<int64_t>(1, (nstates + b.nchunk - 1) / b.nchunk);
 
   const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
@@ -1160,8 +1181,9 @@ wslda_status wslda_get_variant(wslda_ctx* c, int box, char* desc, int len) {
   CHECK_CTX(c);
   Box* b = get_box(c, box);
   if (!b || !desc || len <= 0) return fail(c, WSLDA_EINVAL, "get_variant: bad arguments");
-  snprintf(desc, size_t(len), "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu", b->ks->cs,
-           b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem);
+  snprintf(desc, size_t(len),
+           "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu persistent_clusters=%d", b->ks->cs,
+           b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem, b->ncl);
   return WSLDA_OK;
 }
 
@@ -1246,7 +1268,7 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(c, WSLDA_EINVAL, std::string("save: cannot open ") + path);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '1'};
+  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '2'};
   int32_t hdr[3] = {c->prec, int32_t(c->boxes.size()), c->started ? 1 : 0};
   fwrite(magic, 1, 8, f);
   fwrite(hdr, sizeof(hdr), 1, f);
@@ -1261,7 +1283,10 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   };
   bool ok = true;
   for (Box& b : c->boxes) {
-    int64_t bh[9] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3]};
+    // the launch variant travels with the state, so that a resumed run uses the
+    // same kernels (different variants round differently)
+    int64_t bh[16] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3],
+                      b.ks->cs, b.ks->bt, b.ks->tx, b.ks->ty, b.ks->tz, b.ks->minb, b.ncl > 0 ? 1 : 0};
     fwrite(bh, sizeof(bh), 1, f);
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
     for (int i = 0; i < 5 && ok; ++i) ok = dump(b.slot[i], sb) && dump(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
@@ -1282,7 +1307,7 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
   int32_t hdr[3];
   double t, dts;
   int64_t steps;
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD1", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD2", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
             fread(&t, 8, 1, f) == 1 && fread(&steps, 8, 1, f) == 1 && fread(&dts, 8, 1, f) == 1;
   if (!ok || hdr[0] != c->prec || hdr[1] != int32_t(c->boxes.size())) {
     fclose(f);
@@ -1295,12 +1320,19 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
     return cudaMemcpy(d, host.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   for (Box& b : c->boxes) {
-    int64_t bh[9];
+    int64_t bh[16];
     ok = ok && fread(bh, sizeof(bh), 1, f) == 1 && bh[0] == b.lat.nx && bh[1] == b.lat.ny && bh[2] == b.lat.nz &&
          bh[3] == b.n;
     if (!ok) break;
     b.iphi = int(bh[4]);
     for (int i = 0; i < 4; ++i) b.ih[i] = int(bh[5 + i]);
+    for (const KernelSet& k : registry())
+      if (k.prec == (c->prec == WSLDA_MIXED ? 1 : 0) && k.nx == b.lat.nx && k.ny == b.lat.ny && k.nz == b.lat.nz &&
+          k.cs == bh[9] && k.bt == bh[10] && k.tx == bh[11] && k.ty == bh[12] && k.tz == bh[13] && k.minb == bh[14]) {
+        b.ks = &k;
+        b.ncl = bh[15] ? resident_clusters(&k) : 0;
+        break;
+      }
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
     for (int i = 0; i < 5 && ok; ++i) ok = slurp(b.slot[i], sb) && slurp(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && slurp(b.lam, size_t(b.M) * 8) && slurp(b.vext, size_t(b.M) * 8) && slurp(b.dext, size_t(b.M) * 16) &&

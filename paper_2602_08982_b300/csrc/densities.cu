@@ -4,6 +4,8 @@
 // and precision conversions at the ABI boundary.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "functional.cuh"
 #include "internal.cuh"
 
@@ -17,6 +19,7 @@ namespace wslda {
 // Double states: plain double sums.
 // ---------------------------------------------------------------------------
 constexpr int kGroup = 32;
+constexpr int kBatch = 8;
 
 __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   const float y = x - c;
@@ -46,16 +49,29 @@ __global__ void __launch_bounds__(256) density_partial_kernel(const cx<R>* __res
       const float s2l = nl < n1 ? float(sc[nl] * sc[nl]) : 0.f;
       float sr = 0.f, cr = 0.f, snr = 0.f, cnr = 0.f, sni = 0.f, cni = 0.f;
       const int ge = int(min(int64_t(kGroup), n1 - g));
-#pragma unroll 4
-      for (int k = 0; k < ge; ++k) {
-        const int64_t n = g + k;
-        const float2 u = phi[n * stride + s];
-        const float2 v = phi[n * stride + M + s];
-        const float s2 = __shfl_sync(0xffffffffu, s2l, k);  // deferred normalisation of the stored states
-        const float a = wm[n] * s2, b = wp[n] * s2, d = a - b;
-        kahan(sr, cr, a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y));
-        kahan(snr, cnr, d * (u.x * v.x + u.y * v.y));
-        kahan(sni, cni, d * (u.y * v.x - u.x * v.y));
+      // batches of kBatch states: all their loads are issued before the sums
+      for (int k0 = 0; k0 < ge; k0 += kBatch) {
+        float2 ub[kBatch], vb[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int64_t n = g + k0 + j;
+          if (k0 + j < ge) {
+            ub[j] = phi[n * stride + s];
+            vb[j] = phi[n * stride + M + s];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const float s2 = __shfl_sync(0xffffffffu, s2l, (k0 + j) & 31);  // deferred normalisation
+          if (k0 + j < ge) {
+            const int64_t n = g + k0 + j;
+            const float2 u = ub[j], v = vb[j];
+            const float a = wm[n] * s2, b = wp[n] * s2, d = a - b;
+            kahan(sr, cr, a * (v.x * v.x + v.y * v.y) + b * (u.x * u.x + u.y * u.y));
+            kahan(snr, cnr, d * (u.x * v.x + u.y * v.y));
+            kahan(sni, cni, d * (u.y * v.x - u.x * v.y));
+          }
+        }
       }
       ar += double(sr) - double(cr);
       anr += double(snr) - double(cnr);
@@ -87,6 +103,37 @@ cudaError_t launch_density_partial(const cx<R>* phi, const double* sc, const R* 
   density_partial_kernel<R><<<grid, 256, 0, s>>>(phi, sc, wm, wp, nstates, M, chunk, part);
   return cudaGetLastError();
 }
+// Chunks of states for the density reduction: the grid (site blocks x chunks)
+// should fill whole waves of resident blocks, so that no partial last wave
+// idles most of the GPU. Among chunk counts with at least 16 states per chunk
+// (at most 256 chunks), take the best wave fill, then the fewest chunks.
+int density_chunks(int M, int64_t nstates, int is_float) {
+  int dev = 0, sms = 148, per_sm = 8;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (is_float)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, density_partial_kernel<float>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, density_partial_kernel<double>, 256, 0);
+  }
+  const int64_t resident = int64_t(std::max(1, sms)) * std::max(1, per_sm);
+  const int64_t sb = (M + 255) / 256;
+  const int64_t hi = std::max<int64_t>(1, std::min<int64_t>(256, nstates / 16));
+  int best = 1;
+  double best_fill = -1.0;
+  for (int64_t nc = 1; nc <= hi; ++nc) {
+    const int64_t blocks = sb * nc;
+    if (blocks < resident && nc < hi) continue;  // at least one full wave when possible
+    const int64_t waves = (blocks + resident - 1) / resident;
+    const double fill = double(blocks) / double(waves * resident);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best = int(nc);
+    }
+  }
+  return best;
+}
+
 template cudaError_t launch_density_partial<float>(const float2*, const double*, const float*, const float*, int64_t,
                                                    int, int, int64_t, double*, cudaStream_t);
 template cudaError_t launch_density_partial<double>(const double2*, const double*, const double*, const double*,

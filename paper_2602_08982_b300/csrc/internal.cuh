@@ -11,7 +11,9 @@
 
 namespace wslda {
 
-using LaunchFn = cudaError_t (*)(const void* args, int nstates, cudaStream_t s);
+// nclusters > 0 launches that many clusters, each looping over states
+// cluster, cluster + nclusters, ... (persistent); 0 launches one per state.
+using LaunchFn = cudaError_t (*)(const void* args, int nstates, int nclusters, cudaStream_t s);
 
 // One compiled lattice shape / precision: launchers for every stage mode.
 struct KernelSet {
@@ -29,9 +31,9 @@ struct Registrar {
   explicit Registrar(const KernelSet& k) { registry().push_back(k); }
 };
 
-template <class G, int MODE>
-cudaError_t launch_stage(const void* args, int nstates, cudaStream_t s) {
-  auto kern = stage_kernel<G, MODE>;
+template <class G, int MODE, bool PERSIST>
+cudaError_t launch_stage_as(const StageArgs<typename G::R>& a, int ncl, cudaStream_t s) {
+  auto kern = stage_kernel<G, MODE, PERSIST>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::smem_bytes));
@@ -43,7 +45,7 @@ cudaError_t launch_stage(const void* args, int nstates, cudaStream_t s) {
     configured = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(nstates) * G::CS);
+  cfg.gridDim = dim3(unsigned(ncl) * G::CS);
   cfg.blockDim = dim3(G::BT);
   cfg.dynamicSmemBytes = G::smem_bytes;
   cfg.stream = s;
@@ -54,7 +56,15 @@ cudaError_t launch_stage(const void* args, int nstates, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, *static_cast<const StageArgs<typename G::R>*>(args));
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <class G, int MODE>
+cudaError_t launch_stage(const void* args, int nstates, int nclusters, cudaStream_t s) {
+  StageArgs<typename G::R> a = *static_cast<const StageArgs<typename G::R>*>(args);
+  a.nstates = nstates;
+  if (nclusters > 0 && nclusters < nstates) return launch_stage_as<G, MODE, true>(a, nclusters, s);
+  return launch_stage_as<G, MODE, false>(a, nstates, s);
 }
 
 template <class G>
@@ -70,12 +80,12 @@ KernelSet make_set() {
   k.launch[MODE_HORNER] = launch_stage<G, MODE_HORNER>;
   k.launch[MODE_EKIN] = launch_stage<G, MODE_EKIN>;
   k.launch[MODE_GRAD] = launch_stage<G, MODE_GRAD>;
-  k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X>;
-  k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y>;
-  k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F>;
-  k.fn[MODE_HORNER] = (const void*)stage_kernel<G, MODE_HORNER>;
-  k.fn[MODE_EKIN] = (const void*)stage_kernel<G, MODE_EKIN>;
-  k.fn[MODE_GRAD] = (const void*)stage_kernel<G, MODE_GRAD>;
+  k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X, false>;
+  k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y, false>;
+  k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F, false>;
+  k.fn[MODE_HORNER] = (const void*)stage_kernel<G, MODE_HORNER, false>;
+  k.fn[MODE_EKIN] = (const void*)stage_kernel<G, MODE_EKIN, false>;
+  k.fn[MODE_GRAD] = (const void*)stage_kernel<G, MODE_GRAD, false>;
   return k;
 }
 
@@ -100,6 +110,9 @@ struct FunctionalDev {
 template <typename R>
 cudaError_t launch_density_partial(const cx<R>* phi, const double* sc, const R* wm, const R* wp, int64_t nstates,
                                    int M, int nchunk, int64_t chunk, double* part, cudaStream_t s);
+
+// Number of state chunks of the density reduction for M sites and n states.
+int density_chunks(int M, int64_t nstates, int is_float);
 
 // Sum the chunk partials, build (U, Delta) with the frozen regulator lam
 // (or first compute lam by the t = 0 fixed point when init_lam), and write

@@ -302,8 +302,10 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
   }
 }
 
+// One state of a stage, inlined into the kernel (so that the arguments stay
+// kernel parameters, read where they are used).
 template <class G, int MODE>
-__global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<typename G::R> a) {
+__device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, const int n, const int ncl) {
   using C = typename G::C;
   using R = typename G::R;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -312,51 +314,46 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   C* tws = reinterpret_cast<C*>(ktab + 2 * (G::NX + G::NY + G::NZ));
   double* red = reinterpret_cast<double*>(tws + (G::NX + G::NY + G::NZ));
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
-
+  const fx4<R>* WD = a.WD;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = cl.block_rank();
-  const int n = blockIdx.x / G::CS;
   const int tid = threadIdx.x;
-  const size_t sbase = size_t(n) * 2 * G::M;
   const int gs0 = rank * G::NS;  // first global site of this slab
   constexpr int U = G::U;
   auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
-
-  constexpr int NAX = G::NX + G::NY + G::NZ;
-  for (int i = tid; i < NAX; i += G::BT) {
-    ktab[i] = a.ktab[i];
-    ktab[NAX + i] = a.ktab[NAX + i];
-    tws[i] = a.tw[i];
-  }
   const C* twx = tws;
   const C* twy = tws + G::NX;
   const C* twz = tws + G::NX + G::NY;
-
+  const size_t sbase = size_t(n) * 2 * G::M;
   const C* in = a.phi + sbase;
   // load the slab of both components (asynchronous copies, all in flight)
   for (int i = tid; i < 2 * G::NS; i += G::BT) {
     const int comp = i / G::NS, s = i % G::NS;
     cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
   }
-  cp_async_wait_all();
-  __syncthreads();
-
   // Prologue sweep over the slab: the potential part of <H>_n,
   // sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v), of the scaled input (the slab
   // itself stays unscaled; the FFT is linear, so the scale is applied to its
-  // results instead).
+  // results instead). The first batch of a thread's field loads is issued
+  // before the wait for the slab, so both round trips overlap.
   const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
-  const R sin_ = R(a.sc_in[n]);
-  R ep = 0, ec = 0;  // compensated partial sum
-  // all of a thread's field loads in one round trip (registers are free here)
-  constexpr int UP = (G::NS + G::BT - 1) / G::BT < 16 ? (G::NS + G::BT - 1) / G::BT : 16;
-  for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * UP) {
-    fx4<R> wd[UP];
+  constexpr int UPMAX = G::MINB >= 3 ? 4 : 16;  // fewer under a tight register budget
+  constexpr int UP = (G::NS + G::BT - 1) / G::BT < UPMAX ? (G::NS + G::BT - 1) / G::BT : UPMAX;
+  fx4<R> wd[UP];
+  auto load_wd = [&](int s0) {
 #pragma unroll
     for (int k = 0; k < UP; ++k) {
       const int s = s0 + k * G::BT;
-      if (s < G::NS) wd[k] = a.WD[gs0 + s];
+      if (s < G::NS) wd[k] = WD[gs0 + s];
     }
+  };
+  if (need_e) load_wd(tid);
+  const R sin_ = R(a.sc_in[n]);
+  cp_async_wait_all();
+  __syncthreads();
+  R ep = 0, ec = 0;  // compensated partial sum
+  for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * UP) {
+    if (s0 != tid) load_wd(s0);
 #pragma unroll
     for (int k = 0; k < UP; ++k) {
       const int s = s0 + k * G::BT;
@@ -377,6 +374,9 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
   __syncthreads();
   local_pass<G, 1, false>(buf, twy);
   cl.sync();
+  // the next state's input slab starts moving into L2 while this one is transformed
+  if (tid < 2 && n + ncl < a.nstates)
+    prefetch_l2(a.phi + size_t(n + ncl) * 2 * G::M + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
   R eku = 0, ekv = 0;
   x_pass<G, MODE == MODE_GRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
   // Publish this CTA's partial <H>_n (or kinetic sums) into the slots of every
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
           const int g = gs0 + s;
           u[k] = in[g];
           v[k] = in[G::M + g];
-          wd[k] = a.WD[g];
+          wd[k] = WD[g];
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
@@ -539,6 +539,40 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const StageArgs<t
     } else if (rank == 0 && tid == 0 && a.sc_out) {
       a.sc_out[n] = 1.0;
     }
+  }
+}
+
+// PERSIST = false: one cluster per state. PERSIST = true: a cluster handles
+// states n, n + ncl, ... (ncl clusters resident at once), prefetching the next
+// state's input slab into L2 during the current one. Between states the whole
+// CTA passes a barrier before the slab is overwritten; remote CTAs touch this
+// slab and the reduction slots only after the next state's first cluster
+// barrier. (The one-state form is a separate instance because the loop makes
+// the compiler keep per-state invariants in registers.)
+template <class G, int MODE, bool PERSIST>
+__global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_constant__ StageArgs<typename G::R> a) {
+  using C = typename G::C;
+  using R = typename G::R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* buf = reinterpret_cast<C*>(smem);
+  R* ktab = reinterpret_cast<R*>(buf + 2 * G::SLAB);
+  C* tws = reinterpret_cast<C*>(ktab + 2 * (G::NX + G::NY + G::NZ));
+  constexpr int NAX = G::NX + G::NY + G::NZ;
+  for (int i = threadIdx.x; i < NAX; i += G::BT) {
+    ktab[i] = a.ktab[i];
+    ktab[NAX + i] = a.ktab[NAX + i];
+    tws[i] = a.tw[i];
+  }
+  const int ncl = gridDim.x / G::CS;
+  if constexpr (PERSIST) {
+#pragma unroll 1
+    for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl) {
+      __syncthreads();
+      stage_state<G, MODE>(a, n, ncl);
+    }
+  } else {
+    __syncthreads();
+    stage_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
   }
 }
 
