@@ -495,6 +495,61 @@ def evolve(sys: TDSystem, st: ABMState, dt: float, nsteps: int) -> ABMState:
 
 
 # ----------------------------------------------------------------------------
+# The other predictor-corrector pairs of Sec. 3.3: AB3AM4 and AB5AM5
+# ----------------------------------------------------------------------------
+SCHEMES = {"AB3AM4": (AB3, AM4), "AB4AM5": (AB4, AM5), "AB5AM5": (AB5, AM5)}
+
+
+@dataclass
+class ABMHistory:
+    """phi_{k-1} and the history f_{k-1}, f_{k-2}, ..., f_{k-p} of an ABpAMq
+    scheme (p = predictor order: p + 2 buffers in the in-place form, Sec. 3.3)."""
+    phi: np.ndarray
+    f: list
+    t: float = 0.0
+    steps: int = 0
+
+
+def abm_step(sys: TDSystem, st: ABMHistory, dt: float, scheme: str) -> ABMHistory:
+    """One step of the scheme, in the order of Alg. 2 (which Sec. 3.3 says the
+    other schemes follow): predictor and corrector partial from phi_{k-1} and
+    the history, normalise, f at the predictor, complete the corrector,
+    shift the history, normalise, f at the new state."""
+    b, a = SCHEMES[scheme]
+    lat = sys.lat
+    pred = st.phi + dt * sum(b[j] * st.f[j] for j in range(len(b)))
+    corr = st.phi + dt * sum(a[j + 1] * st.f[j] for j in range(len(a) - 1))
+    phi = normalize(pred, lat)
+    phi = (a[0] * dt) * sys.f(phi) + corr
+    phi = normalize(phi, lat)
+    hist = [sys.f(phi)] + st.f[:-1]
+    return ABMHistory(phi=phi, f=hist, t=st.t + dt, steps=st.steps + 1)
+
+
+def start_scheme(sys: TDSystem, phi0, dt: float, stationary: bool, scheme: str, r: int = 5) -> ABMHistory:
+    """Start-up for a scheme whose predictor uses p history values: a stationary
+    start (f_{k-2..k-p} = 0) or p - 1 Taylor steps (readings S1, T2, T3)."""
+    p = len(SCHEMES[scheme][0])
+    lat = sys.lat
+    phi = normalize(phi0, lat)
+    if sys.lam is None:
+        sys.init_regulator(phi)
+    if stationary:
+        return ABMHistory(phi=phi, f=[sys.f(phi)] + [np.zeros_like(phi) for _ in range(p - 1)])
+    hist = [sys.f(phi)]
+    for _ in range(p - 1):
+        phi = taylor_step(sys, phi, dt, r)
+        hist.insert(0, sys.f(phi))
+    return ABMHistory(phi=phi, f=hist, t=(p - 1) * dt, steps=p - 1)
+
+
+def evolve_scheme(sys: TDSystem, st: ABMHistory, dt: float, nsteps: int, scheme: str) -> ABMHistory:
+    for _ in range(nsteps):
+        st = abm_step(sys, st, dt, scheme)
+    return st
+
+
+# ----------------------------------------------------------------------------
 # Uniform systems (Sec. 5.2.1 "inittype 0"): lattice seeds and continuum checks
 # ----------------------------------------------------------------------------
 def bcs_amplitudes(xi, delta):

@@ -353,3 +353,44 @@ def test_splitmix64_matches_scalar_definition():
     for seed in (0, 1, 12345678901234):
         assert [int(x) for x in inputs.splitmix64(seed, 20)] == scalar(seed, 20)
     assert int(inputs.splitmix64(7, 1, offset=5)[0]) == scalar(7, 6)[5]
+
+
+def test_general_scheme_reproduces_ab4am5():
+    """The general ABpAMq step with the AB4AM5 coefficients is Alg. 2."""
+    lat, fn, phi0, vext, dext = _tiny_case()
+    sys = o.TDSystem(lat, fn, vext=vext, dext=dext)
+    st = o.start(sys, phi0, 0.02, stationary=False)
+    gs = o.start_scheme(sys, phi0, 0.02, False, "AB4AM5")
+    assert np.array_equal(gs.phi, st.phi)
+    st = o.evolve(sys, st, 0.02, 3)
+    gs = o.evolve_scheme(sys, gs, 0.02, 3, "AB4AM5")
+    assert np.abs(gs.phi - st.phi).max() < 1e-14
+
+
+@pytest.mark.parametrize("scheme,order", [("AB3AM4", 4), ("AB5AM5", 5)])
+def test_other_schemes_converge_at_their_order(scheme, order):
+    """Frozen fields, exact exp(-iHt) from the dense eigen-decomposition: the
+    error falls by about 2^order per halving of dt (AB3AM4: fourth order,
+    AB5AM5: fifth)."""
+    lat = o.Lattice(4, 4, 4)
+    rng = np.random.default_rng(8)
+    F = o.Fields(W=0.3 * rng.standard_normal(lat.M),
+                 D=0.2 * (rng.standard_normal(lat.M) + 1j * rng.standard_normal(lat.M)))
+    q, _ = np.linalg.qr(rng.standard_normal((2 * lat.M, 12)) + 1j * rng.standard_normal((2 * lat.M, 12)))
+    phi0 = q.T.reshape(12, 2, lat.M)
+    wm, wp = np.ones(12), np.zeros(12)
+    w, V = np.linalg.eigh(o.dense_bdg(F, lat))
+    T = 0.4
+    exact = (V @ (np.exp(-1j * w * T)[:, None] * (V.conj().T @ phi0.reshape(12, -1).T))).T.reshape(phi0.shape)
+    r_ex, n_ex = o.densities(exact, wm, wp)
+    p = len(o.SCHEMES[scheme][0])
+    errs = []
+    for dt in (0.02, 0.01):
+        sys = o.TDSystem(lat, o.Functional(), vext=np.zeros(lat.M), freeze_fields=F, lam=np.zeros(lat.M))
+        st = o.evolve_scheme(sys, o.start_scheme(sys, phi0, dt, False, scheme), dt, int(round(T / dt)) - (p - 1),
+                             scheme)
+        assert abs(st.t - T) < 1e-12
+        r, n = o.densities(st.phi, wm, wp)
+        errs.append(max(np.abs(r - r_ex).max() / np.abs(r_ex).max(), np.abs(n - n_ex).max() / np.abs(n_ex).max()))
+    ratio = errs[0] / errs[1]
+    assert 2 ** order * 0.6 < ratio < 2 ** order * 1.6, (errs, ratio)
