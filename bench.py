@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", action="store_true",
                    help="also time the batched workload: 64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps")
+    p.add_argument("--integrator", default="AB4AM5", choices=["AB4AM5", "AB3AM4", "AB5AM5"],
+                   help="predictor-corrector scheme of Sec. 3.3 (AB4AM5 is Alg. 2)")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -140,31 +142,36 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arms
-def make_box(W, prec, shape, nstates, omega, stream):
+def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5"):
     from paper_2602_08982_b300 import inputs
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(prec, stream=stream)
+    ctx.set_integrator(scheme)
     box = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=nstates)
     ctx.set_vext(box, inputs.harmonic_trap(shape, omega))
     return ctx, box, u
 
 
-def stage_x_algorithmic(prec, shape):
+HISTORY_READS = {"AB3AM4": 2, "AB4AM5": 3, "AB5AM5": 4}
+
+
+def stage_x_algorithmic(prec, shape, scheme="AB4AM5"):
     """Algorithmic traffic / work of one stage-X launch per state-site.
-    Bytes: reads phi, f_{k-2}, f_{k-3}, f_{k-4}; writes f_{k-1}, phi_p, c
-    (7 state passes of two complex numbers). Flops (FP64 path): forward and
-    inverse 3D FFT of both components at 5 M log2 M each, plus the pointwise
-    H, <H>_n, f, predictor, corrector partial, norm and scaling (128)."""
+    Bytes: reads phi and the history (AB4AM5: f_{k-2}, f_{k-3}, f_{k-4});
+    writes f_{k-1}, phi_p, c (AB4AM5: 7 state passes of two complex numbers).
+    Flops (FP64 path): forward and inverse 3D FFT of both components at
+    5 M log2 M each, plus the pointwise H, <H>_n, f, predictor, corrector
+    partial, norm and scaling (128)."""
     M = shape[0] * shape[1] * shape[2]
     csize = 8 if prec == 1 else 16
-    bytes_per = 7 * 2 * csize
+    bytes_per = (1 + HISTORY_READS[scheme] + 3) * 2 * csize
     flops_per = 2 * 2 * 5 * math.log2(M) + 128
     return bytes_per, flops_per
 
 
 def run_arm(W, torch, prec, args, shape, rank, world, dev):
     stream = torch.cuda.current_stream()
-    ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
     ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
     ctx.start(args.stationary, args.dt)      # Taylor start: the trapped plane waves are not stationary
     variant = ctx.get_variant(box)
@@ -194,14 +201,14 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     M = shape[0] * shape[1] * shape[2]
     units = float(args.nstates) * M * args.steps
     value = job_rate(units, world, ms * 1e-3)
-    bx, fx = stage_x_algorithmic(prec, shape)
+    bx, fx = stage_x_algorithmic(prec, shape, args.integrator)
     x_ms, x_n = kt["stage_x"]
     x_avg = x_ms / max(x_n, 1)
     per_launch = float(args.nstates) * M
     if prec == 1:
         peak, which = measured_peaks()
         achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
-        tb = profiled_traffic()
+        tb = profiled_traffic() if args.integrator == "AB4AM5" else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if tb is None else tb * per_launch,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
@@ -221,7 +228,7 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
 def run_e2e(W, torch, args, shape, world):
     """Mixed path end to end through the ABI with pinned host buffers."""
     stream = torch.cuda.current_stream()
-    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
     ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
     M = shape[0] * shape[1] * shape[2]
     host = torch.empty((args.nstates, 2, M), dtype=torch.complex128, pin_memory=True)
@@ -234,7 +241,7 @@ def run_e2e(W, torch, args, shape, world):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
-    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream)
+    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
     ctx.load_states(box, host_np)
     ctx.start(False, args.dt)
     for _ in range(args.steps):
@@ -331,7 +338,15 @@ def oracle_sample(shape, omega, n):
     return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, omega)), phi, lat
 
 
-def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048):
+def oracle_stepper(o, scheme):
+    """(start, step) of the oracle for the scheme: Alg. 2 itself for AB4AM5."""
+    if scheme == "AB4AM5":
+        return (lambda sysm, phi, dt: o.start(sysm, phi, dt, stationary=True)), o.ab4am5_step
+    return ((lambda sysm, phi, dt: o.start_scheme(sysm, phi, dt, True, scheme)),
+            (lambda sysm, st, dt: o.abm_step(sysm, st, dt, scheme)))
+
+
+def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048, scheme="AB4AM5"):
     """The oracle as it stands, on a bounded sample of the workload: the same
     lattice and trap with a subset of the uniform plane-wave states, timed over
     whole ABM steps after a stationary start."""
@@ -339,9 +354,10 @@ def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048):
     n = min(64, max_states)
     while True:
         o, sysm, phi, lat = oracle_sample(shape, omega, n)
-        st = o.start(sysm, phi, dt, stationary=True)
+        start, step = oracle_stepper(o, scheme)
+        st = start(sysm, phi, dt)
         t0 = time.perf_counter()
-        st = o.ab4am5_step(sysm, st, dt)
+        st = step(sysm, st, dt)
         one = time.perf_counter() - t0
         if one * 4 > seconds or n >= max_states:
             break
@@ -349,10 +365,10 @@ def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048):
     k = max(1, int(seconds / max(one, 1e-3)))
     t0 = time.perf_counter()
     for _ in range(k):
-        st = o.ab4am5_step(sysm, st, dt)
+        st = step(sysm, st, dt)
     sec = time.perf_counter() - t0
     return {"value": n * lat.M * k / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "n": n,
-            "sample": f"{n} of the workload's states on the same {shape[0]}x{shape[1]}x{shape[2]} trap, {k} AB4AM5 "
+            "sample": f"{n} of the workload's states on the same {shape[0]}x{shape[1]}x{shape[2]} trap, {k} {scheme} "
                       f"steps after a stationary start, {sec:.1f} s"}
 
 
@@ -364,16 +380,17 @@ def reference_arm(args, shape):
         if rank != 0:
             dist.barrier()
             return
-    # each step: one oracle AB4AM5 step over a bounded sample of the states,
-    # sized so that one step takes about a second
-    n = cpu_oracle_rate(shape, args.omega, args.dt, seconds=args.cpu_seconds / 4)["n"]
+    # each step: one oracle step of the scheme over a bounded sample of the
+    # states, sized so that one step takes about a second
+    n = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds / 4, scheme=args.integrator)["n"]
     o, sysm, phi, lat = oracle_sample(shape, args.omega, n)
-    st = o.start(sysm, phi, args.dt, stationary=True)
+    start, step = oracle_stepper(o, args.integrator)
+    st = start(sysm, phi, args.dt)
     for _ in range(args.warmup):
-        st = o.ab4am5_step(sysm, st, args.dt)
+        st = step(sysm, st, args.dt)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        st = o.ab4am5_step(sysm, st, args.dt)
+        st = step(sysm, st, args.dt)
     sec = time.perf_counter() - t0
     value = n * lat.M * args.steps / sec
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -390,7 +407,7 @@ def reference_arm(args, shape):
 
 
 def workload_config(args, shape, precision):
-    return {"workload": f"TDSLDA AB4AM5 step, {shape[0]}x{shape[1]}x{shape[2]} periodic lattice, harmonic trap "
+    return {"workload": f"TDSLDA {args.integrator} step, {shape[0]}x{shape[1]}x{shape[2]} periodic lattice, harmonic trap "
                         f"w={args.omega}, {args.nstates} quasiparticle states",
             "lattice": list(shape), "nstates": args.nstates, "trap_omega": args.omega, "dt": args.dt,
             "functional": "SLDA (A=1), B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
@@ -414,7 +431,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds)
+        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds, scheme=args.integrator)
     arms = {}
     if args.precision in ("both", "mixed"):
         arms["mixed"] = run_arm(W, torch, W.MIXED, args, shape, rank, world, local)

@@ -100,9 +100,19 @@ const char* wslda_last_error(const wslda_ctx* ctx);
 /* 1 if kernels for this lattice shape and precision are compiled in. */
 int wslda_lattice_supported(int precision, int nx, int ny, int nz);
 
-/* Add a box with `nstates` quasiparticle states. Allocates its five state
- * buffers (phi and four ABM history slots, Alg. 2) after checking the device
- * budget. Returns the box id (>= 0) or -(wslda_status) on failure. */
+/* Predictor-corrector scheme of the boxes added afterwards (Sec. 3.3):
+ * AB4AM5 (default, Alg. 2, five state buffers), AB3AM4 (four buffers,
+ * fourth order) or AB5AM5 (six buffers, fifth order with a fifth-order
+ * predictor). Each is run in place in the manner of Alg. 2: the predictor
+ * stage writes f(phi), the predictor and the corrector partial (over the
+ * oldest history value, its last use); the start-up takes p - 1 Taylor steps
+ * for a predictor of order p. WSLDA_ESTATE once a box exists. */
+typedef enum { WSLDA_AB4AM5 = 0, WSLDA_AB3AM4 = 1, WSLDA_AB5AM5 = 2 } wslda_scheme;
+wslda_status wslda_set_integrator(wslda_ctx* ctx, int scheme);
+
+/* Add a box with `nstates` quasiparticle states. Allocates its state buffers
+ * (phi and the ABM history slots: five for AB4AM5, Alg. 2) after checking the
+ * device budget. Returns the box id (>= 0) or -(wslda_status) on failure. */
 int wslda_add_box(wslda_ctx* ctx, const wslda_lattice* lat, const wslda_functional* fn, int64_t nstates);
 
 /* External potential V_ext [M] and external pairing field Delta_ext [M complex]
@@ -119,12 +129,14 @@ wslda_status wslda_load_states(wslda_ctx* ctx, int box, const double* uv, const 
 
 /* Prepare the integrator for every box (Sec. 3.3, start-up). Computes the
  * densities, freezes the regulator Lambda_c at its t = 0 value, then either
- * assumes a stationary state (stationary = 1: f_{k-2..k-4} = 0) or runs three
- * Taylor predictor-corrector steps of order 5 (Eq. Taylor-exp), which advance
- * the time by 3 dt. Must be called again after changing the sign of dt. */
+ * assumes a stationary state (stationary = 1: the older history is zero) or
+ * runs Taylor predictor-corrector steps of order 5 (Eq. Taylor-exp): three for
+ * AB4AM5 (two for AB3AM4, four for AB5AM5), which advance the time by that
+ * many dt. Must be called again after changing the sign of dt. */
 wslda_status wslda_start(wslda_ctx* ctx, int stationary, double dt);
 
-/* Advance every box by nsteps AB4AM5 steps of size dt (Alg. 2). */
+/* Advance every box by nsteps predictor-corrector steps of size dt (Alg. 2
+ * for AB4AM5). */
 wslda_status wslda_step(wslda_ctx* ctx, double dt, int nsteps);
 
 /* Copy the current states out as [n][2][M] complex double. */

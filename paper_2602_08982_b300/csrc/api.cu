@@ -44,12 +44,13 @@ struct Box {
   const KernelSet* ks = nullptr;
   int ncl = 0;           // persistent stage launches: clusters (0 = one cluster per state)
   size_t csize = 0;      // bytes per complex element (8 or 16)
-  void* slot[5] = {};    // state buffers [n][2][M]
-  int iphi = 0, ih[4] = {1, 2, 3, 4};
+  int D = 3;             // history values the predictor reads (AB3AM4 2, AB4AM5 3, AB5AM5 4)
+  void* slot[6] = {};    // D + 2 state buffers [n][2][M]
+  int iphi = 0, ih[5] = {1, 2, 3, 4, 5};  // ih[0]: next f_{k-1}; ih[1..D]: f_{k-2}, ..., f_{k-1-D}
   double *vext = nullptr, *dext = nullptr, *lam = nullptr, *rho = nullptr, *nu = nullptr, *U = nullptr,
          *delta = nullptr;
   void* WD = nullptr;                   // working-precision H fields {W, Re D, Im D, 0}
-  double* sc[5] = {};                   // per-slot per-state scale (deferred normalisation)
+  double* sc[6] = {};                   // per-slot per-state scale (deferred normalisation)
   void *ktab = nullptr, *tw = nullptr;  // per-axis kinetic symbol and twiddles
   double *wm = nullptr, *wp = nullptr;  // double weights
   void *wm_r = nullptr, *wp_r = nullptr;
@@ -69,6 +70,7 @@ struct Box {
 
 struct wslda_ctx {
   int prec = 0;
+  int scheme_depth = 3;           // history depth of the integrator of boxes added from now on
   cudaStream_t stream = nullptr;  // the caller's stream
   cudaStream_t cur = nullptr;     // stream the box-level launches go to (stream, or a forked one)
   // batched execution: boxes spread over forked streams, four steps captured
@@ -267,11 +269,15 @@ StageArgs<R> base_args(const Box& b, double dV) {
   a.npart = b.npart;
   a.out2 = b.ekin2;
   a.dV = dV;
+  a.ycoef = b.D == 2 ? 9.0 / 24.0 : 251.0 / 720.0;  // new term of Eq. AM4 / Eq. AM5
   a.nstates = int(b.n);
   return a;
 }
 
 double box_dV(const Box& b) { return b.lat.dx * b.lat.dy * b.lat.dz; }
+
+// predictor-stage kernel mode of the box's scheme
+int x_mode(const Box& b) { return b.D == 2 ? MODE_X3 : (b.D == 4 ? MODE_X5 : MODE_X); }
 
 // A stage launch; normalising modes are followed by the kernel that turns the
 // per-CTA norm partials into the per-state factor (same profiling scope).
@@ -282,7 +288,8 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   ProfScope ps(c, kind);
   CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), b.ncl, c->cur));
   c->launches += 1;
-  const bool norm_out = mode == MODE_X || mode == MODE_Y || (mode == MODE_HORNER && a.normalize);
+  const bool norm_out = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
+                        (mode == MODE_HORNER && a.normalize);
   if (norm_out) {
     CUDA_TRY(c, launch_finalize_norm(a.npart, b.ks->cs, b.n, box_dV(b), a.sc_out, c->err_d, c->cur));
     c->launches += 1;
@@ -322,18 +329,19 @@ wslda_status stage_x(wslda_ctx* c, Box& b, double dt) {
   a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[0]));
   a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[1]));
   a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
-  a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  if (b.D >= 3) a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  if (b.D >= 4) a.h4 = static_cast<cx<R>*>(b.ptr(b.ih[4]));
   a.sc_in = b.sc[b.iphi];
   a.sc_out = b.sc[b.iphi];
   a.dt = dt;
-  return launch_mode<R>(c, b, MODE_X, a, PROF_X);
+  return launch_mode<R>(c, b, x_mode(b), a, PROF_X);
 }
 
 template <typename R>
 wslda_status stage_y(wslda_ctx* c, Box& b, double dt) {
   StageArgs<R> a = base_args<R>(b, box_dV(b));
   a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
-  a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+  a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[b.D]));  // the corrector partial
   a.sc_in = b.sc[b.iphi];
   a.sc_out = b.sc[b.iphi];
   a.dt = dt;
@@ -423,7 +431,7 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   const size_t bytes = size_t(nt) * 2 * b.M * b.csize;
   CUDA_TRY(c, cudaMemcpyAsync(b.ptr(b.ih[0]), b.ptr(b.iphi), bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(b.sc[b.ih[0]], b.sc[b.iphi], size_t(nt) * 8, cudaMemcpyDeviceToDevice, c->stream));
-  for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
+  for (int i = 1; i <= 2; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
   CUDA_TRY(c, cudaEventCreate(&e1));
@@ -436,11 +444,14 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
       if (pmode >= 0 && mode != pmode) continue;
       const int ncl = mode ? res : 0;
       StageArgs<R> a = base_args<R>(b, box_dV(b));
+      // scratch: phi copy in ih[0], f out in ih[1], every history read and
+      // the corrector partial in ih[2] (each element read, then written, by one thread)
       a.phi = static_cast<cx<R>*>(b.ptr(b.ih[0]));
       a.h0 = static_cast<cx<R>*>(b.ptr(b.ih[1]));
       a.h1 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
       a.h2 = static_cast<const cx<R>*>(b.ptr(b.ih[2]));
-      a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[3]));
+      a.h3 = static_cast<cx<R>*>(b.ptr(b.ih[2]));
+      a.h4 = static_cast<cx<R>*>(b.ptr(b.ih[2]));
       a.sc_in = b.sc[b.ih[0]];
       a.sc_out = b.sc[b.ih[1]];
       a.dt = dt;
@@ -448,7 +459,7 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
       float ms = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-        CUDA_TRY(c, v[k]->launch[MODE_X](&a, int(nt), ncl, c->stream));
+        CUDA_TRY(c, v[k]->launch[x_mode(b)](&a, int(nt), ncl, c->stream));
         CUDA_TRY(c, cudaEventRecord(e1, c->stream));
         CUDA_TRY(c, cudaEventSynchronize(e1));
         float t = 0.f;
@@ -506,15 +517,15 @@ wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
   if ((st = autotune_box<R>(c, b, dt))) return st;
   const size_t bytes = size_t(b.n) * 2 * b.M * b.csize;
   if (stationary) {
-    for (int i = 1; i < 4; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
+    for (int i = 1; i <= b.D; ++i) CUDA_TRY(c, cudaMemsetAsync(b.ptr(b.ih[i]), 0, bytes, c->stream));
     return WSLDA_OK;
   }
-  // history f(phi_0), f(phi_1), f(phi_2) into f_{k-4}, f_{k-3}, f_{k-2};
-  // f(phi_3) is formed by the first stage X.
-  if ((st = eval_f_into<R>(c, b, b.iphi, b.ih[3]))) return st;
-  for (int s = 1; s <= 3; ++s) {
+  // D Taylor steps; history f(phi_0) .. f(phi_{D-1}) into ih[D] .. ih[1]
+  // (oldest in ih[D]); f(phi_D) is formed by the first predictor stage.
+  if ((st = eval_f_into<R>(c, b, b.iphi, b.ih[b.D]))) return st;
+  for (int s = 1; s <= b.D; ++s) {
     if ((st = taylor_step<R>(c, b, dt))) return st;
-    if (s < 3 && (st = eval_f_into<R>(c, b, b.iphi, b.ih[3 - s]))) return st;
+    if (s < b.D && (st = eval_f_into<R>(c, b, b.iphi, b.ih[b.D - s]))) return st;
   }
   return WSLDA_OK;
 }
@@ -527,10 +538,8 @@ wslda_status step_box(wslda_ctx* c, Box& b, double dt) {
   if ((st = stage_y<R>(c, b, dt))) return st;
   if ((st = refresh_fields(c, b, b.iphi, 0))) return st;
   // Alg. 2 steps 5-7: the slot that held c becomes the slot for the next f_{k-1}
-  const int freed = b.ih[3];
-  b.ih[3] = b.ih[2];
-  b.ih[2] = b.ih[1];
-  b.ih[1] = b.ih[0];
+  const int freed = b.ih[b.D];
+  for (int i = b.D; i >= 1; --i) b.ih[i] = b.ih[i - 1];
   b.ih[0] = freed;
   return WSLDA_OK;
 }
@@ -574,7 +583,7 @@ std::vector<int> slot_phase(const wslda_ctx* c) {
   std::vector<int> key;
   for (const Box& b : c->boxes) {
     key.push_back(b.iphi);
-    for (int i = 0; i < 4; ++i) key.push_back(b.ih[i]);
+    for (int i = 0; i <= b.D; ++i) key.push_back(b.ih[i]);
   }
   return key;
 }
@@ -620,7 +629,8 @@ wslda_status step_graph4(wslda_ctx* c, double dt) {
     if (e != cudaSuccess) return fail(c, WSLDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     c->graphs.push_back({key, exec});
     c->graph_kernels.push_back(kernels);
-    // capture advanced the host-side slot rotation by four steps, back to `key`
+    // capture advanced the host-side slot rotation by four steps (one period
+    // for AB4AM5; other schemes cycle through several captured phases)
   }
   CUDA_TRY(c, cudaEventRecord(c->cap_in, user));
   CUDA_TRY(c, cudaStreamWaitEvent(c->cap, c->cap_in, 0));
@@ -704,6 +714,16 @@ const char* wslda_last_error(const wslda_ctx* c) {
   return c->err.empty() ? "" : c->err.c_str();
 }
 
+wslda_status wslda_set_integrator(wslda_ctx* c, int scheme) {
+  CHECK_CTX(c);
+  if (!c->boxes.empty()) return fail(c, WSLDA_ESTATE, "set_integrator after add_box");
+  if (scheme == WSLDA_AB4AM5) c->scheme_depth = 3;
+  else if (scheme == WSLDA_AB3AM4) c->scheme_depth = 2;
+  else if (scheme == WSLDA_AB5AM5) c->scheme_depth = 4;
+  else return fail(c, WSLDA_EINVAL, "set_integrator: unknown scheme");
+  return WSLDA_OK;
+}
+
 int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional* fn, int64_t nstates) {
   if (!c) return -WSLDA_EINVAL;
   if (c->status != WSLDA_OK) return -WSLDA_ESTATE;
@@ -742,7 +762,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   const size_t state_bytes = size_t(nstates) * 2 * M * b.csize;
   const size_t field_bytes = size_t(M) * (8 * 13 + rsize * 4) + size_t(4) * M * 8 * b.nchunk +
                              size_t(nstates) * (8 * 26 + rsize * 2) + 4096;
-  const size_t need = 5 * state_bytes + field_bytes;
+  const int D = c->scheme_depth;
+  const size_t need = size_t(D + 2) * state_bytes + field_bytes;
   size_t freeb = 0, totalb = 0;
   CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
   const size_t margin = size_t(1) << 30;
@@ -765,7 +786,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
     ptr = decltype(ptr)(p_);                                                         \
   } while (0)
 
-  for (int i = 0; i < 5; ++i) ALLOC(b.slot[i], state_bytes);
+  b.D = D;
+  for (int i = 0; i < D + 2; ++i) ALLOC(b.slot[i], state_bytes);
   ALLOC(b.vext, M * 8);
   ALLOC(b.dext, 2 * M * 8);
   ALLOC(b.lam, M * 8);
@@ -774,7 +796,7 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.U, M * 8);
   ALLOC(b.delta, 2 * M * 8);
   ALLOC(b.WD, 4 * M * rsize);
-  for (int i = 0; i < 5; ++i) ALLOC(b.sc[i], std::max<int64_t>(nstates, 1) * 8);
+  for (int i = 0; i < D + 2; ++i) ALLOC(b.sc[i], std::max<int64_t>(nstates, 1) * 8);
   const int naxis = lat->nx + lat->ny + lat->nz;
   ALLOC(b.ktab, 2 * naxis * rsize);
   ALLOC(b.tw, 2 * naxis * rsize);
@@ -1007,8 +1029,8 @@ wslda_status wslda_start(wslda_ctx* c, int stationary, double dt) {
   drop_graphs(c);
   c->started = true;
   c->dt_start = dt;
-  c->t = stationary ? 0.0 : 3 * dt;
-  c->steps = stationary ? 0 : 3;
+  c->t = stationary ? 0.0 : c->scheme_depth * dt;  // one Taylor step per history value
+  c->steps = stationary ? 0 : c->scheme_depth;
   return WSLDA_OK;
 }
 
@@ -1268,7 +1290,7 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(c, WSLDA_EINVAL, std::string("save: cannot open ") + path);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '2'};
+  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '3'};
   int32_t hdr[3] = {c->prec, int32_t(c->boxes.size()), c->started ? 1 : 0};
   fwrite(magic, 1, 8, f);
   fwrite(hdr, sizeof(hdr), 1, f);
@@ -1285,11 +1307,11 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   for (Box& b : c->boxes) {
     // the launch variant travels with the state, so that a resumed run uses the
     // same kernels (different variants round differently)
-    int64_t bh[16] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3],
+    int64_t bh[18] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.D, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3], b.ih[4],
                       b.ks->cs, b.ks->bt, b.ks->tx, b.ks->ty, b.ks->tz, b.ks->minb, b.ncl > 0 ? 1 : 0};
     fwrite(bh, sizeof(bh), 1, f);
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
-    for (int i = 0; i < 5 && ok; ++i) ok = dump(b.slot[i], sb) && dump(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
+    for (int i = 0; i < b.D + 2 && ok; ++i) ok = dump(b.slot[i], sb) && dump(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && dump(b.lam, size_t(b.M) * 8) && dump(b.vext, size_t(b.M) * 8) && dump(b.dext, size_t(b.M) * 16) &&
          dump(b.wm, std::max<int64_t>(b.n, 1) * 8) && dump(b.wp, std::max<int64_t>(b.n, 1) * 8);
   }
@@ -1307,7 +1329,7 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
   int32_t hdr[3];
   double t, dts;
   int64_t steps;
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD2", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD3", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
             fread(&t, 8, 1, f) == 1 && fread(&steps, 8, 1, f) == 1 && fread(&dts, 8, 1, f) == 1;
   if (!ok || hdr[0] != c->prec || hdr[1] != int32_t(c->boxes.size())) {
     fclose(f);
@@ -1320,21 +1342,21 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
     return cudaMemcpy(d, host.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   for (Box& b : c->boxes) {
-    int64_t bh[16];
+    int64_t bh[18];
     ok = ok && fread(bh, sizeof(bh), 1, f) == 1 && bh[0] == b.lat.nx && bh[1] == b.lat.ny && bh[2] == b.lat.nz &&
-         bh[3] == b.n;
+         bh[3] == b.n && bh[4] == b.D;
     if (!ok) break;
-    b.iphi = int(bh[4]);
-    for (int i = 0; i < 4; ++i) b.ih[i] = int(bh[5 + i]);
+    b.iphi = int(bh[5]);
+    for (int i = 0; i < 5; ++i) b.ih[i] = int(bh[6 + i]);
     for (const KernelSet& k : registry())
       if (k.prec == (c->prec == WSLDA_MIXED ? 1 : 0) && k.nx == b.lat.nx && k.ny == b.lat.ny && k.nz == b.lat.nz &&
-          k.cs == bh[9] && k.bt == bh[10] && k.tx == bh[11] && k.ty == bh[12] && k.tz == bh[13] && k.minb == bh[14]) {
+          k.cs == bh[11] && k.bt == bh[12] && k.tx == bh[13] && k.ty == bh[14] && k.tz == bh[15] && k.minb == bh[16]) {
         b.ks = &k;
-        b.ncl = bh[15] ? resident_clusters(&k) : 0;
+        b.ncl = bh[17] ? resident_clusters(&k) : 0;
         break;
       }
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
-    for (int i = 0; i < 5 && ok; ++i) ok = slurp(b.slot[i], sb) && slurp(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
+    for (int i = 0; i < b.D + 2 && ok; ++i) ok = slurp(b.slot[i], sb) && slurp(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && slurp(b.lam, size_t(b.M) * 8) && slurp(b.vext, size_t(b.M) * 8) && slurp(b.dext, size_t(b.M) * 16) &&
          slurp(b.wm, std::max<int64_t>(b.n, 1) * 8) && slurp(b.wp, std::max<int64_t>(b.n, 1) * 8);
     if (!ok) break;

@@ -80,12 +80,16 @@ KernelSet make_set() {
   k.launch[MODE_HORNER] = launch_stage<G, MODE_HORNER>;
   k.launch[MODE_EKIN] = launch_stage<G, MODE_EKIN>;
   k.launch[MODE_GRAD] = launch_stage<G, MODE_GRAD>;
+  k.launch[MODE_X3] = launch_stage<G, MODE_X3>;
+  k.launch[MODE_X5] = launch_stage<G, MODE_X5>;
   k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X, false>;
   k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y, false>;
   k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F, false>;
   k.fn[MODE_HORNER] = (const void*)stage_kernel<G, MODE_HORNER, false>;
   k.fn[MODE_EKIN] = (const void*)stage_kernel<G, MODE_EKIN, false>;
   k.fn[MODE_GRAD] = (const void*)stage_kernel<G, MODE_GRAD, false>;
+  k.fn[MODE_X3] = (const void*)stage_kernel<G, MODE_X3, false>;
+  k.fn[MODE_X5] = (const void*)stage_kernel<G, MODE_X5, false>;
   return k;
 }
 

@@ -46,7 +46,11 @@ template <> struct fx4_of<float> { using type = float4; };
 template <> struct fx4_of<double> { using type = double4; };
 template <typename R> using fx4 = typename fx4_of<R>::type;
 
-enum Mode : int { MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, NMODES = 6 };
+// MODE_X3 / MODE_X5: the predictor stage of AB3AM4 / AB5AM5 (MODE_X is AB4AM5's).
+enum Mode : int {
+  MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, MODE_X3 = 6, MODE_X5 = 7,
+  NMODES = 8
+};
 
 template <typename R>
 struct StageArgs {
@@ -54,7 +58,8 @@ struct StageArgs {
   cx<R>* h0;         // X: receives f_{k-1};            F: output f;  HORNER: output
   const cx<R>* h1;   // X: f_{k-2}                                   HORNER: base
   const cx<R>* h2;   // X: f_{k-3}
-  cx<R>* h3;         // X: f_{k-4} in, c out;  Y: c in
+  cx<R>* h3;         // X: f_{k-4} in, c out;  X5: f_{k-4};  Y: c in
+  cx<R>* h4;         // X5: f_{k-5} in, c out (X3 reads f_{k-2}, f_{k-3} from h1, h2 and writes c over h2)
   const fx4<R>* WD;  // [M] {U + V_ext - mu, Re, Im (Delta + Delta_ext), 0}
   const R* ktab;     // [2 (NX+NY+NZ)]: per-slot k_d^2 * 0.5 / M, then k_d / M with the Nyquist mode zeroed
   const cx<R>* tw;   // [NX+NY+NZ] W_N^k per axis (used where a pencil spans lanes)
@@ -68,6 +73,7 @@ struct StageArgs {
   double dt;
   double dV;
   double coef_re, coef_im;  // HORNER coefficient
+  double ycoef;      // Y: coefficient of the new term of the corrector (251/720 for AM5, 9/24 for AM4)
   const double* wm;  // GRAD: frozen weights f(-E_n), f(E_n)
   const double* wp;
   int dir;           // GRAD: derivative direction 0, 1, 2
@@ -76,11 +82,24 @@ struct StageArgs {
   int nstates;
 };
 
-// Integrator coefficients of Eqs. AB4 and AM5.
-struct ABM {
-  static constexpr double b0 = 55.0 / 24.0, b1 = -59.0 / 24.0, b2 = 37.0 / 24.0, b3 = -9.0 / 24.0;
-  static constexpr double a0 = 251.0 / 720.0, a1 = 646.0 / 720.0, a2 = -264.0 / 720.0, a3 = 106.0 / 720.0,
-                          a4 = -19.0 / 720.0;
+// Predictor-stage coefficients: b[j] multiplies f_{k-1-j} in the predictor
+// (Eqs. AB3, AB4, AB5), a[j] in the corrector partial (Eqs. AM4, AM5 without
+// the new term); D = history values read from memory (f_{k-1} is on chip).
+template <int MODE> struct Scheme { static constexpr int D = 0; };
+template <> struct Scheme<MODE_X3> {  // AB3AM4
+  static constexpr int D = 2;
+  static constexpr double b[5] = {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0.0, 0.0};
+  static constexpr double a[4] = {19.0 / 24.0, -5.0 / 24.0, 1.0 / 24.0, 0.0};
+};
+template <> struct Scheme<MODE_X> {  // AB4AM5
+  static constexpr int D = 3;
+  static constexpr double b[5] = {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0, 0.0};
+  static constexpr double a[4] = {646.0 / 720.0, -264.0 / 720.0, 106.0 / 720.0, -19.0 / 720.0};
+};
+template <> struct Scheme<MODE_X5> {  // AB5AM5
+  static constexpr int D = 4;
+  static constexpr double b[5] = {1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0};
+  static constexpr double a[4] = {646.0 / 720.0, -264.0 / 720.0, 106.0 / 720.0, -19.0 / 720.0};
 };
 
 template <typename R_, int NX_, int NY_, int NZ_, int CS_, int BT_, int TX_, int TY_, int TZ_, int MINB_ = 1>
@@ -336,7 +355,8 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   // itself stays unscaled; the FFT is linear, so the scale is applied to its
   // results instead). The first batch of a thread's field loads is issued
   // before the wait for the slab, so both round trips overlap.
-  const bool need_e = MODE == MODE_X || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
+  constexpr bool XM = MODE == MODE_X || MODE == MODE_X3 || MODE == MODE_X5;  // a predictor stage
+  const bool need_e = XM || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
   constexpr int UPMAX = G::MINB >= 3 ? 4 : 16;  // fewer under a tight register budget
   constexpr int UP = (G::NS + G::BT - 1) / G::BT < UPMAX ? (G::NS + G::BT - 1) / G::BT : UPMAX;
   fx4<R> wd[UP];
@@ -407,7 +427,12 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   if (tid < 2) {
     const size_t off = sbase + size_t(tid) * G::M + gs0;
     constexpr unsigned nb = unsigned(G::NS * sizeof(C));
-    if constexpr (MODE == MODE_X) { prefetch_l2(a.h1 + off, nb); prefetch_l2(a.h2 + off, nb); prefetch_l2(a.h3 + off, nb); }
+    if constexpr (XM) {
+      prefetch_l2(a.h1 + off, nb);
+      prefetch_l2(a.h2 + off, nb);
+      if constexpr (Scheme<MODE>::D >= 3) prefetch_l2(a.h3 + off, nb);
+      if constexpr (Scheme<MODE>::D >= 4) prefetch_l2(a.h4 + off, nb);
+    }
     if constexpr (MODE == MODE_Y) prefetch_l2(a.h3 + off, nb);
   }
   double En = 0.0, Ev = 0.0;
@@ -453,17 +478,19 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
     }
     const R Er = R(En);
     R np = 0, nc = 0;  // compensated norm partial
-    const bool norm_out = MODE == MODE_X || MODE == MODE_Y || (MODE == MODE_HORNER && a.normalize);
+    const bool norm_out = XM || MODE == MODE_Y || (MODE == MODE_HORNER && a.normalize);
     C* dst = (MODE == MODE_HORNER || MODE == MODE_F) ? a.h0 + sbase : a.phi + sbase;
     const R dt = R(a.dt);
     const R sbase_ = MODE == MODE_HORNER ? R(a.sc_base[n]) : R(1);
     // one pointwise sweep: H phi on the fly, f = -i (H - <H>_n) phi, integrator;
     // results go straight to global memory (normalisation deferred)
-    for (int s0 = tid; s0 < G::NS; s0 += G::BT * U) {
-      C u[U], v[U], x1[2][U], x2[2][U], x3[2][U];
-      fx4<R> wd[U];
+    constexpr int D = Scheme<MODE>::D;
+    constexpr int UE = (D >= 4 && U > 2) ? U / 2 : U;  // five history reads per site: smaller batches
+    for (int s0 = tid; s0 < G::NS; s0 += G::BT * UE) {
+      C u[UE], v[UE], x1[2][UE], x2[2][UE], x3[2][UE], x4[2][D >= 4 ? UE : 1];
+      fx4<R> wd[UE];
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
+      for (int k = 0; k < UE; ++k) {
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
           const int g = gs0 + s;
@@ -473,14 +500,19 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
-            if constexpr (MODE == MODE_X) { x1[c][k] = a.h1[gg]; x2[c][k] = a.h2[gg]; x3[c][k] = a.h3[gg]; }
+            if constexpr (XM) {
+              x1[c][k] = a.h1[gg];
+              x2[c][k] = a.h2[gg];
+              if constexpr (D >= 3) x3[c][k] = a.h3[gg];
+              if constexpr (D >= 4) x4[c][k] = a.h4[gg];
+            }
             if constexpr (MODE == MODE_Y) x3[c][k] = a.h3[gg];
             if constexpr (MODE == MODE_HORNER) x1[c][k] = a.h1[gg];
           }
         }
       }
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
+      for (int k = 0; k < UE; ++k) {
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
           const int g = gs0 + s;
@@ -497,16 +529,27 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
             C res;
-            if constexpr (MODE == MODE_X) {
+            if constexpr (XM) {
+              using S = Scheme<MODE>;
               const C fv = mul_mi(hm[c]);  // f(phi) = -i (H - <H>_n) phi
-              res = add(ph[c], scl(add(add(scl(fv, R(ABM::b0)), scl(x1[c][k], R(ABM::b1))),
-                                       add(scl(x2[c][k], R(ABM::b2)), scl(x3[c][k], R(ABM::b3)))), dt));
-              const C corr = add(ph[c], scl(add(add(scl(fv, R(ABM::a1)), scl(x1[c][k], R(ABM::a2))),
-                                                add(scl(x2[c][k], R(ABM::a3)), scl(x3[c][k], R(ABM::a4)))), dt));
+              // predictor phi + dt sum_j b_j f_{k-1-j}, corrector partial phi + dt sum_j a_j f_{k-1-j}
+              C pb = add(scl(fv, R(S::b[0])), scl(x1[c][k], R(S::b[1])));
+              C pa = add(scl(fv, R(S::a[0])), scl(x1[c][k], R(S::a[1])));
+              pb = add(pb, scl(x2[c][k], R(S::b[2])));
+              pa = add(pa, scl(x2[c][k], R(S::a[2])));
+              if constexpr (D >= 3) {
+                pb = add(pb, scl(x3[c][k], R(S::b[3])));
+                pa = add(pa, scl(x3[c][k], R(S::a[3])));
+              }
+              if constexpr (D >= 4) pb = add(pb, scl(x4[c][k], R(S::b[4])));
+              res = add(ph[c], scl(pb, dt));
+              const C corr = add(ph[c], scl(pa, dt));
               a.h0[gg] = fv;
-              a.h3[gg] = corr;
+              if constexpr (D == 2) const_cast<C*>(a.h2)[gg] = corr;  // over f_{k-3}, its last use
+              if constexpr (D == 3) a.h3[gg] = corr;                  // over f_{k-4}
+              if constexpr (D == 4) a.h4[gg] = corr;                  // over f_{k-5}
             } else if constexpr (MODE == MODE_Y) {
-              res = add(x3[c][k], scl(mul_mi(hm[c]), R(ABM::a0 * a.dt)));
+              res = add(x3[c][k], scl(mul_mi(hm[c]), R(a.ycoef * a.dt)));
             } else if constexpr (MODE == MODE_F) {
               res = mul_mi(hm[c]);
             } else {  // HORNER: out = base + coef (H - E) in

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libwslda_td.so")
 
 FP64, MIXED = 0, 1
 SLDA_A1, BDG = 0, 1
+SCHEMES = {"AB4AM5": 0, "AB3AM4": 1, "AB5AM5": 2}
 # B of the spin-symmetric ASLDA functional (Sec. 2.4): 2^(2/3) [0.357 - 2 A(0) 2^(-5/3)], A(0) = 1.094
 B_SLDA = 2.0 ** (2.0 / 3.0) * (0.357 - 2.0 * 1.094 * 2.0 ** (-5.0 / 3.0))
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN", 5: "EDRIFT", 6: "ETIMEOUT", 7: "ESTATE",
@@ -97,6 +98,7 @@ def _load():
         "wslda_set_graph": (I, [P, I, I]),
         "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
+        "wslda_set_integrator": (I, [P, I]),
         "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
     }
     for name, (res, args) in sig.items():
@@ -185,6 +187,10 @@ class Context:
         self.close()
 
     # ------------------------------------------------------------------ ABI
+    def set_integrator(self, scheme: str):
+        """'AB4AM5' (default), 'AB3AM4' or 'AB5AM5' for boxes added afterwards."""
+        self._check(lib.wslda_set_integrator(self._h, SCHEMES[scheme]))
+
     def add_box(self, shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, C=-1.0, inv_4pi_a=0.0, mu=0.0,
                 ec=-1.0, rho_floor=1e-12, nstates: int) -> int:
         lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])

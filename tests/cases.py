@@ -88,9 +88,11 @@ def oracle_evolve(c: Case, dt: float, nsteps: int, stationary: bool, phi0=None):
     return sysm, st
 
 
-def gpu_context(c: Case, precision: int):
+def gpu_context(c: Case, precision: int, scheme: str | None = None):
     from paper_2602_08982_b300 import wslda as W
     ctx = W.Context(precision)
+    if scheme is not None:
+        ctx.set_integrator(scheme)
     kind = W.SLDA_A1 if c.fn.kind == "slda" else W.BDG
     box = ctx.add_box(c.lat.shape, (c.lat.dx, c.lat.dy, c.lat.dz), kind=kind, B=c.fn.B, C=c.fn.C,
                       inv_4pi_a=c.fn.inv_4pi_a, mu=c.fn.mu, nstates=c.phi.shape[0])
