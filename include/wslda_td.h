@@ -279,6 +279,38 @@ wslda_status wslda_static_solve(wslda_ctx* ctx, int box, const double* U0, const
 wslda_status wslda_densities_noalloc(int precision, const void* uv, const double* w_minus, const double* w_plus,
                                      int64_t nstates, int nx, int ny, int nz, double* rho, double* nu, void* stream);
 
+/* Learned starting fields for the static solver (a companion of Alg. 1, not a
+ * method of the paper): a network of four 3x3x3 convolutions with periodic
+ * wrap-around, channels 2 -> hidden -> hidden -> hidden -> 2, tanh between
+ * layers, mapping per-site (V_ext / eF, coupling) to (U / eF, Delta / eF).
+ * Weights: float32 master copy, used rounded to bfloat16 (nearest even);
+ * activations, accumulation, gradients and Adam (b1 0.9, b2 0.999, eps 1e-8)
+ * are float32. Parameters are flattened per layer as W[co][ci][27] (offset
+ * (dx, dy, dz) in {-1, 0, 1}^3 at (dx+1)*9 + (dy+1)*3 + (dz+1)) then bias[co];
+ * a layer computes y[b][co][r] = bias[co] + sum_ci sum_d W[co][ci][d]
+ * x[b][ci][r + d]. Activations are device float arrays [batch][2][M]; the
+ * calls queue work on `stream` (a cudaStream_t); loss_grad synchronises it.
+ *  - create: hidden is 8 or 32; up to max_batch samples per call; parameters
+ *    start at zero (set them with set_params, host floats; this also resets
+ *    Adam's moments).
+ *  - loss_grad: forward, mean squared error against the targets, backward;
+ *    the gradient stays in the network for adam() and is copied to grad_host
+ *    when that pointer is not NULL.
+ *  - symmetrize: average of each of nfields fields over the reflections
+ *    i -> N - i (mod N) of the three axes (out must not alias y). */
+typedef struct wslda_net wslda_net;
+wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch, wslda_net** out);
+void wslda_net_destroy(wslda_net* net);
+const char* wslda_net_last_error(const wslda_net* net);
+int64_t wslda_net_param_count(const wslda_net* net);
+wslda_status wslda_net_set_params(wslda_net* net, const float* theta);
+wslda_status wslda_net_get_params(wslda_net* net, float* theta);
+wslda_status wslda_net_forward(wslda_net* net, const float* x, int batch, float* y, void* stream);
+wslda_status wslda_net_loss_grad(wslda_net* net, const float* x, const float* target, int batch, double* loss,
+                                 float* grad_host, void* stream);
+wslda_status wslda_net_adam(wslda_net* net, double lr, void* stream);
+wslda_status wslda_net_symmetrize(const float* y, int64_t nfields, int nx, int ny, int nz, float* out, void* stream);
+
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
  * the context's stream and its duration is added to the kernel's total.
  * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction,

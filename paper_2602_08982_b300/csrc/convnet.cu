@@ -1,0 +1,457 @@
+// Learned starting fields for the static self-consistent solver: a stack of
+// four 3x3x3 convolutions with periodic wrap-around (the lattice of Sec. 3.1
+// is periodic), channels 2 -> H -> H -> H -> 2, tanh between layers, trained
+// on the mean squared error with Adam (Kingma and Ba, arXiv:1412.6980).
+// Inputs per site: V_ext / eF and the coupling; outputs: U / eF, Delta / eF,
+// which start the iteration of Alg. 1 (Sec. 3.2).
+//
+// Weights are kept as a float32 master copy and used in bfloat16 (rounded to
+// nearest even before every forward pass); activations, accumulation,
+// gradients and the optimiser are float32. Layout: activations [B][C][M]
+// (M = nx ny nz, z fastest); parameters flattened per layer as
+// W[co][ci][27] (offset (dx, dy, dz) in {-1,0,1}^3 at (dx+1)*9 + (dy+1)*3 +
+// (dz+1)) followed by bias[co]. A layer computes
+//   y[b][co][r] = bias[co] + sum_ci sum_d W[co][ci][d] x[b][ci][r + d].
+//
+// Kernels: quantize (bfloat16 weight copy), conv_fwd (thread per site, all
+// output channels in registers, the layer's weights in shared memory),
+// conv_bwd_data (transposed and mirrored weights, times 1 - a^2 through tanh),
+// conv_bwd_weight (CTA per (co, ci) pair, fixed-order reduction over batch and
+// sites), bias_grad, mse (gradient of the loss and per-block partial sums),
+// adam, mirror_avg (projection onto reflection-symmetric fields).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/wslda_td.h"
+
+namespace {
+
+constexpr int kLayers = 4;
+constexpr int kIO = 2;  // input and output channels
+
+struct Lat {
+  int nx, ny, nz;
+};
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// site index of (ix, iy, iz) + d, periodic; d = offset index 0..26
+__device__ __forceinline__ int neighbour(const Lat& L, int ix, int iy, int iz, int d) {
+  const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+  return (wrap(ix + dx, L.nx) * L.ny + wrap(iy + dy, L.ny)) * L.nz + wrap(iz + dz, L.nz);
+}
+
+__global__ void quantize(const float* __restrict__ theta, float* __restrict__ wq, int64_t n, const int64_t* wb,
+                         const int64_t* we) {
+  // weight entries [wb[l], we[l]) of each layer are rounded; biases are copied
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool w = false;
+  for (int l = 0; l < kLayers; ++l) w = w || (i >= wb[l] && i < we[l]);
+  wq[i] = w ? __bfloat162float(__float2bfloat16_rn(theta[i])) : theta[i];
+}
+
+// Forward layer: COUT accumulators per thread; grid (ceil(M/128), B).
+template <int COUT>
+__global__ void __launch_bounds__(128) conv_fwd(Lat L, int cin, const float* __restrict__ W,
+                                                const float* __restrict__ bias, const float* __restrict__ x,
+                                                float* __restrict__ y, int act) {
+  extern __shared__ float w_s[];  // [COUT][cin][27] then bias[COUT]
+  const int M = L.nx * L.ny * L.nz;
+  const int nw = COUT * cin * 27;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) w_s[i] = W[i];
+  for (int i = threadIdx.x; i < COUT; i += blockDim.x) w_s[nw + i] = bias[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int b = blockIdx.y;
+  const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
+  const float* xb = x + int64_t(b) * cin * M;
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = w_s[nw + co];
+  for (int d = 0; d < 27; ++d) {
+    const int q = neighbour(L, ix, iy, iz, d);
+    for (int ci = 0; ci < cin; ++ci) {
+      const float v = xb[int64_t(ci) * M + q];
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(w_s[(co * cin + ci) * 27 + d], v, acc[co]);
+    }
+  }
+  float* yb = y + int64_t(b) * COUT * M;
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) yb[int64_t(co) * M + s] = act ? tanhf(acc[co]) : acc[co];
+}
+
+// Gradient with respect to the layer input: CIN accumulators per thread,
+// gx[ci][r] = sum_co sum_d W[co][ci][d] g[co][r - d]; when `through_tanh`
+// the result is multiplied by 1 - x^2 (x the layer input, a tanh output).
+template <int CIN>
+__global__ void __launch_bounds__(128) conv_bwd_data(Lat L, int cout, const float* __restrict__ W,
+                                                     const float* __restrict__ g, const float* __restrict__ x,
+                                                     float* __restrict__ gx, int through_tanh) {
+  extern __shared__ float w_s[];  // [cout][CIN][27]
+  const int M = L.nx * L.ny * L.nz;
+  const int nw = cout * CIN * 27;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) w_s[i] = W[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int b = blockIdx.y;
+  const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
+  const float* gb = g + int64_t(b) * cout * M;
+  float acc[CIN];
+#pragma unroll
+  for (int ci = 0; ci < CIN; ++ci) acc[ci] = 0.f;
+  for (int d = 0; d < 27; ++d) {
+    const int q = neighbour(L, ix, iy, iz, 26 - d);  // r - d
+    for (int co = 0; co < cout; ++co) {
+      const float v = gb[int64_t(co) * M + q];
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) acc[ci] = fmaf(w_s[(co * CIN + ci) * 27 + d], v, acc[ci]);
+    }
+  }
+  const float* xb = x + int64_t(b) * CIN * M;
+  float* ob = gx + int64_t(b) * CIN * M;
+#pragma unroll
+  for (int ci = 0; ci < CIN; ++ci) {
+    float v = acc[ci];
+    if (through_tanh) {
+      const float a = xb[int64_t(ci) * M + s];
+      v *= 1.f - a * a;
+    }
+    ob[int64_t(ci) * M + s] = v;
+  }
+}
+
+// Weight gradient: CTA per (co, ci); 27 partial sums per thread over the
+// batch and sites, then a fixed-order reduction across the CTA.
+__global__ void __launch_bounds__(256) conv_bwd_weight(Lat L, int cin, int cout, int batch,
+                                                       const float* __restrict__ g, const float* __restrict__ x,
+                                                       float* __restrict__ gW) {
+  __shared__ float red[8][27];
+  const int co = blockIdx.x / cin, ci = blockIdx.x % cin;
+  const int M = L.nx * L.ny * L.nz;
+  float acc[27];
+#pragma unroll
+  for (int d = 0; d < 27; ++d) acc[d] = 0.f;
+  const int64_t total = int64_t(batch) * M;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = int(t / M), s = int(t % M);
+    const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
+    const float gv = g[(int64_t(b) * cout + co) * M + s];
+    const float* xb = x + (int64_t(b) * cin + ci) * M;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) acc[d] = fmaf(gv, xb[neighbour(L, ix, iy, iz, d)], acc[d]);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    float v = acc[d];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    float v = 0.f;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i][threadIdx.x];
+    gW[(co * cin + ci) * 27 + threadIdx.x] = v;
+  }
+}
+
+// Bias gradient: CTA per output channel.
+__global__ void __launch_bounds__(256) bias_grad(int M, int cout, int batch, const float* __restrict__ g,
+                                                 float* __restrict__ gb) {
+  __shared__ float red[8];
+  const int co = blockIdx.x;
+  float acc = 0.f;
+  const int64_t total = int64_t(batch) * M;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = int(t / M), s = int(t % M);
+    acc += g[(int64_t(b) * cout + co) * M + s];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i];
+    gb[co] = v;
+  }
+}
+
+// dL/dy = 2 (y - t) / n and per-block partial sums of (y - t)^2.
+__global__ void __launch_bounds__(256) mse(const float* __restrict__ y, const float* __restrict__ t, int64_t n,
+                                           float* __restrict__ g, double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  const float scale = float(2.0 / double(n));
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float d = y[i] - t[i];
+    g[i] = scale * d;
+    acc += double(d) * double(d);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i];
+    part[blockIdx.x] = v;
+  }
+}
+
+__global__ void adam(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                     float* __restrict__ v, int64_t n, float lr, float b1, float b2, float c1, float c2, float eps) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void mirror_avg(Lat L, int64_t nfields, const float* __restrict__ y, float* __restrict__ out) {
+  const int M = L.nx * L.ny * L.nz;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nfields * M) return;
+  const int64_t f = i / M;
+  const int s = int(i % M);
+  const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
+  const float* yf = y + f * M;
+  // the 8 images summed in ascending site order, so every site of an orbit
+  // gets the bit-identical average
+  int idx[8];
+  for (int k = 0; k < 8; ++k) {
+    const int jx = (k & 4) ? (L.nx - ix) % L.nx : ix;
+    const int jy = (k & 2) ? (L.ny - iy) % L.ny : iy;
+    const int jz = (k & 1) ? (L.nz - iz) % L.nz : iz;
+    int q = (jx * L.ny + jy) * L.nz + jz, k2 = k;
+    while (k2 > 0 && idx[k2 - 1] > q) {
+      idx[k2] = idx[k2 - 1];
+      --k2;
+    }
+    idx[k2] = q;
+  }
+  float acc = 0.f;
+  for (int k = 0; k < 8; ++k) acc += yf[idx[k]];
+  out[i] = 0.125f * acc;
+}
+
+}  // namespace
+
+struct wslda_net {
+  Lat L{};
+  int M = 0, hidden = 0, max_batch = 0;
+  int cin[kLayers] = {}, cout[kLayers] = {};
+  int64_t woff[kLayers] = {}, boff[kLayers] = {}, P = 0;
+  float *theta = nullptr, *wq = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  float* act[kLayers + 1] = {};  // act[0] is the caller's input (not owned)
+  float *g0 = nullptr, *g1 = nullptr;
+  double* part = nullptr;
+  int64_t *wb = nullptr, *we = nullptr;
+  int64_t step = 0;
+  std::vector<void*> owned;
+  std::string err;
+};
+
+namespace {
+constexpr int kMseBlocks = 148;
+
+wslda_status net_fail(wslda_net* n, wslda_status s, const std::string& msg) {
+  if (n) n->err = msg;
+  return s;
+}
+
+template <int COUT>
+cudaError_t launch_fwd(const wslda_net* n, int l, const float* x, float* y, int batch, cudaStream_t s) {
+  const size_t smem = (size_t(COUT) * n->cin[l] * 27 + COUT) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(conv_fwd<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid(unsigned((n->M + 127) / 128), unsigned(batch));
+  conv_fwd<COUT><<<grid, 128, smem, s>>>(n->L, n->cin[l], n->wq + n->woff[l], n->wq + n->boff[l], x, y,
+                                         l < kLayers - 1);
+  return cudaGetLastError();
+}
+
+template <int CIN>
+cudaError_t launch_bwd_data(const wslda_net* n, int l, const float* g, float* gx, int batch, cudaStream_t s) {
+  const size_t smem = size_t(n->cout[l]) * CIN * 27 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(conv_bwd_data<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid(unsigned((n->M + 127) / 128), unsigned(batch));
+  conv_bwd_data<CIN><<<grid, 128, smem, s>>>(n->L, n->cout[l], n->wq + n->woff[l], g, n->act[l], gx, l > 0);
+  return cudaGetLastError();
+}
+
+cudaError_t forward(wslda_net* n, const float* x, int batch, float* y, cudaStream_t s) {
+  cudaError_t e;
+  const int64_t P = n->P;
+  quantize<<<unsigned((P + 255) / 256), 256, 0, s>>>(n->theta, n->wq, P, n->wb, n->we);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  n->act[0] = const_cast<float*>(x);
+  for (int l = 0; l < kLayers; ++l) {
+    float* out = (l == kLayers - 1 && y) ? y : n->act[l + 1];
+    const int co = n->cout[l];
+    if (co == 2) e = launch_fwd<2>(n, l, n->act[l], out, batch, s);
+    else if (co == 8) e = launch_fwd<8>(n, l, n->act[l], out, batch, s);
+    else e = launch_fwd<32>(n, l, n->act[l], out, batch, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch, wslda_net** out) {
+  if (!out || nx < 3 || ny < 3 || nz < 3 || (hidden != 8 && hidden != 32) || max_batch < 1) return WSLDA_EINVAL;
+  *out = nullptr;
+  wslda_net* n = new wslda_net();
+  n->L = {nx, ny, nz};
+  n->M = nx * ny * nz;
+  n->hidden = hidden;
+  n->max_batch = max_batch;
+  const int ch[kLayers + 1] = {kIO, hidden, hidden, hidden, kIO};
+  int64_t k = 0;
+  for (int l = 0; l < kLayers; ++l) {
+    n->cin[l] = ch[l];
+    n->cout[l] = ch[l + 1];
+    n->woff[l] = k;
+    k += int64_t(ch[l + 1]) * ch[l] * 27;
+    n->boff[l] = k;
+    k += ch[l + 1];
+  }
+  n->P = k;
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    n->owned.push_back(*p);
+    return true;
+  };
+  const size_t amax = size_t(max_batch) * hidden * n->M * sizeof(float);
+  bool ok = alloc((void**)&n->theta, n->P * 4) && alloc((void**)&n->wq, n->P * 4) &&
+            alloc((void**)&n->grad, n->P * 4) && alloc((void**)&n->m, n->P * 4) && alloc((void**)&n->v, n->P * 4) &&
+            alloc((void**)&n->g0, amax) && alloc((void**)&n->g1, amax) &&
+            alloc((void**)&n->part, kMseBlocks * sizeof(double)) && alloc((void**)&n->wb, kLayers * 8) &&
+            alloc((void**)&n->we, kLayers * 8);
+  for (int l = 1; l <= kLayers && ok; ++l)
+    ok = alloc((void**)&n->act[l], size_t(max_batch) * ch[l] * n->M * sizeof(float));
+  if (ok) {
+    int64_t wb[kLayers], we[kLayers];
+    for (int l = 0; l < kLayers; ++l) {
+      wb[l] = n->woff[l];
+      we[l] = n->boff[l];
+    }
+    ok = cudaMemcpy(n->wb, wb, sizeof(wb), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(n->we, we, sizeof(we), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(n->theta, 0, n->P * 4) == cudaSuccess && cudaMemset(n->m, 0, n->P * 4) == cudaSuccess &&
+         cudaMemset(n->v, 0, n->P * 4) == cudaSuccess;
+  }
+  if (!ok) {
+    for (void* p : n->owned) cudaFree(p);
+    delete n;
+    return WSLDA_ENOMEM;
+  }
+  *out = n;
+  return WSLDA_OK;
+}
+
+void wslda_net_destroy(wslda_net* n) {
+  if (!n) return;
+  for (void* p : n->owned) cudaFree(p);
+  delete n;
+}
+
+const char* wslda_net_last_error(const wslda_net* n) { return n ? n->err.c_str() : "null network"; }
+
+int64_t wslda_net_param_count(const wslda_net* n) { return n ? n->P : -1; }
+
+wslda_status wslda_net_set_params(wslda_net* n, const float* theta) {
+  if (!n || !theta) return WSLDA_EINVAL;
+  for (int64_t i = 0; i < n->P; ++i)
+    if (!std::isfinite(theta[i])) return net_fail(n, WSLDA_ENAN, "non-finite parameter");
+  if (cudaMemcpy(n->theta, theta, n->P * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(n->m, 0, n->P * 4) != cudaSuccess || cudaMemset(n->v, 0, n->P * 4) != cudaSuccess)
+    return net_fail(n, WSLDA_ECUDA, "set_params copy failed");
+  n->step = 0;
+  return WSLDA_OK;
+}
+
+wslda_status wslda_net_get_params(wslda_net* n, float* theta) {
+  if (!n || !theta) return WSLDA_EINVAL;
+  if (cudaMemcpy(theta, n->theta, n->P * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return net_fail(n, WSLDA_ECUDA, "get_params copy failed");
+  return WSLDA_OK;
+}
+
+wslda_status wslda_net_forward(wslda_net* n, const float* x, int batch, float* y, void* stream) {
+  if (!n || !x || !y || batch < 1 || batch > n->max_batch) return WSLDA_EINVAL;
+  cudaError_t e = forward(n, x, batch, y, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return net_fail(n, WSLDA_ECUDA, std::string("forward: ") + cudaGetErrorString(e));
+  return WSLDA_OK;
+}
+
+wslda_status wslda_net_loss_grad(wslda_net* n, const float* x, const float* t, int batch, double* loss,
+                                 float* grad_host, void* stream) {
+  if (!n || !x || !t || !loss || batch < 1 || batch > n->max_batch) return WSLDA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = forward(n, x, batch, nullptr, s);
+  const int64_t nout = int64_t(batch) * kIO * n->M;
+  float* g = n->g0;
+  float* gnext = n->g1;
+  if (e == cudaSuccess) {
+    mse<<<kMseBlocks, 256, 0, s>>>(n->act[kLayers], t, nout, g, n->part);
+    e = cudaGetLastError();
+  }
+  for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+    conv_bwd_weight<<<unsigned(n->cout[l] * n->cin[l]), 256, 0, s>>>(n->L, n->cin[l], n->cout[l], batch, g,
+                                                                     n->act[l], n->grad + n->woff[l]);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    bias_grad<<<unsigned(n->cout[l]), 256, 0, s>>>(n->M, n->cout[l], batch, g, n->grad + n->boff[l]);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if (l > 0) {
+      e = n->cin[l] == 8 ? launch_bwd_data<8>(n, l, g, gnext, batch, s) : launch_bwd_data<32>(n, l, g, gnext, batch, s);
+      std::swap(g, gnext);
+    }
+  }
+  std::vector<double> part(kMseBlocks);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), n->part, kMseBlocks * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && grad_host) e = cudaMemcpyAsync(grad_host, n->grad, n->P * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return net_fail(n, WSLDA_ECUDA, std::string("loss_grad: ") + cudaGetErrorString(e));
+  double acc = 0.0;
+  for (double p : part) acc += p;
+  *loss = acc / double(nout);
+  return std::isfinite(*loss) ? WSLDA_OK : net_fail(n, WSLDA_ENAN, "non-finite loss");
+}
+
+wslda_status wslda_net_adam(wslda_net* n, double lr, void* stream) {
+  if (!n || !(lr > 0.0)) return WSLDA_EINVAL;
+  const double b1 = 0.9, b2 = 0.999;
+  n->step += 1;
+  const double c1 = 1.0 - std::pow(b1, double(n->step)), c2 = 1.0 - std::pow(b2, double(n->step));
+  adam<<<unsigned((n->P + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n->theta, n->grad, n->m, n->v, n->P, float(lr), float(b1), float(b2), float(c1), float(c2), 1e-8f);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? WSLDA_OK : net_fail(n, WSLDA_ECUDA, std::string("adam: ") + cudaGetErrorString(e));
+}
+
+wslda_status wslda_net_symmetrize(const float* y, int64_t nfields, int nx, int ny, int nz, float* out,
+                                  void* stream) {
+  if (!y || !out || y == out || nfields < 0 || nx < 1 || ny < 1 || nz < 1) return WSLDA_EINVAL;
+  const int64_t total = nfields * int64_t(nx) * ny * nz;
+  if (total == 0) return WSLDA_OK;
+  mirror_avg<<<unsigned((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(Lat{nx, ny, nz}, nfields,
+                                                                                          y, out);
+  return cudaGetLastError() == cudaSuccess ? WSLDA_OK : WSLDA_ECUDA;
+}
+
+}  // extern "C"

@@ -99,6 +99,16 @@ def _load():
         "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
         "wslda_set_integrator": (I, [P, I]),
+        "wslda_net_create": (I, [I, I, I, I, I, ct.POINTER(P)]),
+        "wslda_net_destroy": (None, [P]),
+        "wslda_net_last_error": (ct.c_char_p, [P]),
+        "wslda_net_param_count": (I64, [P]),
+        "wslda_net_set_params": (I, [P, P]),
+        "wslda_net_get_params": (I, [P, P]),
+        "wslda_net_forward": (I, [P, P, I, P, P]),
+        "wslda_net_loss_grad": (I, [P, P, P, I, DP, P, P]),
+        "wslda_net_adam": (I, [P, D, P]),
+        "wslda_net_symmetrize": (I, [P, I64, I, I, I, P, P]),
         "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
     }
     for name, (res, args) in sig.items():
@@ -340,3 +350,78 @@ class Context:
         n = ct.c_int64()
         self._check(lib.wslda_get_kernel_time(self._h, k, ct.byref(ms), ct.byref(n)))
         return ms.value, n.value
+
+
+class Net:
+    """The learned starting-field network (wslda_net_*): four periodic 3x3x3
+    convolutions 2 -> hidden -> hidden -> hidden -> 2 with tanh, bfloat16
+    weights. Activations are device float32 arrays [batch][2][M] given as
+    torch tensors (or raw device pointers)."""
+
+    def __init__(self, shape, hidden: int = 32, max_batch: int = 16):
+        h = ct.c_void_p()
+        st = lib.wslda_net_create(int(shape[0]), int(shape[1]), int(shape[2]), int(hidden), int(max_batch),
+                                  ct.byref(h))
+        if st:
+            raise WsldaError(st, "wslda_net_create failed")
+        self._h = h
+        self.shape = tuple(int(v) for v in shape)
+        self.hidden = hidden
+        self.max_batch = max_batch
+
+    def _check(self, st: int):
+        if st:
+            raise WsldaError(st, lib.wslda_net_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib.wslda_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nparams(self) -> int:
+        return int(lib.wslda_net_param_count(self._h))
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.nparams:
+            raise ValueError("wrong parameter count")
+        self._check(lib.wslda_net_set_params(self._h, t.ctypes.data_as(ct.c_void_p)))
+
+    def get_params(self):
+        t = np.empty(self.nparams, dtype=np.float32)
+        self._check(lib.wslda_net_get_params(self._h, t.ctypes.data_as(ct.c_void_p)))
+        return t
+
+    @staticmethod
+    def _dev(x):
+        return ct.c_void_p(x.data_ptr()) if hasattr(x, "data_ptr") else ct.c_void_p(int(x))
+
+    @staticmethod
+    def _stream(stream):
+        return ct.c_void_p(0 if stream is None else int(stream))
+
+    def forward(self, x, y, batch: int, stream=None):
+        self._check(lib.wslda_net_forward(self._h, self._dev(x), int(batch), self._dev(y), self._stream(stream)))
+
+    def loss_grad(self, x, target, batch: int, want_grad: bool = False, stream=None):
+        loss = ct.c_double()
+        g = np.empty(self.nparams, dtype=np.float32) if want_grad else None
+        self._check(lib.wslda_net_loss_grad(self._h, self._dev(x), self._dev(target), int(batch), ct.byref(loss),
+                                            g.ctypes.data_as(ct.c_void_p) if want_grad else None,
+                                            self._stream(stream)))
+        return (loss.value, g) if want_grad else loss.value
+
+    def adam(self, lr: float, stream=None):
+        self._check(lib.wslda_net_adam(self._h, float(lr), self._stream(stream)))
+
+    def symmetrize(self, y, out, nfields: int, stream=None):
+        st = lib.wslda_net_symmetrize(self._dev(y), int(nfields), *self.shape, self._dev(out), self._stream(stream))
+        if st:
+            raise WsldaError(st, "wslda_net_symmetrize failed")

@@ -1,0 +1,96 @@
+"""The learned starting-field network on the GPU against its oracle, and what
+it gains for the static solver."""
+import numpy as np
+import pytest
+
+from oracle import convnet as cn
+from paper_2602_08982_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(shape, hidden, batch, seed):
+    import torch
+    from paper_2602_08982_b300 import wslda as W
+    net = W.Net(shape, hidden=hidden, max_batch=batch)
+    shapes = cn.layer_shapes(2, hidden, 2)
+    assert net.nparams == cn.param_count(shapes)
+    theta = (0.4 * (2.0 * inputs.uniform01(seed, net.nparams) - 1.0)).astype(np.float32)
+    net.set_params(theta)
+    M = int(np.prod(shape))
+    x = (2.0 * inputs.uniform01(seed + 1, batch * 2 * M) - 1.0).astype(np.float32).reshape(batch, 2, M)
+    t = (0.5 * inputs.uniform01(seed + 2, batch * 2 * M)).astype(np.float32).reshape(batch, 2, M)
+    xd, td = torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda")
+    return net, shapes, theta, x, t, xd, td
+
+
+@pytest.mark.parametrize("shape,hidden,batch", [((6, 6, 8), 8, 2), ((12, 12, 12), 32, 3)])
+def test_forward_and_gradient_match_oracle(shape, hidden, batch):
+    import torch
+    net, shapes, theta, x, t, xd, td = _setup(shape, hidden, batch, 101)
+    M = int(np.prod(shape))
+    y = torch.empty_like(xd)
+    net.forward(xd, y, batch)
+    th = theta.astype(np.float64)
+    xo = x.astype(np.float64).reshape((batch, 2) + shape)
+    to = t.astype(np.float64).reshape((batch, 2) + shape)
+    yo, _ = cn.forward(th, shapes, xo)
+    assert np.abs(y.cpu().numpy().reshape(yo.shape) - yo).max() < 2e-5 * np.abs(yo).max()
+    loss, g = net.loss_grad(xd, td, batch, want_grad=True)
+    Lo, go = cn.gradient(th, shapes, xo, to)
+    assert abs(loss - Lo) < 1e-5 * Lo
+    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+    net.close()
+
+
+def test_adam_step_matches_oracle():
+    net, shapes, theta, x, t, xd, td = _setup((6, 6, 8), 8, 2, 202)
+    _, g = net.loss_grad(xd, td, 2, want_grad=True)
+    net.adam(1e-3)
+    got = net.get_params()
+    opt = cn.Adam(net.nparams, lr=1e-3)
+    ref = opt.step(theta.astype(np.float64), g.astype(np.float64))
+    assert np.abs(got - ref).max() < 1e-6
+    net.close()
+
+
+def test_symmetrize_matches_mirror_average():
+    import torch
+    from paper_2602_08982_b300 import wslda as W
+    shape = (6, 8, 4)
+    net = W.Net(shape, hidden=8, max_batch=1)
+    y = (2.0 * inputs.uniform01(7, 3 * 192) - 1.0).astype(np.float32).reshape(3, 192)
+    yd = torch.as_tensor(y, device="cuda")
+    out = torch.empty_like(yd)
+    net.symmetrize(yd, out, 3)
+    ref = cn.mirror_average(y.astype(np.float64).reshape((1, 3) + shape)).reshape(3, 192)
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-6
+    net.close()
+
+
+def test_trained_network_cuts_static_iterations():
+    """Train on solved 12^3 traps, then start held-out traps from the network's
+    fields and from the uniform system's: plain linear mixing needs fewer
+    iterations from the network's start."""
+    import torch
+    from paper_2602_08982_b300 import learned as L
+    from paper_2602_08982_b300 import wslda as W
+    shape = (12, 12, 12)
+    X, T, _ = L.dataset(shape, 32, seed=1000)
+    net = W.Net(shape, hidden=32, max_batch=8)
+    L.init_params(net, 77)
+    losses = L.train(net, torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda"), steps=400, batch=8,
+                     lr=2e-3, seed=5)
+    assert losses[-1] < 0.2 * losses[0]
+    base, learned = [], []
+    for seed in (5000, 5001, 5003):
+        om, a = L.draw_trap(seed, 0.1, 0.2)
+        n0, ok0 = L.iterations(shape, om, a, eps=1e-5, max_iters=400)
+        U, D = L.predict(net, L.net_input(shape, om, a))
+        # the BdG functional has no mean field: only Delta is taken from the network
+        n1, ok1 = L.iterations(shape, om, a, U0=np.zeros_like(U), D0=D, eps=1e-5, max_iters=400)
+        assert ok0 and ok1
+        base.append(n0)
+        learned.append(n1)
+    net.close()
+    assert np.mean(learned) < 0.8 * np.mean(base), (base, learned)
