@@ -40,6 +40,11 @@ FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (SM count x FP64 units x cloc
 RHO_SIGMA = 1.0 / (6 * math.pi ** 2)
 
 
+def _omega(text):
+    v = [float(x) for x in text.split(",")]
+    return v[0] if len(v) == 1 else tuple(v)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -48,7 +53,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--shape", default="32,32,32")
     p.add_argument("--nstates", type=int, default=32768)
-    p.add_argument("--omega", type=float, default=0.05)
+    p.add_argument("--omega", type=_omega, default=0.05,
+                   help="trap frequency, or wx,wy,wz for an anisotropic trap")
     p.add_argument("--dt", type=float, default=0.007)
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     p.add_argument("--no-e2e", action="store_true")
