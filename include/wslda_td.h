@@ -250,6 +250,9 @@ typedef struct {
   int method;        /* 0 linear mixing, 1 modified Broyden mixing */
   int broyden_memory;   /* iterations kept, 1..8; <= 0: 7 */
   double broyden_w0;    /* regularisation weight w_0; <= 0: 0.01 */
+  int fp32_iters;       /* leading iterations that diagonalise in single precision (a cheaper
+                           approach to the fixed point); convergence is judged only between
+                           two double-precision iterations; 0: double throughout */
 } wslda_scf_params;
 typedef struct {
   int iters, converged;

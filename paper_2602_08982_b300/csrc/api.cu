@@ -979,7 +979,7 @@ wslda_status wslda_static_solve(wslda_ctx* c, int box, const double* U0, const d
   if (!(p->mixing > 0.0 && p->mixing <= 1.0) || p->max_iters < 1 || !(p->eps_energy >= 0.0) ||
       !std::isfinite(p->e_ref) || !std::isfinite(p->n_target) || !std::isfinite(p->a_mu) ||
       (p->n_target > 0 && !(p->eps_npart > 0.0)) || (p->method != 0 && p->method != 1) ||
-      !std::isfinite(p->broyden_w0))
+      !std::isfinite(p->broyden_w0) || p->fp32_iters < 0)
     return fail(c, WSLDA_EINVAL, "static_solve: bad parameters");
   const size_t M = size_t(b->M);
   std::vector<double> v(M), d(2 * M);

@@ -7,5 +7,8 @@ WSLDA_INSTANCE(float, 32, 32, 32, 16, 128, 1, 1, 1, 4)
 WSLDA_INSTANCE(float, 32, 32, 32, 4, 512, 1, 1, 1, 1)
 WSLDA_INSTANCE(float, 32, 32, 32, 8, 256, 1, 1, 1, 3)
 WSLDA_INSTANCE(float, 32, 32, 32, 8, 128, 1, 1, 1, 3)
+WSLDA_INSTANCE(float, 32, 32, 32, 8, 192, 1, 1, 1, 3)
 WSLDA_INSTANCE(float, 12, 12, 48, 1, 288, 1, 1, 2)
 WSLDA_INSTANCE(float, 24, 24, 96, 8, 288, 1, 1, 4)
+WSLDA_INSTANCE(float, 24, 24, 96, 12, 256, 1, 1, 4, 2)
+WSLDA_INSTANCE(float, 24, 24, 96, 12, 192, 1, 1, 4, 3)

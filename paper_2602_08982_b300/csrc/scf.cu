@@ -61,8 +61,9 @@ __device__ __forceinline__ void decode(const BlockGeom& g, int r, int& a, int& b
   a = t / g.my;
 }
 
+template <typename T>
 __global__ void build_block(BlockGeom g, const double* __restrict__ U, const double* __restrict__ D,
-                            const double* __restrict__ vext, double mu, double* __restrict__ H) {
+                            const double* __restrict__ vext, double mu, T* __restrict__ H) {
   const int64_t n2 = 2 * int64_t(g.m);
   const int64_t total = n2 * n2;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
@@ -90,7 +91,7 @@ __global__ void build_block(BlockGeom g, const double* __restrict__ U, const dou
       decode(g, r, a, b, cc);
       v = D[lattice_site(g, a, b, cc)];
     }
-    H[idx] = v;
+    H[idx] = T(v);
   }
 }
 
@@ -100,14 +101,15 @@ __global__ void build_block(BlockGeom g, const double* __restrict__ U, const dou
 __device__ __forceinline__ double orbit_weight(int i, int n) { return (i == 0 || 2 * i == n) ? 1.0 : 0.5; }
 
 // Thread = block row r; sums over the m positive-energy columns.
-__global__ void block_density(BlockGeom g, const double* __restrict__ Z, double inv_dV, double* __restrict__ frho,
+template <typename T>
+__global__ void block_density(BlockGeom g, const T* __restrict__ Z, double inv_dV, double* __restrict__ frho,
                               double* __restrict__ fnu) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= g.m) return;
   const int64_t n2 = 2 * int64_t(g.m);
   double sr = 0.0, sn = 0.0;
   for (int j = g.m; j < 2 * g.m; ++j) {
-    const double* col = Z + int64_t(j) * n2;
+    const T* col = Z + int64_t(j) * n2;
     const double cu = col[r], cv = col[g.m + r];
     sr += cv * cv;
     sn += cu * cv;
@@ -125,13 +127,15 @@ __global__ void block_density(BlockGeom g, const double* __restrict__ Z, double 
 // CTA = one positive-energy state (column m + blockIdx.x). The column is
 // staged in shared memory, L_b is applied through its Kronecker structure,
 // and <u|-L/2|u>, <v|-L/2|v> are written as ekin2[2 j], ekin2[2 j + 1].
-__global__ void __launch_bounds__(256) block_kinetic(BlockGeom g, const double* __restrict__ Z,
+template <typename T>
+__global__ void __launch_bounds__(256) block_kinetic(BlockGeom g, const T* __restrict__ Z,
                                                      double* __restrict__ ekin2) {
-  extern __shared__ double col[];
+  extern __shared__ __align__(16) unsigned char col_raw[];
+  T* col = reinterpret_cast<T*>(col_raw);
   __shared__ double red[2][8];
   const int j = blockIdx.x;
   const int64_t n2 = 2 * int64_t(g.m);
-  const double* src = Z + (int64_t(g.m) + j) * n2;
+  const T* src = Z + (int64_t(g.m) + j) * n2;
   for (int i = threadIdx.x; i < 2 * g.m; i += blockDim.x) col[i] = src[i];
   __syncthreads();
   double tu = 0.0, tv = 0.0;
@@ -305,8 +309,8 @@ __device__ __forceinline__ bool axis_basis(int i, int n, int p, int& a, double& 
 
 // Thread = (state j, lattice site s): the block eigenvector expanded on the
 // lattice, scaled to sum_r dV (|u|^2 + |v|^2) = 1.
-template <typename C>
-__global__ void unfold_states(BlockGeom g, const double* __restrict__ Z, double inv_sqrt_dV, C* __restrict__ out) {
+template <typename T, typename C>
+__global__ void unfold_states(BlockGeom g, const T* __restrict__ Z, double inv_sqrt_dV, C* __restrict__ out) {
   const int64_t M = int64_t(g.nx) * g.ny * g.nz;
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(g.m) * M) return;
@@ -317,7 +321,7 @@ __global__ void unfold_states(BlockGeom g, const double* __restrict__ Z, double 
   double fx, fy, fz;
   double u = 0.0, v = 0.0;
   if (axis_basis(ix, g.nx, g.px, a, fx) && axis_basis(iy, g.ny, g.py, b, fy) && axis_basis(iz, g.nz, g.pz, c, fz)) {
-    const double* col = Z + (int64_t(g.m) + j) * 2 * g.m;
+    const T* col = Z + (int64_t(g.m) + j) * 2 * g.m;
     const int r = (a * g.my + b) * g.mz + c;
     const double f = fx * fy * fz * inv_sqrt_dV;
     u = col[r] * f;
@@ -482,7 +486,9 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
     return WSLDA_ECUDA;
   }
   cusolverDnSetStream(sh.h, s);
-  int lwork = 0;
+  // the leading p.fp32_iters iterations diagonalise in single precision in
+  // the same buffers (a float matrix takes half of a double one)
+  int lwork = 0, lwork_s = 0;
   for (const Blk& k : blks) {
     int lw = 0;
     if (cusolverDnDsyevd_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, 2 * k.g.m, k.Z,
@@ -491,11 +497,20 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
       return WSLDA_ECUDA;
     }
     lwork = std::max(lwork, lw);
+    if (p.fp32_iters > 0) {
+      if (cusolverDnSsyevd_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, 2 * k.g.m,
+                                      reinterpret_cast<float*>(k.Z), 2 * k.g.m, reinterpret_cast<float*>(k.W),
+                                      &lw) != CUSOLVER_STATUS_SUCCESS) {
+        err = "cusolverDnSsyevd_bufferSize failed";
+        return WSLDA_ECUDA;
+      }
+      lwork_s = std::max(lwork_s, lw);
+    }
   }
   double *work, *Uin, *Din, *Uout, *frho, *fnu;
   int* info;
   const int nf = (nx / 2 + 1) * (ny / 2 + 1) * (nz / 2 + 1);
-  SCF_CUDA(sc.get(&work, size_t(lwork)));
+  SCF_CUDA(sc.get(&work, std::max<size_t>(size_t(lwork), (size_t(lwork_s) + 1) / 2)));
   SCF_CUDA(sc.get(&info, blks.size()));
   // x = (U_in, Delta_in, mu): the mixed vector; mu lives on the host between iterations
   const int nvec = 2 * M + 1;
@@ -516,7 +531,7 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
   }
   int max_smem = 0;
   for (const Blk& k : blks) max_smem = std::max(max_smem, int(2 * k.g.m * sizeof(double)));
-  SCF_CUDA(cudaFuncSetAttribute(block_kinetic, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  SCF_CUDA(cudaFuncSetAttribute(block_kinetic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
 
   // modified Broyden state: ring of (dF, u) pairs, previous x and F, dot partials
   const bool broyden = p.method == 1;
@@ -558,7 +573,16 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
   int it = 0;
   bool converged = false;
   std::vector<std::vector<double>> evals(blks.size());
+  std::vector<float> evals_s;
+  bool single = false, prev_double = false;
+  SCF_CUDA(cudaFuncSetAttribute(block_kinetic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem / 2));
   for (it = 1; it <= p.max_iters; ++it) {
+    single = it <= p.fp32_iters;
+    if (!single && it == p.fp32_iters + 1 && p.fp32_iters > 0) {
+      bcount = 0;  // the Broyden history of the single-precision phase is dropped
+      bhead = 0;
+      bprev = false;
+    }
     SCF_CUDA(cudaMemsetAsync(frho, 0, size_t(nf) * 8, s));
     SCF_CUDA(cudaMemsetAsync(fnu, 0, size_t(nf) * 8, s));
     for (size_t bi = 0; bi < blks.size(); ++bi) {
@@ -566,15 +590,29 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
       const int n2 = 2 * k.g.m;
       const int64_t tot = int64_t(n2) * n2;
       const unsigned grid = unsigned(std::min<int64_t>((tot + 255) / 256, 148 * 16));
-      build_block<<<grid, 256, 0, s>>>(k.g, Uin, Din, b.vext, fn.mu, k.Z);
-      SCF_CUDA(cudaGetLastError());
-      if (cusolverDnDsyevd(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n2, k.Z, n2, k.W, work, lwork,
-                           info + bi) != CUSOLVER_STATUS_SUCCESS) {
-        err = "cusolverDnDsyevd failed";
-        return WSLDA_ECUDA;
+      if (single) {
+        float* Zs = reinterpret_cast<float*>(k.Z);
+        build_block<float><<<grid, 256, 0, s>>>(k.g, Uin, Din, b.vext, fn.mu, Zs);
+        SCF_CUDA(cudaGetLastError());
+        if (cusolverDnSsyevd(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n2, Zs, n2,
+                             reinterpret_cast<float*>(k.W), reinterpret_cast<float*>(work), lwork_s,
+                             info + bi) != CUSOLVER_STATUS_SUCCESS) {
+          err = "cusolverDnSsyevd failed";
+          return WSLDA_ECUDA;
+        }
+        block_density<float><<<(k.g.m + 127) / 128, 128, 0, s>>>(k.g, Zs, 1.0 / dV, frho, fnu);
+        block_kinetic<float><<<k.g.m, 256, 2 * k.g.m * sizeof(float), s>>>(k.g, Zs, b.ekin2 + 2 * k.first);
+      } else {
+        build_block<double><<<grid, 256, 0, s>>>(k.g, Uin, Din, b.vext, fn.mu, k.Z);
+        SCF_CUDA(cudaGetLastError());
+        if (cusolverDnDsyevd(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n2, k.Z, n2, k.W, work, lwork,
+                             info + bi) != CUSOLVER_STATUS_SUCCESS) {
+          err = "cusolverDnDsyevd failed";
+          return WSLDA_ECUDA;
+        }
+        block_density<double><<<(k.g.m + 127) / 128, 128, 0, s>>>(k.g, k.Z, 1.0 / dV, frho, fnu);
+        block_kinetic<double><<<k.g.m, 256, 2 * k.g.m * sizeof(double), s>>>(k.g, k.Z, b.ekin2 + 2 * k.first);
       }
-      block_density<<<(k.g.m + 127) / 128, 128, 0, s>>>(k.g, k.Z, 1.0 / dV, frho, fnu);
-      block_kinetic<<<k.g.m, 256, 2 * k.g.m * sizeof(double), s>>>(k.g, k.Z, b.ekin2 + 2 * k.first);
       SCF_CUDA(cudaGetLastError());
     }
     scf_fields<<<(M + 127) / 128, 128, 0, s>>>(nx, ny, nz, frho, fnu, Uin, b.vext, fn, b.rho, b.nu, Uout, b.delta);
@@ -585,7 +623,16 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
     SCF_CUDA(cudaMemcpyAsync(hinfo.data(), info, blks.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
     for (size_t bi = 0; bi < blks.size(); ++bi) {
       evals[bi].resize(2 * size_t(blks[bi].g.m));
-      SCF_CUDA(cudaMemcpyAsync(evals[bi].data(), blks[bi].W, evals[bi].size() * 8, cudaMemcpyDeviceToHost, s));
+      if (!single)
+        SCF_CUDA(cudaMemcpyAsync(evals[bi].data(), blks[bi].W, evals[bi].size() * 8, cudaMemcpyDeviceToHost, s));
+    }
+    if (single) {
+      SCF_CUDA(cudaStreamSynchronize(s));
+      for (size_t bi = 0; bi < blks.size(); ++bi) {
+        evals_s.resize(evals[bi].size());
+        SCF_CUDA(cudaMemcpy(evals_s.data(), blks[bi].W, evals_s.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < evals_s.size(); ++j) evals[bi][j] = evals_s[j];
+      }
     }
     SCF_CUDA(cudaStreamSynchronize(s));
     for (size_t bi = 0; bi < blks.size(); ++bi) {
@@ -609,12 +656,14 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
     if (it >= 2) {
       change = 0.0;
       for (int k = 0; k < 6; ++k) change = std::max(change, std::fabs(cur[k] - prev[k]) / e_ref);
-      if (change < p.eps_energy && n_ok) {
+      // convergence is judged only between two double-precision iterations
+      if (change < p.eps_energy && n_ok && !single && prev_double) {
         converged = true;
         break;
       }
     }
     for (int k = 0; k < 6; ++k) prev[k] = cur[k];
+    prev_double = !single;
     if (it == p.max_iters) break;
     // Eq. update-mu is a step of the map; mu_out is mixed with the potentials
     const double mu_out = fixed_n ? fn.mu + (p.a_mu / p.n_target) * (p.n_target - n_sigma) : fn.mu;
@@ -706,10 +755,18 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
   for (const Blk& k : blks) {
     const int64_t tot = int64_t(k.g.m) * M;
     const unsigned grid = unsigned((tot + 255) / 256);
-    if (b.prec == WSLDA_MIXED)
-      unfold_states<float2><<<grid, 256, 0, s>>>(k.g, k.Z, isq, static_cast<float2*>(b.states) + 2 * k.first * M);
+    const float* Zs = reinterpret_cast<const float*>(k.Z);
+    if (b.prec == WSLDA_MIXED && single)
+      unfold_states<float, float2><<<grid, 256, 0, s>>>(k.g, Zs, isq, static_cast<float2*>(b.states) + 2 * k.first * M);
+    else if (b.prec == WSLDA_MIXED)
+      unfold_states<double, float2><<<grid, 256, 0, s>>>(k.g, k.Z, isq,
+                                                         static_cast<float2*>(b.states) + 2 * k.first * M);
+    else if (single)
+      unfold_states<float, double2><<<grid, 256, 0, s>>>(k.g, Zs, isq,
+                                                         static_cast<double2*>(b.states) + 2 * k.first * M);
     else
-      unfold_states<double2><<<grid, 256, 0, s>>>(k.g, k.Z, isq, static_cast<double2*>(b.states) + 2 * k.first * M);
+      unfold_states<double, double2><<<grid, 256, 0, s>>>(k.g, k.Z, isq,
+                                                          static_cast<double2*>(b.states) + 2 * k.first * M);
     SCF_CUDA(cudaGetLastError());
   }
   SCF_CUDA(launch_fill(b.sc, 1.0, M, s));

@@ -55,7 +55,7 @@ class ScfParams(ct.Structure):
     _fields_ = [("mixing", ct.c_double), ("eps_energy", ct.c_double), ("e_ref", ct.c_double),
                 ("max_iters", ct.c_int), ("n_target", ct.c_double), ("a_mu", ct.c_double),
                 ("eps_npart", ct.c_double), ("method", ct.c_int), ("broyden_memory", ct.c_int),
-                ("broyden_w0", ct.c_double)]
+                ("broyden_w0", ct.c_double), ("fp32_iters", ct.c_int)]
 
 
 class ScfResult(ct.Structure):
@@ -241,7 +241,7 @@ class Context:
     def static_solve(self, box: int, U0, delta0, *, mixing: float = 0.5, eps_energy: float = 1e-6,
                      e_ref: float = 0.5, max_iters: int = 200, n_target: float = 0.0, a_mu: float = 0.0,
                      eps_npart: float = 1e-6, method: str = "linear", broyden_memory: int = 7,
-                     broyden_w0: float = 0.01):
+                     broyden_w0: float = 0.01, fp32_iters: int = 0):
         """Static self-consistent solve (Alg. 1); the box's states become the
         positive-energy eigenstates. Returns (result dict, quasiparticle energies)."""
         M = self._M(box)
@@ -254,7 +254,7 @@ class Context:
             raise ValueError("method is 'linear' or 'broyden'")
         prm = ScfParams(float(mixing), float(eps_energy), float(e_ref), int(max_iters), float(n_target),
                         float(a_mu), float(eps_npart), int(method == "broyden"), int(broyden_memory),
-                        float(broyden_w0))
+                        float(broyden_w0), int(fp32_iters))
         out = ScfResult()
         self._check(lib.wslda_static_solve(self._h, box, U0.ctypes.data_as(ct.c_void_p),
                                            d0.ctypes.data_as(ct.c_void_p), ct.byref(prm),

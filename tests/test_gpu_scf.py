@@ -197,3 +197,20 @@ def test_16cubed_trap_converges_and_stays_stationary():
     rho2, _ = ctx.get_densities(b)
     ctx.close()
     assert np.abs(rho2 - rho).max() < 1e-7 * rho.max()
+
+
+def test_single_precision_warmup_reaches_the_double_fixed_point(converged_8):
+    """Leading iterations diagonalised in float change the path, not the fixed
+    point: the final double-precision iterations land where the double-only
+    solve does."""
+    from paper_2602_08982_b300 import wslda as W
+    lat, sd, fn, v, ref = converged_8
+    ctx, b = _ctx(W, W.FP64, lat, fn, v)
+    res, E = ctx.static_solve(b, np.zeros(lat.M), np.full(lat.M, sd.delta), mixing=1.0, eps_energy=1e-8,
+                              max_iters=300, fp32_iters=10)
+    rho, nu = ctx.get_densities(b)
+    ctx.close()
+    assert res["converged"] and res["iters"] > 11
+    assert np.abs(np.sort(E) - np.sort(ref.last.E)).max() < 1e-6 * ref.last.E.max()
+    assert np.abs(rho - ref.last.rho).max() < 1e-6 * ref.last.rho.max()
+    assert np.abs(nu - ref.last.nu).max() < 1e-6 * np.abs(ref.last.nu).max()
