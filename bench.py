@@ -64,6 +64,12 @@ def parse():
                    help="also time the batched workload: 64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps")
     p.add_argument("--integrator", default="AB4AM5", choices=["AB4AM5", "AB3AM4", "AB5AM5"],
                    help="predictor-corrector scheme of Sec. 3.3 (AB4AM5 is Alg. 2)")
+    p.add_argument("--init", default="quench", choices=["quench", "scf"],
+                   help="quench: uniform plane-wave states in the trap (default); scf: states of a static "
+                        "self-consistent solve with nstates = M (slow: minutes at 32^3)")
+    p.add_argument("--scf-n", type=float, default=200.0, help="particle-number target per spin for --init scf")
+    p.add_argument("--scf-iters", type=int, default=40)
+    p.add_argument("--scf-fp32-iters", type=int, default=30)
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -148,12 +154,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arms
-def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5"):
+def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5", mu=None):
     from paper_2602_08982_b300 import inputs
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(prec, stream=stream)
     ctx.set_integrator(scheme)
-    box = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=nstates)
+    box = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"] if mu is None else mu,
+                      nstates=nstates)
     ctx.set_vext(box, inputs.harmonic_trap(shape, omega))
     return ctx, box, u
 
@@ -175,11 +182,47 @@ def stage_x_algorithmic(prec, shape, scheme="AB4AM5"):
     return bytes_per, flops_per
 
 
+SCF_START = {}
+
+
+def scf_start(W, args, shape):
+    """Trapped start from a static self-consistent solve (Alg. 1) of the
+    workload's SLDA system with a particle-number target (Eq. update-mu),
+    modified Broyden mixing and single-precision leading iterations; the
+    states are kept in host memory for every arm."""
+    if "phi" in SCF_START:
+        return SCF_START
+    from paper_2602_08982_b300 import inputs
+    M = shape[0] * shape[1] * shape[2]
+    u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
+    ctx = W.Context(W.FP64)
+    b = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=M)
+    ctx.set_vext(b, inputs.harmonic_trap(shape, args.omega))
+    t0 = time.perf_counter()
+    res, _ = ctx.static_solve(b, np.full(M, u["U"]), np.full(M, u["delta"]), method="broyden", mixing=0.5,
+                              eps_energy=1e-6, max_iters=args.scf_iters, n_target=args.scf_n, a_mu=0.5,
+                              eps_npart=1e-3, fp32_iters=args.scf_fp32_iters)
+    sec = time.perf_counter() - t0
+    SCF_START["phi"] = ctx.get_states(b)
+    ctx.close()
+    SCF_START["info"] = {"iters": res["iters"], "converged": res["converged"], "mu": res["mu"],
+                         "n_sigma": res["n_sigma"], "max_rel_change": res["max_rel_change"], "seconds": sec,
+                         "fp32_iters": args.scf_fp32_iters, "n_target": args.scf_n}
+    return SCF_START
+
+
 def run_arm(W, torch, prec, args, shape, rank, world, dev):
     stream = torch.cuda.current_stream()
-    ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
-    ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
-    ctx.start(args.stationary, args.dt)      # Taylor start: the trapped plane waves are not stationary
+    if args.init == "scf":
+        start = scf_start(W, args, shape)
+        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
+                               mu=start["info"]["mu"])
+        ctx.load_states(box, start["phi"])
+        ctx.start(True, args.dt)               # a static solution: stationary start
+    else:
+        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
+        ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+        ctx.start(args.stationary, args.dt)  # Taylor start: the trapped plane waves are not stationary
     variant = ctx.get_variant(box)
     if args.warmup:
         ctx.step(args.dt, args.warmup)
@@ -417,7 +460,9 @@ def workload_config(args, shape, precision):
                         f"w={args.omega}, {args.nstates} quasiparticle states",
             "lattice": list(shape), "nstates": args.nstates, "trap_omega": args.omega, "dt": args.dt,
             "functional": "SLDA (A=1), B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
-            "init": "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start",
+            "init": ("states of a static self-consistent solve (fixed N, Broyden), stationary start"
+                     if args.init == "scf" else
+                     "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start"),
             "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
@@ -465,6 +510,8 @@ def main():
             "after_steps": 3 + args.warmup + args.steps}
     if e2e:
         line["e2e"] = e2e
+    if "info" in SCF_START:
+        line["scf_start"] = SCF_START["info"]
     if batched:
         line["batched"] = batched
     if cpu:
