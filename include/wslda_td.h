@@ -142,6 +142,14 @@ wslda_status wslda_step(wslda_ctx* ctx, double dt, int nsteps);
 /* Copy the current states out as [n][2][M] complex double. */
 wslda_status wslda_get_states(wslda_ctx* ctx, int box, double* uv, int on_device);
 
+/* The same with complex float elements ([n][2][M], (re, im) float pairs):
+ * the mixed path moves its states at their stored precision (half the bytes
+ * of the double calls; on load they go straight into the state buffer); the
+ * FP64 path widens on load and rounds on read-out. */
+wslda_status wslda_load_states_f32(wslda_ctx* ctx, int box, const float* uv, const double* w_minus,
+                                   const double* w_plus, int on_device);
+wslda_status wslda_get_states_f32(wslda_ctx* ctx, int box, float* uv, int on_device);
+
 /* Densities of the current states: rho = rho_a = rho_b [M], nu [M complex];
  * tau [M] and j [3][M] (Eqs. nab3D..jab3D, gradients with the Nyquist mode
  * zeroed) are computed when the pointers are not NULL. Host pointers. */

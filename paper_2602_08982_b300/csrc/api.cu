@@ -860,6 +860,31 @@ wslda_status wslda_set_dext(wslda_ctx* c, int box, const double* dext, int on_de
   return copy_in(c, b->dext, dext, size_t(b->M) * 16, on_device);
 }
 
+// Frozen weights (T = 0 when NULL) in double and in the working precision;
+// then the device error word (non-finite loaded states) is checked.
+static wslda_status set_weights(wslda_ctx* c, Box& bx, const double* w_minus, const double* w_plus) {
+  Box* b = &bx;
+  std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
+  for (int64_t i = 0; i < b->n; ++i) {
+    if (w_minus) wm[i] = w_minus[i];
+    if (w_plus) wp[i] = w_plus[i];
+    if (!std::isfinite(wm[i]) || !std::isfinite(wp[i])) return fail(c, WSLDA_ENAN, "non-finite weight");
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(b->wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(b->wp, wp.data(), wp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == WSLDA_MIXED) {
+    CUDA_TRY(c, launch_to_real<float>(b->wm, static_cast<float*>(b->wm_r), int64_t(wm.size()), c->stream));
+    CUDA_TRY(c, launch_to_real<float>(b->wp, static_cast<float*>(b->wp_r), int64_t(wp.size()), c->stream));
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(b->wm_r, b->wm, wm.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(b->wp_r, b->wp, wp.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  wslda_status st = check_device_error(c);
+  if (st) return st;
+  b->loaded = true;
+  return WSLDA_OK;
+}
+
 wslda_status wslda_load_states(wslda_ctx* c, int box, const double* uv, const double* w_minus, const double* w_plus,
                                int on_device) {
   CHECK_CTX(c);
@@ -891,25 +916,7 @@ wslda_status wslda_load_states(wslda_ctx* c, int box, const double* uv, const do
   CUDA_TRY(c, launch_fill(b->sc[b->iphi], 1.0, std::max<int64_t>(b->n, 1), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (stage) cudaFree(stage);
-  std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
-  for (int64_t i = 0; i < b->n; ++i) {
-    if (w_minus) wm[i] = w_minus[i];
-    if (w_plus) wp[i] = w_plus[i];
-    if (!std::isfinite(wm[i]) || !std::isfinite(wp[i])) return fail(c, WSLDA_ENAN, "non-finite weight");
-  }
-  CUDA_TRY(c, cudaMemcpyAsync(b->wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(b->wp, wp.data(), wp.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  if (c->prec == WSLDA_MIXED) {
-    CUDA_TRY(c, launch_to_real<float>(b->wm, static_cast<float*>(b->wm_r), int64_t(wm.size()), c->stream));
-    CUDA_TRY(c, launch_to_real<float>(b->wp, static_cast<float*>(b->wp_r), int64_t(wp.size()), c->stream));
-  } else {
-    CUDA_TRY(c, cudaMemcpyAsync(b->wm_r, b->wm, wm.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(b->wp_r, b->wp, wp.size() * 8, cudaMemcpyDeviceToDevice, c->stream));
-  }
-  wslda_status st = check_device_error(c);
-  if (st) return st;
-  b->loaded = true;
-  return WSLDA_OK;
+  return set_weights(c, *b, w_minus, w_plus);
 }
 
 wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, double delta, const int64_t* kidx) {
@@ -1081,6 +1088,79 @@ wslda_status wslda_get_states(wslda_ctx* c, int box, double* uv, int on_device) 
       return fail(c, WSLDA_ECUDA, std::string("widen: ") + cudaGetErrorString(e));
     }
     if (!on_device) CUDA_TRY(c, cudaMemcpyAsync(uv + 2 * off, stage, cnt * 16, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stage) cudaFree(stage);
+  return WSLDA_OK;
+}
+
+wslda_status wslda_load_states_f32(wslda_ctx* c, int box, const float* uv, const double* w_minus,
+                                   const double* w_plus, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || (!uv && b->n > 0)) return fail(c, WSLDA_EINVAL, "load_states_f32: bad box or null pointer");
+  if (c->started) return fail(c, WSLDA_ESTATE, "load_states_f32 after wslda_start");
+  const int64_t total = b->n * 2 * int64_t(b->M);  // complex elements
+  const int64_t per = int64_t(kStageBytes / 8);
+  const float2* src = reinterpret_cast<const float2*>(uv);
+  void* stage = nullptr;
+  if (total > 0 && !on_device && c->prec != WSLDA_MIXED)
+    CUDA_TRY(c, cudaMalloc(&stage, size_t(std::min(total, per)) * 8));
+  for (int64_t off = 0; off < total; off += per) {
+    const int64_t cnt = std::min(per, total - off);
+    const float2* dsrc = src + off;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+      if (c->prec == WSLDA_MIXED) {  // straight into the state slot, then checked in place
+        e = cudaMemcpyAsync(static_cast<float2*>(b->slot[b->iphi]) + off, dsrc, cnt * 8, cudaMemcpyHostToDevice,
+                            c->stream);
+        dsrc = static_cast<const float2*>(b->slot[b->iphi]) + off;
+      } else {
+        e = cudaMemcpyAsync(stage, dsrc, cnt * 8, cudaMemcpyHostToDevice, c->stream);
+        dsrc = static_cast<const float2*>(stage);
+      }
+    }
+    if (e == cudaSuccess)
+      e = c->prec == WSLDA_MIXED
+              ? launch_rescale<float2, float2>(dsrc, static_cast<float2*>(b->slot[b->iphi]) + off, cnt, nullptr, 0,
+                                               1, c->err_d, c->stream)
+              : launch_rescale<float2, double2>(dsrc, static_cast<double2*>(b->slot[b->iphi]) + off, cnt, nullptr, 0,
+                                                1, c->err_d, c->stream);
+    if (e != cudaSuccess) {
+      if (stage) cudaFree(stage);
+      return fail(c, WSLDA_ECUDA, std::string("load_states_f32: ") + cudaGetErrorString(e));
+    }
+  }
+  CUDA_TRY(c, launch_fill(b->sc[b->iphi], 1.0, std::max<int64_t>(b->n, 1), c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stage) cudaFree(stage);
+  return set_weights(c, *b, w_minus, w_plus);
+}
+
+wslda_status wslda_get_states_f32(wslda_ctx* c, int box, float* uv, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || (!uv && b->n > 0)) return fail(c, WSLDA_EINVAL, "get_states_f32: bad box or null pointer");
+  const int64_t total = b->n * 2 * int64_t(b->M);
+  const int64_t per = int64_t(kStageBytes / 8);
+  const int64_t per_state = 2 * int64_t(b->M);
+  float2* out = reinterpret_cast<float2*>(uv);
+  void* stage = nullptr;
+  if (total > 0 && !on_device) CUDA_TRY(c, cudaMalloc(&stage, size_t(std::min(total, per)) * 8));
+  for (int64_t off = 0; off < total; off += per) {
+    const int64_t cnt = std::min(per, total - off);
+    float2* dst = on_device ? out + off : static_cast<float2*>(stage);
+    cudaError_t e = c->prec == WSLDA_MIXED
+                        ? launch_rescale<float2, float2>(static_cast<const float2*>(b->slot[b->iphi]) + off, dst, cnt,
+                                                         b->sc[b->iphi], off, per_state, nullptr, c->stream)
+                        : launch_rescale<double2, float2>(static_cast<const double2*>(b->slot[b->iphi]) + off, dst,
+                                                          cnt, b->sc[b->iphi], off, per_state, nullptr, c->stream);
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(out + off, stage, cnt * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+      if (stage) cudaFree(stage);
+      return fail(c, WSLDA_ECUDA, std::string("get_states_f32: ") + cudaGetErrorString(e));
+    }
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (stage) cudaFree(stage);

@@ -337,6 +337,21 @@ __global__ void widen_kernel(const cx<R>* __restrict__ src, double* __restrict__
   dst[2 * i] = f * double(c.x);
   dst[2 * i + 1] = f * double(c.y);
 }
+// dst = sc[state] * src between complex float / double arrays (sc NULL: 1);
+// non-finite source values set bit 1 of the error word.
+template <typename S, typename D>
+__global__ void rescale_kernel(const S* src, D* dst, int64_t n, const double* sc,
+                               int64_t first, int64_t per_state, int* err) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const S c = src[i];
+  if (err && (!isfinite(double(c.x)) || !isfinite(double(c.y)))) atomicOr(err, 2);
+  const double f = sc ? sc[(first + i) / per_state] : 1.0;
+  D d;
+  d.x = decltype(d.x)(f * double(c.x));
+  d.y = decltype(d.y)(f * double(c.y));
+  dst[i] = d;
+}
 __global__ void fill_kernel(double* p, double v, int64_t n) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -360,6 +375,20 @@ cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t n, const double*
   widen_kernel<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n, sc, first, per_state);
   return cudaGetLastError();
 }
+template <typename S, typename D>
+cudaError_t launch_rescale(const S* src, D* dst, int64_t n, const double* sc, int64_t first, int64_t per_state,
+                           int* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  rescale_kernel<S, D><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, dst, n, sc, first, per_state, err);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rescale<float2, float2>(const float2*, float2*, int64_t, const double*, int64_t, int64_t,
+                                                    int*, cudaStream_t);
+template cudaError_t launch_rescale<float2, double2>(const float2*, double2*, int64_t, const double*, int64_t,
+                                                     int64_t, int*, cudaStream_t);
+template cudaError_t launch_rescale<double2, float2>(const double2*, float2*, int64_t, const double*, int64_t,
+                                                     int64_t, int*, cudaStream_t);
+
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   fill_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(p, v, n);

@@ -167,6 +167,10 @@ template <typename R>
 cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t ncomplex, const double* sc, int64_t first,
                          int64_t per_state, cudaStream_t s);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s);
+// dst = sc[state] * src (sc NULL: 1), complex float <-> double; non-finite src sets err bit 1.
+template <typename S, typename D>
+cudaError_t launch_rescale(const S* src, D* dst, int64_t n, const double* sc, int64_t first, int64_t per_state,
+                           int* err, cudaStream_t s);
 template <typename R>
 cudaError_t launch_to_real(const double* src, R* dst, int64_t n, cudaStream_t s);
 

@@ -99,6 +99,8 @@ def _load():
         "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
         "wslda_set_integrator": (I, [P, I]),
+        "wslda_load_states_f32": (I, [P, I, P, P, P, I]),
+        "wslda_get_states_f32": (I, [P, I, P, I]),
         "wslda_net_create": (I, [I, I, I, I, I, ct.POINTER(P)]),
         "wslda_net_destroy": (None, [P]),
         "wslda_net_last_error": (ct.c_char_p, [P]),
@@ -233,6 +235,23 @@ class Context:
         pm, km = _ptr(w_minus, np.float64, False)
         pp, kp = _ptr(w_plus, np.float64, False)
         self._check(lib.wslda_load_states(self._h, box, p, pm, pp, int(dev)))
+
+    def load_states_f32(self, box: int, uv, w_minus=None, w_plus=None):
+        """load_states with complex64 states (host numpy or device tensor)."""
+        dev = _is_device(uv)
+        p, keep = _ptr(uv, np.complex64, dev)
+        pm, km = _ptr(w_minus, np.float64, False)
+        pp, kp = _ptr(w_plus, np.float64, False)
+        self._check(lib.wslda_load_states_f32(self._h, box, p, pm, pp, int(dev)))
+
+    def get_states_f32(self, box: int, out=None):
+        """get_states as complex64 (host numpy unless `out` is a device tensor)."""
+        n = self.boxes[box][1]
+        if out is None:
+            out = np.empty((n, 2, self._M(box)), dtype=np.complex64)
+        p, keep = _ptr(out, np.complex64, _is_device(out))
+        self._check(lib.wslda_get_states_f32(self._h, box, p, int(_is_device(out))))
+        return out
 
     def fill_uniform_states(self, box: int, mu_eff: float, delta: float, kidx=None):
         p, keep = _ptr(kidx, np.int64, False)

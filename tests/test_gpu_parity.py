@@ -241,3 +241,28 @@ def test_errors_are_status_codes(W):
         ctx.add_box((32, 32, 32), nstates=10 ** 8)
     assert e.value.status == 2
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_complex_float_state_io(prec):
+    """load_states_f32 / get_states_f32 carry the same states as the double
+    calls: a mixed box stores exactly the rounded values either way, and the
+    read-outs agree to float rounding."""
+    c = make_case((8, 8, 8), kick=0.05, trap=0.1, seed=71)
+    a, box = gpu_context(c, prec)
+    a.start(False, 0.01)
+    a.step(0.01, 2)
+    ref = a.get_states(box)
+    got = a.get_states_f32(box)
+    a.close()
+    assert got.dtype == np.complex64
+    assert np.abs(got - ref).max() <= 2.0 ** -23 * np.abs(ref).max()
+    from paper_2602_08982_b300 import wslda as W
+    b = W.Context(prec)
+    kind = W.SLDA_A1 if c.fn.kind == "slda" else W.BDG
+    bx = b.add_box(c.lat.shape, kind=kind, B=c.fn.B, C=c.fn.C, inv_4pi_a=c.fn.inv_4pi_a, mu=c.fn.mu,
+                   nstates=c.phi.shape[0])
+    b.load_states_f32(bx, c.phi.astype(np.complex64))
+    back = b.get_states(bx)
+    b.close()
+    assert np.array_equal(back, c.phi.astype(np.complex64).astype(np.complex128))
