@@ -43,6 +43,8 @@ struct Box {
   int M = 0;
   const KernelSet* ks = nullptr;
   int ncl = 0;           // persistent stage launches: clusters (0 = one cluster per state)
+  const KernelSet* ks_y = nullptr;  // launch variant of the corrector stage (NULL: ks)
+  int ncl_y = 0;
   size_t csize = 0;      // bytes per complex element (8 or 16)
   int D = 3;             // history values the predictor reads (AB3AM4 2, AB4AM5 3, AB5AM5 4)
   void* slot[6] = {};    // D + 2 state buffers [n][2][M]
@@ -286,12 +288,14 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
   ProfScope ps(c, kind);
-  CUDA_TRY(c, b.ks->launch[mode](&a, int(b.n), b.ncl, c->cur));
+  const bool ym = mode == MODE_Y && b.ks_y;
+  const KernelSet* ks = ym ? b.ks_y : b.ks;
+  CUDA_TRY(c, ks->launch[mode](&a, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
   c->launches += 1;
   const bool norm_out = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
                         (mode == MODE_HORNER && a.normalize);
   if (norm_out) {
-    CUDA_TRY(c, launch_finalize_norm(a.npart, b.ks->cs, b.n, box_dV(b), a.sc_out, c->err_d, c->cur));
+    CUDA_TRY(c, launch_finalize_norm(a.npart, ks->cs, b.n, box_dV(b), a.sc_out, c->err_d, c->cur));
     c->launches += 1;
   }
   return WSLDA_OK;
@@ -407,7 +411,8 @@ wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
 template <typename R>
 wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   // cache: (precision, shape, states) -> (variant, persistent clusters)
-  static std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> cache;
+  // (variant, clusters) for the predictor stage, then for the corrector stage
+  static std::vector<std::pair<std::vector<int64_t>, std::vector<int>>> cache;
   if (b.n == 0) return WSLDA_OK;
   // WSLDA_VARIANT=<i> fixes the variant, WSLDA_PERSIST=0/1 the launch form
   const char* forced = getenv("WSLDA_VARIANT");
@@ -417,14 +422,18 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   if (forced) v.assign(1, b.ks);
   if (v.size() == 1 && pmode >= 0) {
     b.ncl = pmode ? resident_clusters(b.ks) : 0;
+    b.ks_y = b.ks;
+    b.ncl_y = b.ncl;
     return WSLDA_OK;
   }
   const std::vector<int64_t> key = {c->prec, b.lat.nx, b.lat.ny, b.lat.nz, std::min<int64_t>(b.n, 512),
                                     forced ? 1 : 0, pmode};
   for (auto& e : cache)
     if (e.first == key) {
-      b.ks = v[e.second.first];
-      b.ncl = e.second.second;
+      b.ks = v[e.second[0]];
+      b.ncl = e.second[1];
+      b.ks_y = v[e.second[2]];
+      b.ncl_y = e.second[3];
       return WSLDA_OK;
     }
   const int64_t nt = std::min<int64_t>(b.n, 512);
@@ -435,8 +444,8 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
   CUDA_TRY(c, cudaEventCreate(&e1));
-  int best = 0, best_ncl = 0;
-  float best_ms = 1e30f;
+  int best[2] = {0, 0}, best_ncl[2] = {0, 0};
+  float best_ms[2] = {1e30f, 1e30f};
   for (size_t k = 0; k < v.size(); ++k) {
     const int res = resident_clusters(v[k]);
     if (res < 1) continue;
@@ -456,34 +465,39 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
       a.sc_out = b.sc[b.ih[1]];
       a.dt = dt;
       a.err = c->err_d;
-      float ms = 1e30f;
-      for (int rep = 0; rep < 4; ++rep) {
-        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-        CUDA_TRY(c, v[k]->launch[x_mode(b)](&a, int(nt), ncl, c->stream));
-        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
-        CUDA_TRY(c, cudaEventSynchronize(e1));
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) ms = std::min(ms, t);
-      }
-      if (getenv("WSLDA_TUNE_VERBOSE"))
-        fprintf(stderr,
-                "[wslda autotune] %dx%dx%d prec=%d variant %zu (cluster=%d threads=%d lanes=%d,%d,%d) "
-                "clusters=%s: %.3f ms\n",
-                b.lat.nx, b.lat.ny, b.lat.nz, c->prec, k, v[k]->cs, v[k]->bt, v[k]->tx, v[k]->ty, v[k]->tz,
-                ncl ? std::to_string(ncl).c_str() : "per-state", ms);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = int(k);
-        best_ncl = ncl;
+      for (int stage = 0; stage < 2; ++stage) {  // predictor stage, corrector stage
+        const int m = stage ? int(MODE_Y) : x_mode(b);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+          CUDA_TRY(c, v[k]->launch[m](&a, int(nt), ncl, c->stream));
+          CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+          CUDA_TRY(c, cudaEventSynchronize(e1));
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0) ms = std::min(ms, t);
+        }
+        if (getenv("WSLDA_TUNE_VERBOSE"))
+          fprintf(stderr,
+                  "[wslda autotune] %dx%dx%d prec=%d %s variant %zu (cluster=%d threads=%d lanes=%d,%d,%d) "
+                  "clusters=%s: %.3f ms\n",
+                  b.lat.nx, b.lat.ny, b.lat.nz, c->prec, stage ? "stage Y" : "stage X", k, v[k]->cs, v[k]->bt,
+                  v[k]->tx, v[k]->ty, v[k]->tz, ncl ? std::to_string(ncl).c_str() : "per-state", ms);
+        if (ms < best_ms[stage]) {
+          best_ms[stage] = ms;
+          best[stage] = int(k);
+          best_ncl[stage] = ncl;
+        }
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b.ks = v[best];
-  b.ncl = best_ncl;
-  cache.push_back({key, {best, best_ncl}});
+  b.ks = v[best[0]];
+  b.ncl = best_ncl[0];
+  b.ks_y = v[best[1]];
+  b.ncl_y = best_ncl[1];
+  cache.push_back({key, {best[0], best_ncl[0], best[1], best_ncl[1]}});
   return WSLDA_OK;
 }
 
@@ -1283,9 +1297,12 @@ wslda_status wslda_get_variant(wslda_ctx* c, int box, char* desc, int len) {
   CHECK_CTX(c);
   Box* b = get_box(c, box);
   if (!b || !desc || len <= 0) return fail(c, WSLDA_EINVAL, "get_variant: bad arguments");
+  const KernelSet* y = b->ks_y ? b->ks_y : b->ks;
   snprintf(desc, size_t(len),
-           "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu persistent_clusters=%d", b->ks->cs,
-           b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem, b->ncl);
+           "cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d smem=%zu persistent_clusters=%d; "
+           "stage Y: cluster=%d threads=%d lanes_per_pencil=%d,%d,%d ctas_per_sm=%d persistent_clusters=%d",
+           b->ks->cs, b->ks->bt, b->ks->tx, b->ks->ty, b->ks->tz, b->ks->minb, b->ks->smem, b->ncl, y->cs, y->bt,
+           y->tx, y->ty, y->tz, y->minb, b->ks_y ? b->ncl_y : b->ncl);
   return WSLDA_OK;
 }
 
@@ -1370,7 +1387,7 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   FILE* f = fopen(path, "wb");
   if (!f) return fail(c, WSLDA_EINVAL, std::string("save: cannot open ") + path);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '3'};
+  const char magic[8] = {'W', 'S', 'L', 'D', 'A', 'T', 'D', '4'};
   int32_t hdr[3] = {c->prec, int32_t(c->boxes.size()), c->started ? 1 : 0};
   fwrite(magic, 1, 8, f);
   fwrite(hdr, sizeof(hdr), 1, f);
@@ -1387,8 +1404,11 @@ wslda_status wslda_save(wslda_ctx* c, const char* path) {
   for (Box& b : c->boxes) {
     // the launch variant travels with the state, so that a resumed run uses the
     // same kernels (different variants round differently)
-    int64_t bh[18] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.D, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3], b.ih[4],
-                      b.ks->cs, b.ks->bt, b.ks->tx, b.ks->ty, b.ks->tz, b.ks->minb, b.ncl > 0 ? 1 : 0};
+    const KernelSet* ky = b.ks_y ? b.ks_y : b.ks;
+    const int ny = b.ks_y ? b.ncl_y : b.ncl;
+    int64_t bh[25] = {b.lat.nx, b.lat.ny, b.lat.nz, b.n, b.D, b.iphi, b.ih[0], b.ih[1], b.ih[2], b.ih[3], b.ih[4],
+                      b.ks->cs, b.ks->bt, b.ks->tx, b.ks->ty, b.ks->tz, b.ks->minb, b.ncl > 0 ? 1 : 0,
+                      ky->cs, ky->bt, ky->tx, ky->ty, ky->tz, ky->minb, ny > 0 ? 1 : 0};
     fwrite(bh, sizeof(bh), 1, f);
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
     for (int i = 0; i < b.D + 2 && ok; ++i) ok = dump(b.slot[i], sb) && dump(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
@@ -1409,7 +1429,7 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
   int32_t hdr[3];
   double t, dts;
   int64_t steps;
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD3", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "WSLDATD4", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
             fread(&t, 8, 1, f) == 1 && fread(&steps, 8, 1, f) == 1 && fread(&dts, 8, 1, f) == 1;
   if (!ok || hdr[0] != c->prec || hdr[1] != int32_t(c->boxes.size())) {
     fclose(f);
@@ -1422,19 +1442,23 @@ wslda_status wslda_load(wslda_ctx* c, const char* path) {
     return cudaMemcpy(d, host.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   for (Box& b : c->boxes) {
-    int64_t bh[18];
+    int64_t bh[25];
     ok = ok && fread(bh, sizeof(bh), 1, f) == 1 && bh[0] == b.lat.nx && bh[1] == b.lat.ny && bh[2] == b.lat.nz &&
          bh[3] == b.n && bh[4] == b.D;
     if (!ok) break;
     b.iphi = int(bh[5]);
     for (int i = 0; i < 5; ++i) b.ih[i] = int(bh[6 + i]);
-    for (const KernelSet& k : registry())
-      if (k.prec == (c->prec == WSLDA_MIXED ? 1 : 0) && k.nx == b.lat.nx && k.ny == b.lat.ny && k.nz == b.lat.nz &&
-          k.cs == bh[11] && k.bt == bh[12] && k.tx == bh[13] && k.ty == bh[14] && k.tz == bh[15] && k.minb == bh[16]) {
-        b.ks = &k;
-        b.ncl = bh[17] ? resident_clusters(&k) : 0;
-        break;
-      }
+    for (int stage = 0; stage < 2; ++stage) {
+      const int64_t* id = bh + 11 + 7 * stage;
+      for (const KernelSet& k : registry())
+        if (k.prec == (c->prec == WSLDA_MIXED ? 1 : 0) && k.nx == b.lat.nx && k.ny == b.lat.ny &&
+            k.nz == b.lat.nz && k.cs == id[0] && k.bt == id[1] && k.tx == id[2] && k.ty == id[3] && k.tz == id[4] &&
+            k.minb == id[5]) {
+          (stage ? b.ks_y : b.ks) = &k;
+          (stage ? b.ncl_y : b.ncl) = id[6] ? resident_clusters(&k) : 0;
+          break;
+        }
+    }
     const size_t sb = size_t(b.n) * 2 * b.M * b.csize;
     for (int i = 0; i < b.D + 2 && ok; ++i) ok = slurp(b.slot[i], sb) && slurp(b.sc[i], std::max<int64_t>(b.n, 1) * 8);
     ok = ok && slurp(b.lam, size_t(b.M) * 8) && slurp(b.vext, size_t(b.M) * 8) && slurp(b.dext, size_t(b.M) * 16) &&
