@@ -99,6 +99,9 @@ const char* wslda_last_error(const wslda_ctx* ctx);
 
 /* 1 if kernels for this lattice shape and precision are compiled in. */
 int wslda_lattice_supported(int precision, int nx, int ny, int nz);
+/* Number of compiled launch variants for the shape (0 if unsupported); the
+ * environment variable WSLDA_VARIANT=<index> forces one of them. */
+int wslda_lattice_variants(int precision, int nx, int ny, int nz);
 
 /* Predictor-corrector scheme of the boxes added afterwards (Sec. 3.3):
  * AB4AM5 (default, Alg. 2, five state buffers), AB3AM4 (four buffers,

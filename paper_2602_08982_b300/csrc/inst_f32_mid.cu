@@ -2,4 +2,6 @@
 #include "internal.cuh"
 WSLDA_INSTANCE(float, 18, 18, 18, 1, 224, 1, 1, 1)
 WSLDA_INSTANCE(float, 20, 20, 20, 2, 416, 1, 1, 1)
+WSLDA_INSTANCE(float, 20, 20, 20, 2, 256, 1, 1, 1, 2)
 WSLDA_INSTANCE(float, 24, 24, 24, 2, 288, 1, 1, 1)
+WSLDA_INSTANCE(float, 24, 24, 24, 3, 256, 1, 1, 1, 2)

@@ -74,6 +74,7 @@ def _load():
         "wslda_destroy": (None, [P]),
         "wslda_last_error": (ct.c_char_p, [P]),
         "wslda_lattice_supported": (I, [I, I, I, I]),
+        "wslda_lattice_variants": (I, [I, I, I, I]),
         "wslda_add_box": (I, [P, ct.POINTER(Lattice), ct.POINTER(Functional), I64]),
         "wslda_set_vext": (I, [P, I, P, I]),
         "wslda_set_dext": (I, [P, I, P, I]),
@@ -125,6 +126,10 @@ lib = _load()
 
 def lattice_supported(precision: int, nx: int, ny: int, nz: int) -> bool:
     return bool(lib.wslda_lattice_supported(precision, nx, ny, nz))
+
+
+def lattice_variants(precision: int, nx: int, ny: int, nz: int) -> int:
+    return int(lib.wslda_lattice_variants(precision, nx, ny, nz))
 
 
 def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4pi_a=0.0, ec=-1.0,
