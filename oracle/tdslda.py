@@ -343,6 +343,38 @@ AM4 = np.array([9.0, 19.0, -5.0, 1.0]) / 24.0                     # Eq. AM4
 
 
 @dataclass
+class Friction:
+    """Dissipative ("quantum friction") terms of Sec. 5.2.4 for the
+    spin-symmetric system (Eqs. cooling_alpha, Deltadiss2):
+      U_diss = -(alpha / rho0) div j_sigma,
+      Delta_diss = Delta [beta sin(theta_nu - theta_B') + i gamma (N - N_req) / N_req],
+      theta_B' = arg[-1/2 sum_n (u_n lap v_n^* + v_n^* lap u_n)],  theta_nu = arg nu.
+    Reading Q1: div j_sigma is evaluated as sum_n [w-_n Im(v_n lap v_n^*)
+    - w+_n Im(u_n lap u_n^*)] (the divergence of j by the product rule, the
+    |grad v|^2 term being real), with the spectral Laplacian of H.
+    Reading Q2: the sum in theta_B' carries the weights of nu, w-_n - w+_n.
+    Reading Q3: rho0 (not defined in the text) is a parameter; N counts both
+    spin species, N = int (rho_a + rho_b)."""
+    alpha: float = 0.0
+    beta: float = 0.0
+    gamma: float = 0.0
+    rho0: float = 1.0 / (6.0 * math.pi ** 2)
+    n_req: float = 1.0
+
+    def fields(self, phi, wm, wp, rho_sigma, nu, delta, lat: "Lattice"):
+        u, v = phi[:, 0, :], phi[:, 1, :]
+        lu, lv = laplacian(u, lat), laplacian(v, lat)
+        div_j = (np.einsum("n,nr->r", wm, np.imag(v * np.conj(lv)))
+                 - np.einsum("n,nr->r", wp, np.imag(u * np.conj(lu))))
+        bp = -0.5 * np.einsum("n,nr->r", wm - wp, u * np.conj(lv) + np.conj(v) * lu)
+        dU = -(self.alpha / self.rho0) * div_j
+        n_tot = lat.dV * np.sum(2.0 * rho_sigma)
+        g = self.gamma * (n_tot - self.n_req) / self.n_req
+        dD = delta * (self.beta * np.sin(np.angle(nu) - np.angle(bp)) + 1j * g)
+        return dU, dD
+
+
+@dataclass
 class TDSystem:
     lat: Lattice
     fn: Functional
@@ -352,6 +384,7 @@ class TDSystem:
     w_plus: np.ndarray | None = None     # [n] frozen thermal weights f(E_n)
     lam: np.ndarray | None = None        # frozen regulator (reading R2)
     freeze_fields: Fields | None = None  # testing aid: H held fixed
+    friction: "Friction | None" = None   # dissipative terms (Sec. 5.2.4)
 
     def weights(self, n):
         wm = np.ones(n) if self.w_minus is None else self.w_minus
@@ -373,7 +406,12 @@ class TDSystem:
         """Densities of all states -> potentials -> (W, D) (Alg. 1 steps 3-4)."""
         if self.freeze_fields is not None:
             return self.freeze_fields
-        _, _, U, delta, _ = self.potentials(phi)
+        rho, nu, U, delta, _ = self.potentials(phi)
+        if self.friction is not None:
+            wm, wp = self.weights(phi.shape[0])
+            dU, dD = self.friction.fields(phi, wm, wp, rho, nu, delta, self.lat)
+            U = U + dU
+            delta = delta + dD
         D = delta if self.dext is None else delta + self.dext
         return Fields(W=U + self.vext - self.fn.mu, D=D)
 
