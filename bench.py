@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--scf-n", type=float, default=200.0, help="particle-number target per spin for --init scf")
     p.add_argument("--scf-iters", type=int, default=40)
     p.add_argument("--scf-fp32-iters", type=int, default=30)
+    p.add_argument("--friction", default=None,
+                   help="alpha,beta,gamma of the quantum-friction terms (Sec. 5.2.4), e.g. 5,5,0")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -222,6 +224,10 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     else:
         ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
         ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+        if args.friction:
+            fa, fb, fg = (float(x) for x in args.friction.split(","))
+            M = shape[0] * shape[1] * shape[2]
+            ctx.set_friction(box, fa, fb, fg, RHO_SIGMA, 2.0 * RHO_SIGMA * M)
         ctx.start(args.stationary, args.dt)  # Taylor start: the trapped plane waves are not stationary
     variant = ctx.get_variant(box)
     if args.warmup:
@@ -464,7 +470,7 @@ def workload_config(args, shape, precision):
             "init": ("states of a static self-consistent solve (fixed N, Broyden), stationary start"
                      if args.init == "scf" else
                      "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start"),
-            "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
+            "friction": args.friction, "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 

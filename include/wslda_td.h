@@ -123,6 +123,22 @@ int wslda_add_box(wslda_ctx* ctx, const wslda_lattice* lat, const wslda_function
 wslda_status wslda_set_vext(wslda_ctx* ctx, int box, const double* vext, int on_device);
 wslda_status wslda_set_dext(wslda_ctx* ctx, int box, const double* dext, int on_device);
 
+/* Dissipative ("quantum friction") terms of Sec. 5.2.4 for one box, added to
+ * the fields of H at every evaluation (also during the start-up):
+ *   U_diss = -(alpha / rho0) div j_sigma,
+ *   Delta_diss = Delta [beta sin(arg nu - arg B') + i gamma (N - n_req) / n_req],
+ *   B' = -1/2 sum_n (w-_n - w+_n) (u_n lap v_n^* + v_n^* lap u_n),
+ * with div j_sigma = sum_n [w-_n Im(v_n lap v_n^*) - w+_n Im(u_n lap u_n^*)]
+ * (the product rule, with the Laplacian of H), N = int (rho_a + rho_b), and
+ * Delta the mean-field pairing (without Delta_ext). The energy diagnostics
+ * keep the conservative functional. Each evaluation adds one transform pass
+ * over the states and a state-sized scratch buffer, allocated on the first
+ * call (WSLDA_ENOMEM when it does not fit). All coefficients 0 switch the
+ * terms off. rho0, n_req > 0. May be called at any time (captured graphs are
+ * dropped). */
+wslda_status wslda_set_friction(wslda_ctx* ctx, int box, double alpha, double beta, double gamma, double rho0,
+                                double n_req);
+
 /* Load states [n][2][M] complex. w_minus / w_plus are the frozen weights
  * f_beta(-E_n), f_beta(E_n) (Sec. 2.5) as [n] host doubles, or NULL for T = 0
  * (w_minus = 1, w_plus = 0). The mixed path rounds the states to complex float.

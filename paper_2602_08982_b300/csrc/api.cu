@@ -64,6 +64,11 @@ struct Box {
   double* ekin2 = nullptr;
   double* out8 = nullptr;
   double e0 = 0.0, n0 = 0.0;  // E_tot - mu N and N of the states at wslda_start
+  // quantum friction (Sec. 5.2.4): coefficients, scratch state buffer, fields
+  bool fric = false;
+  double f_alpha = 0.0, f_beta = 0.0, f_gamma = 0.0, f_rho0 = 1.0, f_nreq = 1.0;
+  void* f_scratch = nullptr;
+  double *f_div = nullptr, *f_bp = nullptr;
   bool loaded = false;
   void* ptr(int i) const { return slot[i]; }
 };
@@ -314,10 +319,30 @@ wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   } else {
     CUDA_TRY(c, cudaMemsetAsync(b.part, 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->cur));
   }
-  ProfScope ps2(c, PROF_POT);
-  c->launches += 1;
-  CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu, b.U,
-                                   b.delta, static_cast<fx4<R>*>(b.WD), c->cur));
+  {
+    ProfScope ps2(c, PROF_POT);
+    c->launches += 1;
+    CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu,
+                                     b.U, b.delta, static_cast<fx4<R>*>(b.WD), c->cur));
+  }
+  if (b.fric && b.n > 0) {
+    // per-state friction contributions (one transform pass), summed over
+    // states, then added to the H fields
+    StageArgs<R> a = base_args<R>(b, box_dV(b));
+    a.phi = static_cast<cx<R>*>(b.ptr(islot));
+    a.h0 = static_cast<cx<R>*>(b.f_scratch);
+    a.sc_in = b.sc[islot];
+    a.wm = b.wm;
+    a.wp = b.wp;
+    wslda_status st = launch_mode<R>(c, b, MODE_LAP, a, PROF_POT);
+    if (st) return st;
+    ProfScope ps3(c, PROF_POT);
+    c->launches += 3;
+    CUDA_TRY(c, launch_sum_tauj<R>(static_cast<const cx<R>*>(b.f_scratch), b.n, b.M, b.nchunk, b.chunk, b.part,
+                                   b.f_div, b.f_bp, c->cur));
+    CUDA_TRY(c, launch_apply_friction<R>(b.M, box_dV(b), b.f_alpha, b.f_beta, b.f_gamma, b.f_rho0, b.f_nreq, b.rho,
+                                         b.nu, b.delta, b.f_div, b.f_bp, static_cast<fx4<R>*>(b.WD), c->cur));
+  }
   return WSLDA_OK;
 }
 
@@ -735,6 +760,42 @@ void wslda_destroy(wslda_ctx* c) {
 const char* wslda_last_error(const wslda_ctx* c) {
   if (!c) return "null context";
   return c->err.empty() ? "" : c->err.c_str();
+}
+
+wslda_status wslda_set_friction(wslda_ctx* c, int box, double alpha, double beta, double gamma, double rho0,
+                                double n_req) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "set_friction: bad box");
+  if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma) || !(rho0 > 0.0) ||
+      !(n_req > 0.0) || !std::isfinite(rho0) || !std::isfinite(n_req))
+    return fail(c, WSLDA_EINVAL, "set_friction: coefficients must be finite, rho0 and n_req > 0");
+  if (!b->f_scratch && b->n > 0) {
+    const size_t sb = size_t(b->n) * 2 * b->M * b->csize;
+    size_t freeb = 0, totalb = 0;
+    CUDA_TRY(c, cudaMemGetInfo(&freeb, &totalb));
+    if (sb + size_t(b->M) * 32 + (size_t(64) << 20) > freeb)
+      return fail(c, WSLDA_ENOMEM, "set_friction: no room for the scratch state buffer");
+    void* p = nullptr;
+    CUDA_TRY(c, cudaMalloc(&p, sb));
+    c->allocs.push_back(p);
+    b->f_scratch = p;
+    CUDA_TRY(c, cudaMalloc(&p, size_t(b->M) * 8));
+    c->allocs.push_back(p);
+    b->f_div = static_cast<double*>(p);
+    CUDA_TRY(c, cudaMalloc(&p, size_t(b->M) * 24));
+    c->allocs.push_back(p);
+    b->f_bp = static_cast<double*>(p);
+  }
+  b->fric = alpha != 0.0 || beta != 0.0 || gamma != 0.0;
+  b->f_alpha = alpha;
+  b->f_beta = beta;
+  b->f_gamma = gamma;
+  b->f_rho0 = rho0;
+  b->f_nreq = n_req;
+  drop_graphs(c);  // captured steps hold the old field pipeline
+  if (c->started && b->loaded) return refresh_fields(c, *b, b->iphi, 0);
+  return WSLDA_OK;
 }
 
 wslda_status wslda_set_integrator(wslda_ctx* c, int scheme) {

@@ -263,6 +263,53 @@ cudaError_t launch_finalize_norm(const double* npart, int cs, int64_t n, double 
 }
 
 // ---------------------------------------------------------------------------
+// Quantum friction (Sec. 5.2.4) on the H fields. bp3 holds the sums of the
+// per-state friction contributions as [3][M]: [1] = Re B', [2] = Im B'.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(1024) apply_friction_kernel(int M, double dV, double alpha, double beta,
+                                                              double gamma, double rho0, double n_req,
+                                                              const double* rho, const double* nu,
+                                                              const double* delta, const double* divj,
+                                                              const double* bp3, fx4<R>* WD) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < M; s += blockDim.x) acc += 2.0 * rho[s];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double N = 0.0;
+  for (int i = 0; i < int(blockDim.x >> 5); ++i) N += red[i];
+  N *= dV;
+  const double gt = gamma * (N - n_req) / n_req;
+  for (int s = threadIdx.x; s < M; s += blockDim.x) {
+    const double dU = -(alpha / rho0) * divj[s];
+    const double th = atan2(nu[2 * s + 1], nu[2 * s]) - atan2(bp3[2 * M + s], bp3[M + s]);
+    const double f = beta * sin(th);
+    const double dr = delta[2 * s], di = delta[2 * s + 1];
+    fx4<R> w = WD[s];
+    w.x = R(double(w.x) + dU);
+    w.y = R(double(w.y) + (f * dr - gt * di));  // Delta (f + i gt)
+    w.z = R(double(w.z) + (f * di + gt * dr));
+    WD[s] = w;
+  }
+}
+
+template <typename R>
+cudaError_t launch_apply_friction(int M, double dV, double alpha, double beta, double gamma, double rho0,
+                                  double n_req, const double* rho, const double* nu, const double* delta,
+                                  const double* divj, const double* bp3, fx4<R>* WD, cudaStream_t s) {
+  apply_friction_kernel<R><<<1, 1024, 0, s>>>(M, dV, alpha, beta, gamma, rho0, n_req, rho, nu, delta, divj, bp3, WD);
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply_friction<float>(int, double, double, double, double, double, double, const double*,
+                                                  const double*, const double*, const double*, const double*,
+                                                  float4*, cudaStream_t);
+template cudaError_t launch_apply_friction<double>(int, double, double, double, double, double, double,
+                                                   const double*, const double*, const double*, const double*,
+                                                   const double*, double4*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Energy (Sec. 3.2, A = 1): one block, fixed-order tree sums in double.
 // out8 = e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part.
 // ---------------------------------------------------------------------------

@@ -82,6 +82,7 @@ KernelSet make_set() {
   k.launch[MODE_GRAD] = launch_stage<G, MODE_GRAD>;
   k.launch[MODE_X3] = launch_stage<G, MODE_X3>;
   k.launch[MODE_X5] = launch_stage<G, MODE_X5>;
+  k.launch[MODE_LAP] = launch_stage<G, MODE_LAP>;
   k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X, false>;
   k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y, false>;
   k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F, false>;
@@ -90,6 +91,7 @@ KernelSet make_set() {
   k.fn[MODE_GRAD] = (const void*)stage_kernel<G, MODE_GRAD, false>;
   k.fn[MODE_X3] = (const void*)stage_kernel<G, MODE_X3, false>;
   k.fn[MODE_X5] = (const void*)stage_kernel<G, MODE_X5, false>;
+  k.fn[MODE_LAP] = (const void*)stage_kernel<G, MODE_LAP, false>;
   return k;
 }
 
@@ -114,6 +116,14 @@ struct FunctionalDev {
 template <typename R>
 cudaError_t launch_density_partial(const cx<R>* phi, const double* sc, const R* wm, const R* wp, int64_t nstates,
                                    int M, int nchunk, int64_t chunk, double* part, cudaStream_t s);
+
+// Quantum friction (Sec. 5.2.4) added to the H fields in place:
+// W += -(alpha / rho0) div_j,  D += Delta [beta sin(arg nu - arg B') + i gamma (N - N_req) / N_req],
+// N = dV sum 2 rho_sigma (one CTA: the sum, then the update).
+template <typename R>
+cudaError_t launch_apply_friction(int M, double dV, double alpha, double beta, double gamma, double rho0,
+                                  double n_req, const double* rho, const double* nu, const double* delta,
+                                  const double* divj, const double* bp3, fx4<R>* WD, cudaStream_t s);
 
 // Number of state chunks of the density reduction for M sites and n states.
 int density_chunks(int M, int64_t nstates, int is_float);

@@ -21,6 +21,10 @@
 //            Taylor series of Eq. Taylor-exp); E_n = <in|H|in> is computed and
 //            stored when requested, else read; optional normalisation.
 //   MODE_EKIN    per-state <u|T|u>, <v|T|v> for the kinetic energy.
+//   MODE_LAP     per-state contributions to the quantum-friction fields
+//            (Sec. 5.2.4): w- Im(v lap v^*) - w+ Im(u lap u^*) (the divergence
+//            of j by the product rule) and -(w- - w+)/2 (u lap v^* + v^* lap u)
+//            (the sum in theta_B'), stored in h0 as [n][2][M] complex.
 //   MODE_GRAD    one Cartesian derivative d_dir (symbol i k_dir, Nyquist mode
 //            zeroed) of u and v, and the per-state weighted contributions to
 //            tau and j_dir (Eqs. nab3D..jab3D), accumulated into h0.
@@ -49,7 +53,7 @@ template <typename R> using fx4 = typename fx4_of<R>::type;
 // MODE_X3 / MODE_X5: the predictor stage of AB3AM4 / AB5AM5 (MODE_X is AB4AM5's).
 enum Mode : int {
   MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, MODE_X3 = 6, MODE_X5 = 7,
-  NMODES = 8
+  MODE_LAP = 8, NMODES = 9
 };
 
 template <typename R>
@@ -448,6 +452,21 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
 
   if constexpr (MODE == MODE_EKIN) {
     if (rank == 0 && tid == 0) { a.out2[2 * n] = En; a.out2[2 * n + 1] = Ev; }
+    return;
+  } else if constexpr (MODE == MODE_LAP) {
+    // buf holds T phi = -1/2 lap phi: lap = -2 T
+    const R wmn = R(a.wm[n]), wpn = R(a.wp[n]), dw = wmn - wpn;
+    C* out = a.h0 + sbase;
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const int g = gs0 + s;
+      const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
+      const C lu = scl(buf[sidx(s)], R(-2) * sin_), lv = scl(buf[G::SLAB + sidx(s)], R(-2) * sin_);
+      const C vlv = mulc(vv, lv), ulu = mulc(uu, lu);  // v conj(lap v), u conj(lap u)
+      const R divj = wmn * vlv.y - wpn * ulu.y;
+      const C bp = scl(add(mulc(uu, lv), mulc(lu, vv)), R(-0.5) * dw);  // u conj(lap v) + conj(v) lap u
+      out[g] = mk<C>(divj, R(0));
+      out[G::M + g] = bp;
+    }
     return;
   } else if constexpr (MODE == MODE_GRAD) {
     // buf holds d_dir u, d_dir v. Per site: tau_dir = w-|dv|^2 + w+|du|^2,

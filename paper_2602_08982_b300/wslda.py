@@ -100,6 +100,7 @@ def _load():
         "wslda_check_conservation": (I, [P, I, D, D, DP, DP]),
         "wslda_densities_noalloc": (I, [I, P, P, P, I64, I, I, I, P, P, P]),
         "wslda_set_integrator": (I, [P, I]),
+        "wslda_set_friction": (I, [P, I, D, D, D, D, D]),
         "wslda_load_states_f32": (I, [P, I, P, P, P, I]),
         "wslda_get_states_f32": (I, [P, I, P, I]),
         "wslda_net_create": (I, [I, I, I, I, I, ct.POINTER(P)]),
@@ -204,6 +205,11 @@ class Context:
         self.close()
 
     # ------------------------------------------------------------------ ABI
+    def set_friction(self, box: int, alpha=0.0, beta=0.0, gamma=0.0, rho0=1.0 / (6.0 * np.pi ** 2), n_req=1.0):
+        """Quantum-friction terms (Sec. 5.2.4) for one box."""
+        self._check(lib.wslda_set_friction(self._h, box, float(alpha), float(beta), float(gamma), float(rho0),
+                                           float(n_req)))
+
     def set_integrator(self, scheme: str):
         """'AB4AM5' (default), 'AB3AM4' or 'AB5AM5' for boxes added afterwards."""
         self._check(lib.wslda_set_integrator(self._h, SCHEMES[scheme]))
