@@ -1,6 +1,7 @@
 """Every compiled launch variant (cluster size, threads, register budget) of
-the mixed-precision lattices the workloads use, forced one at a time, against
-the oracle on a sample of states (Taylor start and two ABM steps)."""
+the lattices the workloads use (mixed precision, and FP64 at 32^3), in both
+launch forms, forced one at a time, against the oracle on a sample of states
+(Taylor start and two ABM steps)."""
 import functools
 
 import numpy as np
@@ -25,23 +26,32 @@ def _reference(shape):
 def _cases():
     from paper_2602_08982_b300 import wslda as W
     out = []
-    for s in SHAPES:
-        for v in range(W.lattice_variants(W.MIXED, *s)):
-            for p in (0, 1):
-                out.append((s, v, p))
+    for prec, shapes in ((W.MIXED, SHAPES), (W.FP64, [(32, 32, 32)])):
+        for s in shapes:
+            for v in range(W.lattice_variants(prec, *s)):
+                for p in (0, 1):
+                    out.append((prec, s, v, p))
     return out
 
 
-@pytest.mark.parametrize("shape,variant,persist", _cases())
-def test_variant_matches_oracle(shape, variant, persist, monkeypatch):
+@functools.lru_cache(maxsize=None)
+def _reference64(shape):
+    c = make_case(shape, nstates=40, kick=0.05, trap=0.06, seed=81 + shape[0])
+    _, st = oracle_evolve(c, 0.01, 5, False)
+    return c, o.densities(st.phi, c.wm, c.wp)
+
+
+@pytest.mark.parametrize("prec,shape,variant,persist", _cases())
+def test_variant_matches_oracle(prec, shape, variant, persist, monkeypatch):
     from paper_2602_08982_b300 import wslda as W
-    c, (r, n) = _reference(shape)
+    c, (r, n) = _reference(shape) if prec == W.MIXED else _reference64(shape)
+    tol = 1e-5 if prec == W.MIXED else 1e-12
     monkeypatch.setenv("WSLDA_VARIANT", str(variant))
     monkeypatch.setenv("WSLDA_PERSIST", str(persist))
-    ctx, box = gpu_context(c, W.MIXED)
+    ctx, box = gpu_context(c, prec)
     ctx.start(False, 0.01)
     ctx.step(0.01, 2)
     desc = ctx.get_variant(box)
     rho, nu = ctx.get_densities(box)
     ctx.close()
-    assert rel(rho, r) < 1e-5 and rel(nu, n) < 1e-5, desc
+    assert rel(rho, r) < tol and rel(nu, n) < tol, desc
