@@ -1,13 +1,17 @@
 // Host runtime of the C ABI declared in include/wslda_td.h.
 //
-// A context owns boxes; a box owns five state buffers (phi and four ABM
-// history slots of Alg. 2), the site fields and the chunked density partials.
-// The AB4AM5 step is four launches per box on the context's stream:
-//   stage X (f, predictor, corrector partial, normalise)   -> phi_p, c, f_{k-1}
-//   densities(phi_p) + potentials                          -> W, D
-//   stage Y (f(phi_p), corrector completion, normalise)    -> phi_k
-//   densities(phi_k) + potentials                          -> W, D
+// A context owns boxes; a box owns D + 2 state buffers (phi, the slot for the
+// next f_{k-1} and D history values: five for AB4AM5, Alg. 2), the site
+// fields and the chunked density partials. A step is, per box, on the
+// context's stream (or a forked one when boxes are batched):
+//   stage X (f, predictor, corrector partial) + norm finalise -> phi_p, c, f_{k-1}
+//   densities(phi_p) + potentials [+ friction terms]          -> W, D
+//   stage Y (f(phi_p), corrector completion) + norm finalise  -> phi_k
+//   densities(phi_k) + potentials [+ friction terms]          -> W, D
 // followed by a pointer rotation of the history slots (Alg. 2 steps 5-7).
+// The static solver (scf.cu), the uniform seed (uniform.cu), the allocation-
+// free density call (noalloc.cu) and the network kernels (convnet.cu) have
+// their own files.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
