@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--scf-fp32-iters", type=int, default=30)
     p.add_argument("--friction", default=None,
                    help="alpha,beta,gamma of the quantum-friction terms (Sec. 5.2.4), e.g. 5,5,0")
+    p.add_argument("--streams", type=int, default=4, help="forked streams of the batched workload")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -345,7 +346,7 @@ def run_batched(W, torch, args):
         ctx.set_dext(b, inputs.pairing_kick(shape, 5000 + i, 1e-3 * u["delta"]))
         ctx.fill_uniform_states(b, u["mu_eff"], u["delta"])
         units += float(n ** 3) ** 2
-    ctx.set_graph(True, 4)
+    ctx.set_graph(True, args.streams)
     ctx.start(False, args.dt)
     steps = max(4, 4 * (args.steps // 4))
     ctx.step(args.dt, 4)                      # warm-up (also captures the graphs)
@@ -366,7 +367,7 @@ def run_batched(W, torch, args):
             "gpu_launches": launches,
             "box_sides_seed": seed, "box_sides": sides, "state_sites_per_step": units,
             "config": "64 cubic boxes 12^3..24^3 (all states), BdG 1/(kF a) uniform in [-1, 1), 1e-3 pairing "
-                      "kick per box, complex64, boxes on 4 forked streams, 4 steps per CUDA graph",
+                      f"kick per box, complex64, boxes on {args.streams} forked streams, 4 steps per CUDA graph",
             "step_roofline": {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                               "frac": step_gbs / peak, "peak_source": which,
                               "algorithmic_bytes_per_state_site": 160, "scope": "whole step (10 state passes)"}}
