@@ -24,7 +24,10 @@ Parity pins: every function here is pinned by a test in tests/test_oracle_pins.p
 against closed forms, printed numbers, textbook limits, invariants or brute
 force. Partial pin: the SLDA constants used with A forced to 1 (Sec. 2.4,
 "A_sigma = 1" option) have no printed number; the functional form they enter
-is pinned through the A = 1.094 uniform solution instead.
+is pinned through the A = 1.094 uniform solution instead. The current terms of
+A != 1 (kinetic factor A, current potential, current part of U, anticommutator
+and energy) are pinned together by the Galilean covariance of the functional
+(tests/test_oracle_current.py).
 """
 from __future__ import annotations
 
@@ -210,9 +213,14 @@ def lambda_c(mu_minus_V, ec: float, A: float = 1.0):
 
 @dataclass
 class Functional:
-    """SLDA with A forced to 1 ('slda', Sec. 2.4 last paragraph) or BdG ('bdg').
+    """SLDA-type ('slda', Sec. 2.4) or BdG ('bdg').
 
-    slda: E_0 = tau_a/2 + tau_b/2 + 3/5 B rho eF(rho) + g_eff |nu|^2
+    slda: E_0 + E_CM = sum_sigma [A/2 (tau_s - j_s^2/rho_s) + j_s^2/(2 rho_s)]
+                       + 3/5 B rho eF(rho) + g_eff |nu|^2
+          (Eqs. sldae-functional-generic, -CM, sldae-functional) with a constant
+          A; A = 1 is the 'A_sigma = 1' option of Sec. 2.4 (last paragraph),
+          where the current terms cancel. The spin-symmetric ASLDA has
+          A = A_a(0) = 1.094, B = B(0), C = -11.11.
     bdg : A = 1, B = 0, coupling 4 pi a (Eq. HBdG)
     Reading R1: 1/g_eff = rho^(1/3)/C - Lambda_c (slda) or 1/(4 pi a) - Lambda_c
     (bdg); Delta = -g_eff nu (Eq. Delta)."""
@@ -223,9 +231,15 @@ class Functional:
     mu: float = 0.0
     ec: float = -1.0          # <= 0 selects lattice_cutoff() (reading R5)
     rho_floor: float = 1e-12  # Reading R4
+    A: float = 1.0            # inverse effective mass alpha = A_sigma (slda only)
 
     def cutoff(self, lat: Lattice) -> float:
         return self.ec if self.ec > 0 else lattice_cutoff(lat)
+
+    @property
+    def currents(self) -> bool:
+        """Whether the current terms are present (A != 1, Sec. 2.4)."""
+        return self.kind == "slda" and self.A != 1.0
 
 
 def inverse_coupling(rho_sigma, lam, fn: Functional):
@@ -245,29 +259,48 @@ def mean_field(rho_sigma, delta, fn: Functional):
     return np.zeros_like(np.asarray(rho_sigma, dtype=np.float64))
 
 
-def potentials(rho_sigma, nu, lam, fn: Functional):
-    """(U, Delta, g_eff) from the densities with a given regulator field."""
+def current_mean_field(rho_sigma, j, fn: Functional):
+    """The part of U = dE/d rho_sigma that the current terms add for a
+    constant A: d/d rho_s [(1 - A) j_s^2 / (2 rho_s)] = (A - 1) j_s^2 / (2 rho_s^2)
+    (reading N1: rho_s floored at rho_floor)."""
+    rs = np.maximum(rho_sigma, fn.rho_floor)
+    return (fn.A - 1.0) * np.sum(j * j, axis=0) / (2.0 * rs * rs)
+
+
+def current_potential(rho_sigma, j, fn: Functional):
+    """Current potential A_sigma = dE/d j_sigma = (1 - A) j_s / rho_s
+    (Sec. 2.2 list of potentials; reading N1 floor)."""
+    rs = np.maximum(rho_sigma, fn.rho_floor)
+    return (1.0 - fn.A) * j / rs[None, :]
+
+
+def potentials(rho_sigma, nu, lam, fn: Functional, j=None):
+    """(U, Delta, g_eff) from the densities with a given regulator field; `j`
+    (the current of one spin, [3][M]) adds the current part of U when A != 1."""
     g = 1.0 / inverse_coupling(rho_sigma, lam, fn)
     delta = -g * nu
     U = mean_field(rho_sigma, delta, fn)
+    if fn.currents and j is not None:
+        U = U + current_mean_field(rho_sigma, j, fn)
     return U, delta, g
 
 
 REGULATOR_ITERS = 60
 
 
-def frozen_regulator(rho_sigma, nu, vext, fn: Functional, lat: Lattice, iters: int = REGULATOR_ITERS):
+def frozen_regulator(rho_sigma, nu, vext, fn: Functional, lat: Lattice, iters: int = REGULATOR_ITERS, j=None):
     """Reading R2: the regulator used during time evolution is fixed at t = 0.
 
-    Lambda_c depends on V = U + V_ext, and U depends on Lambda_c through g_eff;
-    the t = 0 value is the fixed point of that loop, reached by `iters` plain
-    iterations started from U = 0 (the same count on the GPU side)."""
+    Lambda_c depends on V = U + V_ext (and on A_+ = A, Sec. 2.6), and U depends
+    on Lambda_c through g_eff; the t = 0 value is the fixed point of that loop,
+    reached by `iters` plain iterations started from U = 0 (the same count on
+    the GPU side). With A != 1, U includes the current part from `j` at t = 0."""
     ec = fn.cutoff(lat)
     U = np.zeros_like(vext)
     for _ in range(iters):
-        lam = lambda_c(fn.mu - U - vext, ec)
-        U, _, _ = potentials(rho_sigma, nu, lam, fn)
-    return lambda_c(fn.mu - U - vext, ec)
+        lam = lambda_c(fn.mu - U - vext, ec, fn.A)
+        U, _, _ = potentials(rho_sigma, nu, lam, fn, j)
+    return lambda_c(fn.mu - U - vext, ec, fn.A)
 
 
 # ----------------------------------------------------------------------------
@@ -298,17 +331,42 @@ def kinetic_current_densities(phi, w_minus, w_plus, lat: Lattice):
 # ----------------------------------------------------------------------------
 @dataclass
 class Fields:
-    """Pointwise fields defining H for A = 1 (Eq. h_sigma_A1, Eq. dpsidt-Hpsi):
-    W = U + V_ext - mu on the diagonal, D = Delta + Delta_ext off the diagonal."""
+    """Pointwise fields defining H (Eq. h_sigma, Eq. HpsiEpsi):
+    W = U + V_ext - mu on the diagonal, D = Delta + Delta_ext off the diagonal,
+    alpha the (constant) inverse effective mass, Avec [3][M] the current
+    potential and divA its spectral divergence (None: no current term, as in
+    Eq. h_sigma_A1)."""
     W: np.ndarray
     D: np.ndarray
+    alpha: float = 1.0
+    Avec: np.ndarray | None = None
+    divA: np.ndarray | None = None
+
+
+def current_term(f, F: Fields, lat: Lattice):
+    """-(i/2){A, grad} f, the current term of h_sigma (Eq. h_sigma).
+
+    Reading N2: the anticommutator is evaluated as 2 A.grad f + (div A) f with
+    spectral, Nyquist-free first derivatives of f and of A (the gradient
+    buffers Sec. 3.3 counts, with no transform of the product A f)."""
+    g = gradient(f, lat)
+    s = sum(F.Avec[d] * g[d] for d in range(3))
+    return -1j * (s + 0.5 * F.divA * f)
 
 
 def apply_H(phi, F: Fields, lat: Lattice):
-    """(H phi)_u = -1/2 lap u + W u + D v;  (H phi)_v = D^* u + 1/2 lap v - W v."""
+    """(H phi)_u = h u - mu u + D v with h = -alpha/2 lap + U + V_ext - (i/2){A, grad};
+    (H phi)_v = D^* u - h^* v + mu v  (Eqs. HpsiEpsi, h_sigma; spin-symmetric, so
+    h_a = h_b). For a constant alpha, -1/2 grad.alpha grad = -alpha/2 lap
+    (Eq. kinop-alpha with a constant alpha). h^* has the current term with the
+    opposite sign, so -h^* v carries -(i/2){A, grad} v, the same term as h u."""
     u, v = phi[:, 0, :], phi[:, 1, :]
-    Hu = -0.5 * laplacian(u, lat) + F.W * u + F.D * v
-    Hv = np.conj(F.D) * u + 0.5 * laplacian(v, lat) - F.W * v
+    a = F.alpha
+    Hu = -0.5 * a * laplacian(u, lat) + F.W * u + F.D * v
+    Hv = np.conj(F.D) * u + 0.5 * a * laplacian(v, lat) - F.W * v
+    if F.Avec is not None:
+        Hu = Hu + current_term(u, F, lat)
+        Hv = Hv + current_term(v, F, lat)
     return np.stack([Hu, Hv], axis=1)
 
 
@@ -391,53 +449,73 @@ class TDSystem:
         wp = np.zeros(n) if self.w_plus is None else self.w_plus
         return wm, wp
 
+    def current(self, phi):
+        """j_sigma (Eq. jab3D) when the functional has current terms, else None."""
+        if not self.fn.currents:
+            return None
+        wm, wp = self.weights(phi.shape[0])
+        return kinetic_current_densities(phi, wm, wp, self.lat)[1]
+
     def init_regulator(self, phi):
         wm, wp = self.weights(phi.shape[0])
         rho, nu = densities(phi, wm, wp)
-        self.lam = frozen_regulator(rho, nu, self.vext, self.fn, self.lat)
+        self.lam = frozen_regulator(rho, nu, self.vext, self.fn, self.lat, j=self.current(phi))
 
-    def potentials(self, phi):
+    def potentials(self, phi, j=None):
         wm, wp = self.weights(phi.shape[0])
         rho, nu = densities(phi, wm, wp)
-        U, delta, g = potentials(rho, nu, self.lam, self.fn)
+        U, delta, g = potentials(rho, nu, self.lam, self.fn, j)
         return rho, nu, U, delta, g
 
     def fields(self, phi) -> Fields:
-        """Densities of all states -> potentials -> (W, D) (Alg. 1 steps 3-4)."""
+        """Densities of all states -> potentials -> (W, D) and, for A != 1, the
+        current potential and its divergence (Alg. 1 steps 3-4)."""
         if self.freeze_fields is not None:
             return self.freeze_fields
-        rho, nu, U, delta, _ = self.potentials(phi)
+        j = self.current(phi)
+        rho, nu, U, delta, _ = self.potentials(phi, j)
         if self.friction is not None:
             wm, wp = self.weights(phi.shape[0])
             dU, dD = self.friction.fields(phi, wm, wp, rho, nu, delta, self.lat)
             U = U + dU
             delta = delta + dD
         D = delta if self.dext is None else delta + self.dext
-        return Fields(W=U + self.vext - self.fn.mu, D=D)
+        if j is None:
+            return Fields(W=U + self.vext - self.fn.mu, D=D)
+        Avec = current_potential(rho, j, self.fn)
+        divA = np.real(sum(gradient(Avec[d], self.lat)[d] for d in range(3)))
+        return Fields(W=U + self.vext - self.fn.mu, D=D, alpha=self.fn.A, Avec=Avec, divA=divA)
 
     def f(self, phi):
         return rhs_f(phi, self.fields(phi), self.lat)
 
     def energy(self, phi) -> dict:
-        """Energy terms of Sec. 3.2 for A = 1 (reading E1: the kinetic term uses
-        the same Laplacian as H, via sum_n w <v|-lap|v>). The quantity the
-        evolution conserves is e_total - mu * n_part (Eq. E_tot)."""
+        """Energy terms of Sec. 3.2 (reading E1: the kinetic term uses the same
+        Laplacian as H, via sum_n w <v|-lap|v>, times A). With A != 1 the
+        current terms add e_cur = int sum_s (1 - A) j_s^2 / (2 rho_s). The
+        quantity the evolution conserves is e_total - mu * n_part (Eq. E_tot)."""
         lat, fn = self.lat, self.fn
         wm, wp = self.weights(phi.shape[0])
-        rho_s, nu, U, delta, g = self.potentials(phi)
+        j = self.current(phi)
+        rho_s, nu, U, delta, g = self.potentials(phi, j)
         u, v = phi[:, 0, :], phi[:, 1, :]
         lu, lv = laplacian(u, lat), laplacian(v, lat)
-        e_kin = lat.dV * (np.einsum("n,nr->", wm, -np.conj(v) * lv).real
-                          + np.einsum("n,nr->", wp, -np.conj(u) * lu).real)
+        a = fn.A if fn.kind == "slda" else 1.0
+        e_kin = a * lat.dV * (np.einsum("n,nr->", wm, -np.conj(v) * lv).real
+                              + np.einsum("n,nr->", wp, -np.conj(u) * lu).real)
+        e_cur = 0.0
+        if j is not None:
+            rs = np.maximum(rho_s, fn.rho_floor)
+            e_cur = lat.dV * np.sum((1.0 - fn.A) * np.sum(j * j, axis=0) / rs)
         rho = 2.0 * rho_s
         e_pot = lat.dV * np.sum(0.6 * fn.B * rho * fermi_energy(rho)) if fn.kind == "slda" else 0.0
         e_pair = -lat.dV * np.sum(np.real(np.conj(delta) * nu))
         e_ext = lat.dV * np.sum(self.vext * rho)
         e_pext = 0.0 if self.dext is None else -lat.dV * np.sum(2.0 * np.real(self.dext * np.conj(nu)))
         n_part = lat.dV * np.sum(rho)
-        tot = e_kin + e_pot + e_pair + e_ext + e_pext
+        tot = e_kin + e_pot + e_pair + e_ext + e_pext + e_cur
         return dict(e_kin=e_kin, e_pot=e_pot, e_pair=e_pair, e_ext=e_ext, e_pair_ext=e_pext,
-                    e_total=tot, n_part=n_part)
+                    e_cur=e_cur, e_total=tot, n_part=n_part)
 
 
 # ----------------------------------------------------------------------------
