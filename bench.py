@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--friction", default=None,
                    help="alpha,beta,gamma of the quantum-friction terms (Sec. 5.2.4), e.g. 5,5,0")
     p.add_argument("--streams", type=int, default=4, help="forked streams of the batched workload")
+    p.add_argument("--A", type=float, default=1.0,
+                   help="inverse effective mass of the SLDA functional; != 1 adds the current terms "
+                        "(1.094 = A_a(0) of the ASLDA functional)")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
     return p.parse_args()
@@ -157,13 +160,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arms
-def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5", mu=None):
+def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5", mu=None, A=1.0):
+    """A != 1: the SLDA functional with its current terms (same B, C, mu and
+    uniform seed as the A = 1 workload)."""
     from paper_2602_08982_b300 import inputs
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(prec, stream=stream)
     ctx.set_integrator(scheme)
-    box = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"] if mu is None else mu,
-                      nstates=nstates)
+    box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"],
+                      mu=u["mu"] if mu is None else mu, A=A, nstates=nstates)
     ctx.set_vext(box, inputs.harmonic_trap(shape, omega))
     return ctx, box, u
 
@@ -171,16 +176,17 @@ def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5", mu=None):
 HISTORY_READS = {"AB3AM4": 2, "AB4AM5": 3, "AB5AM5": 4}
 
 
-def stage_x_algorithmic(prec, shape, scheme="AB4AM5"):
+def stage_x_algorithmic(prec, shape, scheme="AB4AM5", cur=False):
     """Algorithmic traffic / work of one stage-X launch per state-site.
     Bytes: reads phi and the history (AB4AM5: f_{k-2}, f_{k-3}, f_{k-4});
-    writes f_{k-1}, phi_p, c (AB4AM5: 7 state passes of two complex numbers).
+    writes f_{k-1}, phi_p, c (AB4AM5: 7 state passes of two complex numbers);
+    with the current terms (A != 1) it also reads the current term of H phi.
     Flops (FP64 path): forward and inverse 3D FFT of both components at
     5 M log2 M each, plus the pointwise H, <H>_n, f, predictor, corrector
     partial, norm and scaling (128)."""
     M = shape[0] * shape[1] * shape[2]
     csize = 8 if prec == 1 else 16
-    bytes_per = (1 + HISTORY_READS[scheme] + 3) * 2 * csize
+    bytes_per = (1 + HISTORY_READS[scheme] + 3 + (1 if cur else 0)) * 2 * csize
     flops_per = 2 * 2 * 5 * math.log2(M) + 128
     return bytes_per, flops_per
 
@@ -219,11 +225,12 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     if args.init == "scf":
         start = scf_start(W, args, shape)
         ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
-                               mu=start["info"]["mu"])
+                               mu=start["info"]["mu"], A=args.A)
         ctx.load_states(box, start["phi"])
         ctx.start(True, args.dt)               # a static solution: stationary start
     else:
-        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
+        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
+                               A=args.A)
         ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
         if args.friction:
             fa, fb, fg = (float(x) for x in args.friction.split(","))
@@ -257,7 +264,7 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     M = shape[0] * shape[1] * shape[2]
     units = float(args.nstates) * M * args.steps
     value = job_rate(units, world, ms * 1e-3)
-    bx, fx = stage_x_algorithmic(prec, shape, args.integrator)
+    bx, fx = stage_x_algorithmic(prec, shape, args.integrator, args.A != 1.0)
     x_ms, x_n = kt["stage_x"]
     x_avg = x_ms / max(x_n, 1)
     per_launch = float(args.nstates) * M
@@ -285,7 +292,8 @@ def run_e2e(W, torch, args, shape, world):
     """Mixed path end to end through the ABI with pinned host buffers: the
     states travel as complex64, the precision the mixed path stores them in."""
     stream = torch.cuda.current_stream()
-    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
+    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
+                           A=args.A)
     ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
     M = shape[0] * shape[1] * shape[2]
     host = torch.empty((args.nstates, 2, M), dtype=torch.complex64, pin_memory=True)
@@ -296,7 +304,8 @@ def run_e2e(W, torch, args, shape, world):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
-    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator)
+    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
+                           A=args.A)
     ctx.load_states_f32(box, host_np)
     ctx.start(False, args.dt)
     for _ in range(args.steps):
@@ -374,14 +383,14 @@ def run_batched(W, torch, args):
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(shape, omega, n):
+def oracle_sample(shape, omega, n, A=1.0):
     """CPU-oracle system for the workload's lattice and trap, with n of its
     uniform plane-wave states (seeded choice of momenta)."""
     from oracle import tdslda as o
     from paper_2602_08982_b300 import inputs
     lat = o.Lattice(*shape)
     seed = o.uniform_slda_seed(lat, 0.25, RHO_SIGMA)
-    fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu)
+    fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu, A=float(A))
     r = inputs.uniform01(77, lat.M)
     idx = np.sort(np.argsort(r)[:n])
     kx, ky, kz = (lat.kaxis(a) for a in range(3))
@@ -403,14 +412,14 @@ def oracle_stepper(o, scheme):
             (lambda sysm, st, dt: o.abm_step(sysm, st, dt, scheme)))
 
 
-def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048, scheme="AB4AM5"):
+def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
     """The oracle as it stands, on a bounded sample of the workload: the same
     lattice and trap with a subset of the uniform plane-wave states, timed over
     whole ABM steps after a stationary start."""
     max_states = min(max_states, shape[0] * shape[1] * shape[2])
     n = min(64, max_states)
     while True:
-        o, sysm, phi, lat = oracle_sample(shape, omega, n)
+        o, sysm, phi, lat = oracle_sample(shape, omega, n, A)
         start, step = oracle_stepper(o, scheme)
         st = start(sysm, phi, dt)
         t0 = time.perf_counter()
@@ -439,8 +448,8 @@ def reference_arm(args, shape):
             return
     # each step: one oracle step of the scheme over a bounded sample of the
     # states, sized so that one step takes about a second
-    n = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds / 4, scheme=args.integrator)["n"]
-    o, sysm, phi, lat = oracle_sample(shape, args.omega, n)
+    n = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds / 4, scheme=args.integrator, A=args.A)["n"]
+    o, sysm, phi, lat = oracle_sample(shape, args.omega, n, args.A)
     start, step = oracle_stepper(o, args.integrator)
     st = start(sysm, phi, args.dt)
     for _ in range(args.warmup):
@@ -467,7 +476,8 @@ def workload_config(args, shape, precision):
     return {"workload": f"TDSLDA {args.integrator} step, {shape[0]}x{shape[1]}x{shape[2]} periodic lattice, harmonic trap "
                         f"w={args.omega}, {args.nstates} quasiparticle states",
             "lattice": list(shape), "nstates": args.nstates, "trap_omega": args.omega, "dt": args.dt,
-            "functional": "SLDA (A=1), B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
+            "functional": (f"SLDA with current terms (A={args.A}), " if args.A != 1.0 else "SLDA (A=1), ")
+                          + "B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
             "init": ("states of a static self-consistent solve (fixed N, Broyden), stationary start"
                      if args.init == "scf" else
                      "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start"),
@@ -490,7 +500,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds, scheme=args.integrator)
+        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds, scheme=args.integrator, A=args.A)
     arms = {}
     if args.precision in ("both", "mixed"):
         arms["mixed"] = run_arm(W, torch, W.MIXED, args, shape, rank, world, local)

@@ -59,7 +59,8 @@ typedef enum { WSLDA_FP64 = 0, WSLDA_MIXED = 1 } wslda_precision;
 
 typedef enum {
   WSLDA_FUNC_SLDA_A1 = 0, /* SLDA with A forced to 1 (Sec. 2.4, last paragraph) */
-  WSLDA_FUNC_BDG = 1      /* BdG: A = 1, B = 0, coupling 4 pi a (Eq. HBdG) */
+  WSLDA_FUNC_BDG = 1,     /* BdG: A = 1, B = 0, coupling 4 pi a (Eq. HBdG) */
+  WSLDA_FUNC_SLDA = 2     /* SLDA-type with a constant A (field A), current terms included */
 } wslda_functional_kind;
 
 /* Periodic lattice (Sec. 3.1). Every n must be even; see
@@ -70,12 +71,22 @@ typedef struct {
 } wslda_lattice;
 
 /* Energy density functional and its regularised coupling (Sec. 2.4, 2.6).
- *  slda: E_0 = (tau_a + tau_b)/2 + 3/5 B rho eF(rho) + g_eff |nu|^2,
+ *  slda_a1: E_0 = (tau_a + tau_b)/2 + 3/5 B rho eF(rho) + g_eff |nu|^2,
  *        1/g_eff = rho^(1/3)/C - Lambda_c,  U = B eF - |Delta|^2/(3 C rho^(2/3))
+ *  slda (constant A, spin-symmetric; the ASLDA functional at p = 0 has
+ *        A = 1.094): E_0 + E_CM adds sum_s [(A - 1) tau_s / 2 + (1 - A) j_s^2 / (2 rho_s)]
+ *        (Eqs. sldae-functional-generic..sldae-functional), so that
+ *        h = -A/2 lap + U + V_ext - (i/2){A_s, grad} (Eq. h_sigma) with the
+ *        current potential A_s = (1 - A) j_s / rho_s and
+ *        U += (A - 1) j_s^2 / (2 rho_s^2); Lambda_c uses A_+ = A. j_s is
+ *        reduced over all states at every stage (Eq. jab3D); rho_s is floored
+ *        at rho_floor in these terms. A = 1 gives slda_a1. Static solves and
+ *        the dissipative terms are not available for it (WSLDA_EUNSUPPORTED).
  *  bdg : 1/g_eff = inv_4pi_a - Lambda_c,     U = 0
  *  Delta = -g_eff nu (Eq. Delta). mu is the chemical potential on the diagonal
  *  of H. ec <= 0 selects the zone-corner cutoff (pi^2/2)(1/dx^2+1/dy^2+1/dz^2).
- *  rho_floor bounds rho from below inside the potentials only. */
+ *  rho_floor bounds rho from below inside the potentials only. A is read for
+ *  kind slda only. */
 typedef struct {
   int kind;
   double B, C;
@@ -83,12 +94,15 @@ typedef struct {
   double mu;
   double ec;
   double rho_floor;
+  double A;
 } wslda_functional;
 
-/* Energy terms of Sec. 3.2 for A = 1. e_total is their sum; the evolution
- * conserves e_total - mu * n_part (Eq. E_tot). */
+/* Energy terms of Sec. 3.2. e_kin is A times the sum of the kinetic
+ * densities; e_cur = int sum_s (1 - A) j_s^2 / (2 rho_s) (kind slda, else 0).
+ * e_total is the sum of the terms; the evolution conserves e_total - mu * n_part
+ * (Eq. E_tot). */
 typedef struct {
-  double e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part;
+  double e_kin, e_pot, e_pair, e_ext, e_pair_ext, e_total, n_part, e_cur;
 } wslda_energy;
 
 /* Create a context on the current CUDA device. `cuda_stream` is a borrowed

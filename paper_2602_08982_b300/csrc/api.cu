@@ -73,6 +73,16 @@ struct Box {
   double f_alpha = 0.0, f_beta = 0.0, f_gamma = 0.0, f_rho0 = 1.0, f_nreq = 1.0;
   void* f_scratch = nullptr;
   double *f_div = nullptr, *f_bp = nullptr;
+  // current terms (functional with A != 1): per-state scratch [n][2][M] (the
+  // per-state contributions to j, then the current term of H phi), {tau, j}
+  // [4][M], current potential {A_x, A_y, A_z, div A / 2} [M], <H>_n partials
+  // [n][16], per-axis first-derivative columns
+  bool cur = false;
+  void* cur_buf = nullptr;
+  double* tauj = nullptr;
+  void* av = nullptr;
+  double* ecur = nullptr;
+  double* d1 = nullptr;
   bool loaded = false;
   void* ptr(int i) const { return slot[i]; }
 };
@@ -296,6 +306,27 @@ template <typename R>
 wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int kind) {
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
+  const bool applies_h = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
+                         mode == MODE_F || mode == MODE_HORNER;
+  if (b.cur && applies_h) {
+    // current term -(i/2){A, grad} phi of this launch's input states and its
+    // part of <H>_n: three gradient launches, read by the stage below
+    ProfScope pg(c, PROF_AUX);
+    for (int dir = 0; dir < 3; ++dir) {
+      StageArgs<R> g = base_args<R>(b, box_dV(b));
+      g.phi = a.phi;
+      g.sc_in = a.sc_in;
+      g.h0 = static_cast<cx<R>*>(b.cur_buf);
+      g.av = static_cast<const fx4<R>*>(b.av);
+      g.ecur = b.ecur;
+      g.dir = dir;
+      g.err = c->err_d;
+      CUDA_TRY(c, b.ks->launch[MODE_AGRAD](&g, int(b.n), b.ncl, c->cur));
+      c->launches += 1;
+    }
+    a.cur = static_cast<const cx<R>*>(b.cur_buf);
+    a.ecur = b.ecur;
+  }
   ProfScope ps(c, kind);
   const bool ym = mode == MODE_Y && b.ks_y;
   const KernelSet* ks = ym ? b.ks_y : b.ks;
@@ -313,6 +344,30 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
 // densities of slot `islot` -> potentials -> H fields
 template <typename R>
 wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
+  if (b.cur) {
+    // j of the states in the slot (Eq. jab3D; A != 1): per-state contributions
+    // from three gradient launches, summed over states (before the density
+    // partials, which reuse the partial-sum buffer)
+    if (b.n > 0) {
+      for (int dir = 0; dir < 3; ++dir) {
+        StageArgs<R> a = base_args<R>(b, box_dV(b));
+        a.phi = static_cast<cx<R>*>(b.ptr(islot));
+        a.h0 = static_cast<cx<R>*>(b.cur_buf);
+        a.sc_in = b.sc[islot];
+        a.wm = b.wm;
+        a.wp = b.wp;
+        a.dir = dir;
+        wslda_status st = launch_mode<R>(c, b, MODE_GRAD, a, PROF_DENS);
+        if (st) return st;
+      }
+      ProfScope pj(c, PROF_DENS);
+      c->launches += 2;
+      CUDA_TRY(c, launch_sum_tauj<R>(static_cast<const cx<R>*>(b.cur_buf), b.n, b.M, b.nchunk, b.chunk, b.part,
+                                     b.tauj, b.tauj + b.M, c->cur));
+    } else {
+      CUDA_TRY(c, cudaMemsetAsync(b.tauj, 0, size_t(4) * b.M * 8, c->cur));
+    }
+  }
   if (b.n > 0) {
     ProfScope ps(c, PROF_DENS);
     c->launches += 1;
@@ -326,8 +381,14 @@ wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   {
     ProfScope ps2(c, PROF_POT);
     c->launches += 1;
-    CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam, b.rho, b.nu,
-                                     b.U, b.delta, static_cast<fx4<R>*>(b.WD), c->cur));
+    CUDA_TRY(c, launch_potentials<R>(b.part, b.nchunk, b.M, b.fdev, b.vext, b.dext, b.lam, init_lam,
+                                     b.cur ? b.tauj + b.M : nullptr, b.rho, b.nu, b.U, b.delta,
+                                     static_cast<fx4<R>*>(b.WD), c->cur));
+    if (b.cur) {
+      c->launches += 1;
+      CUDA_TRY(c, launch_current_fields<R>(b.lat.nx, b.lat.ny, b.lat.nz, b.fdev.A, b.fdev.rho_floor, b.rho,
+                                           b.tauj + b.M, b.d1, static_cast<fx4<R>*>(b.av), c->cur));
+    }
   }
   if (b.fric && b.n > 0) {
     // per-state friction contributions (one transform pass), summed over
@@ -543,9 +604,9 @@ wslda_status compute_energy(wslda_ctx* c, Box& b, double* h) {
   c->cur = c->stream;
   wslda_status st = launch_mode<R>(c, b, MODE_EKIN, a, PROF_AUX);
   if (st) return st;
-  CUDA_TRY(c, launch_energy(b.M, b.n, b.fdev, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp, box_dV(b),
-                            b.out8, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(h, b.out8, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, launch_energy(b.M, b.n, b.fdev, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp,
+                            b.cur ? b.tauj + b.M : nullptr, box_dV(b), b.out8, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h, b.out8, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return WSLDA_OK;
 }
@@ -771,6 +832,7 @@ wslda_status wslda_set_friction(wslda_ctx* c, int box, double alpha, double beta
   CHECK_CTX(c);
   Box* b = get_box(c, box);
   if (!b) return fail(c, WSLDA_EINVAL, "set_friction: bad box");
+  if (b->cur) return fail(c, WSLDA_EUNSUPPORTED, "set_friction: functional with A != 1 not supported");
   if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma) || !(rho0 > 0.0) ||
       !(n_req > 0.0) || !std::isfinite(rho0) || !std::isfinite(n_req))
     return fail(c, WSLDA_EINVAL, "set_friction: coefficients must be finite, rho0 and n_req > 0");
@@ -820,9 +882,11 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0 || (lat->nx | lat->ny | lat->nz) & 1)
     return -fail(c, WSLDA_EINVAL, "lattice sizes must be positive and even");
   if (!(lat->dx > 0 && lat->dy > 0 && lat->dz > 0)) return -fail(c, WSLDA_EINVAL, "lattice spacings must be > 0");
-  if (fn->kind != WSLDA_FUNC_SLDA_A1 && fn->kind != WSLDA_FUNC_BDG)
+  if (fn->kind != WSLDA_FUNC_SLDA_A1 && fn->kind != WSLDA_FUNC_BDG && fn->kind != WSLDA_FUNC_SLDA)
     return -fail(c, WSLDA_EINVAL, "unknown functional kind");
-  if (fn->kind == WSLDA_FUNC_SLDA_A1 && !(fn->C != 0.0)) return -fail(c, WSLDA_EINVAL, "SLDA needs C != 0");
+  if (fn->kind != WSLDA_FUNC_BDG && !(fn->C != 0.0)) return -fail(c, WSLDA_EINVAL, "SLDA needs C != 0");
+  if (fn->kind == WSLDA_FUNC_SLDA && !(fn->A > 0.0 && std::isfinite(fn->A)))
+    return -fail(c, WSLDA_EINVAL, "SLDA needs a finite A > 0");
   const int prec = c->prec == WSLDA_MIXED ? 1 : 0;
   const KernelSet* ks = find_kernels(prec, lat->nx, lat->ny, lat->nz);
   if (!ks) return -fail(c, WSLDA_EUNSUPPORTED, "no compiled kernels for this lattice shape and precision");
@@ -837,7 +901,9 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.ks = ks;
   b.csize = prec ? 8 : 16;
   const size_t rsize = prec ? 4 : 8;
-  b.fdev.kind = fn->kind;
+  b.fdev.kind = fn->kind == WSLDA_FUNC_BDG ? 1 : 0;
+  b.fdev.A = fn->kind == WSLDA_FUNC_SLDA ? fn->A : 1.0;
+  b.cur = fn->kind == WSLDA_FUNC_SLDA && fn->A != 1.0;
   b.fdev.B = fn->B;
   b.fdev.C = fn->C;
   b.fdev.inv_4pi_a = fn->inv_4pi_a;
@@ -851,7 +917,8 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   const size_t field_bytes = size_t(M) * (8 * 13 + rsize * 4) + size_t(4) * M * 8 * b.nchunk +
                              size_t(nstates) * (8 * 26 + rsize * 2) + 4096;
   const int D = c->scheme_depth;
-  const size_t need = size_t(D + 2) * state_bytes + field_bytes;
+  const size_t need = size_t(D + 2 + (b.cur ? 1 : 0)) * state_bytes + field_bytes +
+                      (b.cur ? size_t(M) * (32 + 4 * rsize) + size_t(nstates) * 128 : 0);
   size_t freeb = 0, totalb = 0;
   CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
   const size_t margin = size_t(1) << 30;
@@ -897,6 +964,13 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.npart, std::max<int64_t>(nstates, 1) * 16 * 8);
   ALLOC(b.ekin2, std::max<int64_t>(nstates, 1) * 16);
   ALLOC(b.out8, 8 * 8);
+  if (b.cur) {
+    ALLOC(b.cur_buf, std::max<size_t>(state_bytes, 16));
+    ALLOC(b.tauj, size_t(4) * M * 8);
+    ALLOC(b.av, size_t(4) * M * rsize);
+    ALLOC(b.ecur, std::max<int64_t>(nstates, 1) * 16 * 8);
+    ALLOC(b.d1, size_t(lat->nx + lat->ny + lat->nz) * 8);
+  }
 #undef ALLOC
   CUDA_TRY_NEG(c, cudaMemsetAsync(b.vext, 0, M * 8, c->stream));
   CUDA_TRY_NEG(c, cudaMemsetAsync(b.dext, 0, 2 * M * 8, c->stream));
@@ -907,7 +981,27 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   axis_tables(lat->nx, ks->tx, lat->dx, scale, k2, k1, twr, twi);
   axis_tables(lat->ny, ks->ty, lat->dy, scale, k2, k1, twr, twi);
   axis_tables(lat->nz, ks->tz, lat->dz, scale, k2, k1, twr, twi);
+  // constant inverse effective mass: -1/2 grad.alpha grad = -alpha/2 lap (Eq. kinop-alpha)
+  for (double& v : k2) v *= b.fdev.A;
   k2.insert(k2.end(), k1.begin(), k1.end());
+  if (b.cur) {
+    // first column of the periodic first-derivative matrix of each axis with
+    // the Nyquist mode left out: d_j = -(2/N) sum_{m=1}^{N/2-1} k_m sin(2 pi m j / N)
+    std::vector<double> d1;
+    const int ns[3] = {lat->nx, lat->ny, lat->nz};
+    const double ds[3] = {lat->dx, lat->dy, lat->dz};
+    for (int ax = 0; ax < 3; ++ax) {
+      const int N = ns[ax];
+      for (int jj = 0; jj < N; ++jj) {
+        double acc = 0.0;
+        for (int m = 1; m < N / 2; ++m)
+          acc -= 2.0 * (2.0 * M_PI * m / (N * ds[ax])) * sin(2.0 * M_PI * double(m) * double(jj) / double(N));
+        d1.push_back(acc / N);
+      }
+    }
+    CUDA_TRY_NEG(c, cudaMemcpyAsync(b.d1, d1.data(), d1.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY_NEG(c, cudaStreamSynchronize(c->stream));
+  }
   std::vector<double> tw(2 * naxis);
   for (int i = 0; i < naxis; ++i) {
     tw[2 * i] = twr[i];
@@ -1071,6 +1165,7 @@ wslda_status wslda_static_solve(wslda_ctx* c, int box, const double* U0, const d
   if (!b || !U0 || !delta0 || !p || !out) return fail(c, WSLDA_EINVAL, "static_solve: bad box or null pointer");
   if (c->started) return fail(c, WSLDA_ESTATE, "static_solve after wslda_start");
   if (b->n != b->M) return fail(c, WSLDA_EINVAL, "static_solve: the box must hold nstates = M states");
+  if (b->fdev.A != 1.0) return fail(c, WSLDA_EUNSUPPORTED, "static_solve: functional with A != 1 not built");
   if (!(p->mixing > 0.0 && p->mixing <= 1.0) || p->max_iters < 1 || !(p->eps_energy >= 0.0) ||
       !std::isfinite(p->e_ref) || !std::isfinite(p->n_target) || !std::isfinite(p->a_mu) ||
       (p->n_target > 0 && !(p->eps_npart > 0.0)) || (p->method != 0 && p->method != 1) ||
@@ -1345,6 +1440,7 @@ wslda_status wslda_get_energy(wslda_ctx* c, int box, wslda_energy* out) {
   out->e_pair_ext = h[4];
   out->e_total = h[5];
   out->n_part = h[6];
+  out->e_cur = h[7];
   return WSLDA_OK;
 }
 

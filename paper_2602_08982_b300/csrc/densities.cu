@@ -144,7 +144,8 @@ constexpr int kRegulatorIters = 60;  // fixed-point iterations for the t = 0 reg
 template <typename R>
 __global__ void potentials_kernel(const double* __restrict__ part, int nchunk, int M, FunctionalDev fn,
                                   const double* __restrict__ vext, const double* __restrict__ dext, double* lam,
-                                  int init_lam, double* rho, double* nu, double* Uo, double* delta, fx4<R>* WD) {
+                                  int init_lam, const double* __restrict__ j, double* rho, double* nu, double* Uo,
+                                  double* delta, fx4<R>* WD) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= M) return;
   double r = 0.0, nr = 0.0, ni = 0.0;
@@ -155,21 +156,30 @@ __global__ void potentials_kernel(const double* __restrict__ part, int nchunk, i
     ni += p[2 * M + s];
   }
   const double ve = vext[s];
+  // current part of U (A != 1): d/d rho_s [(1 - A) j^2 / (2 rho_s)] = (A - 1) j^2 / (2 rho_s^2)
+  double ucur = 0.0;
+  if (j) {
+    const double rs = fmax(r, fn.rho_floor);
+    const double jx = j[s], jy = j[M + s], jz = j[2 * M + s];
+    ucur = (fn.A - 1.0) * (jx * jx + jy * jy + jz * jz) / (2.0 * rs * rs);
+  }
   double l;
   if (init_lam) {
     // Regulator frozen at its t = 0 value: fixed point of U -> Lambda_c -> U.
     double U = 0.0, dr, di;
     for (int it = 0; it < kRegulatorIters; ++it) {
-      l = regulator(fn.mu - U - ve, fn.ec);
+      l = regulator(fn.mu - U - ve, fn.ec, fn.A);
       site_potentials(fn, r, nr, ni, l, U, dr, di);
+      U += ucur;
     }
-    l = regulator(fn.mu - U - ve, fn.ec);
+    l = regulator(fn.mu - U - ve, fn.ec, fn.A);
     lam[s] = l;
   } else {
     l = lam[s];
   }
   double U, dr, di;
   site_potentials(fn, r, nr, ni, l, U, dr, di);
+  U += ucur;
   rho[s] = r;
   nu[2 * s] = nr;
   nu[2 * s + 1] = ni;
@@ -186,17 +196,56 @@ __global__ void potentials_kernel(const double* __restrict__ part, int nchunk, i
 
 template <typename R>
 cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
-                              const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
-                              double* delta, fx4<R>* WD, cudaStream_t s) {
-  potentials_kernel<R><<<(M + 127) / 128, 128, 0, s>>>(part, nchunk, M, fn, vext, dext, lam, init_lam, rho, nu, U,
-                                                       delta, WD);
+                              const double* dext, double* lam, int init_lam, const double* j, double* rho, double* nu,
+                              double* U, double* delta, fx4<R>* WD, cudaStream_t s) {
+  potentials_kernel<R><<<(M + 127) / 128, 128, 0, s>>>(part, nchunk, M, fn, vext, dext, lam, init_lam, j, rho, nu,
+                                                       U, delta, WD);
   return cudaGetLastError();
 }
 template cudaError_t launch_potentials<float>(const double*, int, int, FunctionalDev, const double*, const double*,
-                                              double*, int, double*, double*, double*, double*, float4*, cudaStream_t);
+                                              double*, int, const double*, double*, double*, double*, double*,
+                                              float4*, cudaStream_t);
 template cudaError_t launch_potentials<double>(const double*, int, int, FunctionalDev, const double*, const double*,
-                                               double*, int, double*, double*, double*, double*, double4*,
-                                               cudaStream_t);
+                                               double*, int, const double*, double*, double*, double*, double*,
+                                               double4*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Current potential (A != 1): A_d = (1 - A) j_d / rho_s at each site and its
+// divergence by the periodic first-derivative matrices of Eq. d_dxA, applied
+// as direct sums along the three axes (d1 holds the first column of each
+// circulant matrix, axis by axis). Output {A_x, A_y, A_z, div A / 2}.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void current_fields_kernel(int nx, int ny, int nz, double one_minus_A, double rho_floor,
+                                      const double* __restrict__ rho, const double* __restrict__ j,
+                                      const double* __restrict__ d1, fx4<R>* __restrict__ AV) {
+  const int M = nx * ny * nz;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int x = s / (ny * nz), y = (s / nz) % ny, z = s % nz;
+  auto comp = [&](int d, int site) { return one_minus_A * j[d * M + site] / fmax(rho[site], rho_floor); };
+  double div = 0.0;
+  for (int l = 0; l < nx; ++l) div += d1[(x - l + nx) % nx] * comp(0, (l * ny + y) * nz + z);
+  for (int l = 0; l < ny; ++l) div += d1[nx + (y - l + ny) % ny] * comp(1, (x * ny + l) * nz + z);
+  for (int l = 0; l < nz; ++l) div += d1[nx + ny + (z - l + nz) % nz] * comp(2, (x * ny + y) * nz + l);
+  fx4<R> f;
+  f.x = R(comp(0, s));
+  f.y = R(comp(1, s));
+  f.z = R(comp(2, s));
+  f.w = R(0.5 * div);
+  AV[s] = f;
+}
+template <typename R>
+cudaError_t launch_current_fields(int nx, int ny, int nz, double A, double rho_floor, const double* rho,
+                                  const double* j, const double* d1, fx4<R>* AV, cudaStream_t s) {
+  const int M = nx * ny * nz;
+  current_fields_kernel<R><<<(M + 127) / 128, 128, 0, s>>>(nx, ny, nz, 1.0 - A, rho_floor, rho, j, d1, AV);
+  return cudaGetLastError();
+}
+template cudaError_t launch_current_fields<float>(int, int, int, double, double, const double*, const double*,
+                                                  const double*, float4*, cudaStream_t);
+template cudaError_t launch_current_fields<double>(int, int, int, double, double, const double*, const double*,
+                                                   const double*, double4*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // tau and j: sums over states of the per-state contributions (read-out only).
@@ -316,9 +365,10 @@ template cudaError_t launch_apply_friction<double>(int, double, double, double, 
 __global__ void __launch_bounds__(1024) energy_kernel(int M, int64_t nstates, FunctionalDev fn,
                                                       const double* rho_s, const double* nu, const double* delta,
                                                       const double* vext, const double* dext, const double* ekin2,
-                                                      const double* wm, const double* wp, double dV, double* out8) {
-  __shared__ double sh[6][32];
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+                                                      const double* wm, const double* wp, const double* j, double dV,
+                                                      double* out8) {
+  __shared__ double sh[7][32];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t n = threadIdx.x; n < nstates; n += blockDim.x)
     acc[0] += 2.0 * (wm[n] * ekin2[2 * n + 1] + wp[n] * ekin2[2 * n]);  // <v|-lap|v> = 2 <v|T|v>
   for (int s = threadIdx.x; s < M; s += blockDim.x) {
@@ -328,17 +378,22 @@ __global__ void __launch_bounds__(1024) energy_kernel(int M, int64_t nstates, Fu
     acc[3] += vext[s] * rho * dV;
     acc[4] += -2.0 * (dext[2 * s] * nu[2 * s] + dext[2 * s + 1] * nu[2 * s + 1]) * dV;
     acc[5] += rho * dV;
+    if (j) {  // current terms (A != 1): sum_s (1 - A) j_s^2 / (2 rho_s)
+      const double rs = fmax(rho_s[s], fn.rho_floor);
+      const double jx = j[s], jy = j[M + s], jz = j[2 * M + s];
+      acc[6] += (1.0 - fn.A) * (jx * jx + jy * jy + jz * jz) / rs * dV;
+    }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     double v = acc[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) sh[k][w] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t[6];
-    for (int k = 0; k < 6; ++k) {
+    double t[7];
+    for (int k = 0; k < 7; ++k) {
       t[k] = 0.0;
       for (int i = 0; i < int(blockDim.x >> 5); ++i) t[k] += sh[k][i];
     }
@@ -347,15 +402,17 @@ __global__ void __launch_bounds__(1024) energy_kernel(int M, int64_t nstates, Fu
     out8[2] = t[2];
     out8[3] = t[3];
     out8[4] = t[4];
-    out8[5] = t[0] + t[1] + t[2] + t[3] + t[4];
+    out8[5] = t[0] + t[1] + t[2] + t[3] + t[4] + t[6];
     out8[6] = t[5];
+    out8[7] = t[6];
   }
 }
 
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
                           const double* delta, const double* vext, const double* dext, const double* ekin2,
-                          const double* wm, const double* wp, double dV, double* out8, cudaStream_t s) {
-  energy_kernel<<<1, 1024, 0, s>>>(M, nstates, fn, rho, nu, delta, vext, dext, ekin2, wm, wp, dV, out8);
+                          const double* wm, const double* wp, const double* j, double dV, double* out8,
+                          cudaStream_t s) {
+  energy_kernel<<<1, 1024, 0, s>>>(M, nstates, fn, rho, nu, delta, vext, dext, ekin2, wm, wp, j, dV, out8);
   return cudaGetLastError();
 }
 

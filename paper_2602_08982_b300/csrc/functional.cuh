@@ -10,14 +10,14 @@ namespace wslda {
 // ---------------------------------------------------------------------------
 // Functional (Sec. 2.4) and regulator (Sec. 2.6) at one site.
 // ---------------------------------------------------------------------------
-__device__ inline double regulator(double mu_minus_V, double ec) {
-  // Lambda_c = (1/2 pi^2) PV int_0^kc k^2 dk / (k^2 - k0^2), A = 1:
-  // k0^2 = 2 (mu - V), kc^2 = 2 (E_c + mu - V).
-  const double k0sq = 2.0 * mu_minus_V;
-  const double kcsq = 2.0 * (ec + mu_minus_V);
+__device__ inline double regulator(double mu_minus_V, double ec, double A = 1.0) {
+  // Lambda_c = (1/2 pi^2) PV int_0^kc k^2 dk / (A k^2 - A k0^2):
+  // A k0^2 / 2 = mu - V, A kc^2 / 2 = E_c + mu - V (A_+ = A, spin-symmetric).
+  const double k0sq = 2.0 * mu_minus_V / A;
+  const double kcsq = 2.0 * (ec + mu_minus_V) / A;
   if (!(kcsq > 0.0)) return 0.0;
   const double kc = sqrt(kcsq);
-  const double pref = kc / (2.0 * M_PI * M_PI);
+  const double pref = kc / (2.0 * M_PI * M_PI * A);
   if (k0sq > 0.0) {
     const double k0 = sqrt(k0sq);
     return pref * (1.0 - (k0 / (2.0 * kc)) * log((kc + k0) / (kc - k0)));

@@ -83,6 +83,7 @@ KernelSet make_set() {
   k.launch[MODE_X3] = launch_stage<G, MODE_X3>;
   k.launch[MODE_X5] = launch_stage<G, MODE_X5>;
   k.launch[MODE_LAP] = launch_stage<G, MODE_LAP>;
+  k.launch[MODE_AGRAD] = launch_stage<G, MODE_AGRAD>;
   k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X, false>;
   k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y, false>;
   k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F, false>;
@@ -92,6 +93,7 @@ KernelSet make_set() {
   k.fn[MODE_X3] = (const void*)stage_kernel<G, MODE_X3, false>;
   k.fn[MODE_X5] = (const void*)stage_kernel<G, MODE_X5, false>;
   k.fn[MODE_LAP] = (const void*)stage_kernel<G, MODE_LAP, false>;
+  k.fn[MODE_AGRAD] = (const void*)stage_kernel<G, MODE_AGRAD, false>;
   return k;
 }
 
@@ -107,8 +109,9 @@ KernelSet make_set() {
 // Site-major kernels (densities.cu)
 // ---------------------------------------------------------------------------
 struct FunctionalDev {
-  int kind;  // 0 slda(A=1), 1 bdg
+  int kind;  // 0 slda, 1 bdg
   double B, C, inv_4pi_a, mu, ec, rho_floor;
+  double A;  // inverse effective mass (1 unless the box carries the current terms)
 };
 
 // Partial sums over chunks of states: part[c][0..2][M] = rho, Re nu, Im nu.
@@ -133,8 +136,15 @@ int density_chunks(int M, int64_t nstates, int is_float);
 // the H fields in precision R.
 template <typename R>
 cudaError_t launch_potentials(const double* part, int nchunk, int M, FunctionalDev fn, const double* vext,
-                              const double* dext, double* lam, int init_lam, double* rho, double* nu, double* U,
-                              double* delta, fx4<R>* WD, cudaStream_t s);
+                              const double* dext, double* lam, int init_lam, const double* j, double* rho, double* nu,
+                              double* U, double* delta, fx4<R>* WD, cudaStream_t s);
+
+// Current potential of A != 1 boxes: AV[s] = {A_x, A_y, A_z, div A / 2} with
+// A_d = (1 - A) j_d / max(rho_s, rho_floor); d1 = first columns of the
+// per-axis first-derivative matrices, concatenated x, y, z.
+template <typename R>
+cudaError_t launch_current_fields(int nx, int ny, int nz, double A, double rho_floor, const double* rho,
+                                  const double* j, const double* d1, fx4<R>* AV, cudaStream_t s);
 
 // tau and j (Eqs. nab3D..jab3D) from per-state contributions stored as
 // [n][2][M] complex {tau, j_x}, {j_y, j_z}: summed over states per site.
@@ -149,7 +159,8 @@ cudaError_t launch_finalize_norm(const double* npart, int cs, int64_t n, double 
 // Energy terms (Sec. 3.2) from the site fields and per-state kinetic values.
 cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double* rho, const double* nu,
                           const double* delta, const double* vext, const double* dext, const double* ekin2,
-                          const double* wm, const double* wp, double dV, double* out8, cudaStream_t s);
+                          const double* wm, const double* wp, const double* j, double dV, double* out8,
+                          cudaStream_t s);
 
 // Plane-wave states of a uniform solution (uniform.cu); dst is float2 or double2.
 cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,

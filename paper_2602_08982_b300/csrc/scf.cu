@@ -617,7 +617,7 @@ wslda_status static_solve(const ScfBox& b, const double* U0, const double* D0, c
     }
     scf_fields<<<(M + 127) / 128, 128, 0, s>>>(nx, ny, nz, frho, fnu, Uin, b.vext, fn, b.rho, b.nu, Uout, b.delta);
     SCF_CUDA(cudaGetLastError());
-    SCF_CUDA(launch_energy(M, M, fn, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp, dV, b.out8, s));
+    SCF_CUDA(launch_energy(M, M, fn, b.rho, b.nu, b.delta, b.vext, b.dext, b.ekin2, b.wm, b.wp, nullptr, dV, b.out8, s));
     std::vector<int> hinfo(blks.size());
     SCF_CUDA(cudaMemcpyAsync(cur, b.out8, 7 * 8, cudaMemcpyDeviceToHost, s));
     SCF_CUDA(cudaMemcpyAsync(hinfo.data(), info, blks.size() * sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -28,6 +28,12 @@
 //   MODE_GRAD    one Cartesian derivative d_dir (symbol i k_dir, Nyquist mode
 //            zeroed) of u and v, and the per-state weighted contributions to
 //            tau and j_dir (Eqs. nab3D..jab3D), accumulated into h0.
+//   MODE_AGRAD   the current term of h (Eq. h_sigma, A != 1) of the input
+//            states, one direction per launch: S = sum_d A_d d_d phi +
+//            (div A / 2) phi is accumulated in h0 and the third launch stores
+//            -i S and the per-CTA partials of sum_r Re(phi^* (-i S)) (the
+//            current part of <H>_n). The stage modes add it to H phi when
+//            `cur` is set.
 // Normalisation (Alg. 2 steps 2 and 8) is deferred: states are written as
 // computed, each CTA stores its partial norm, a small kernel turns the partials
 // into the per-state factor 1/sqrt(norm), and every consumer (the next stage,
@@ -53,7 +59,7 @@ template <typename R> using fx4 = typename fx4_of<R>::type;
 // MODE_X3 / MODE_X5: the predictor stage of AB3AM4 / AB5AM5 (MODE_X is AB4AM5's).
 enum Mode : int {
   MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, MODE_X3 = 6, MODE_X5 = 7,
-  MODE_LAP = 8, NMODES = 9
+  MODE_LAP = 8, MODE_AGRAD = 9, NMODES = 10
 };
 
 template <typename R>
@@ -80,7 +86,10 @@ struct StageArgs {
   double ycoef;      // Y: coefficient of the new term of the corrector (251/720 for AM5, 9/24 for AM4)
   const double* wm;  // GRAD: frozen weights f(-E_n), f(E_n)
   const double* wp;
-  int dir;           // GRAD: derivative direction 0, 1, 2
+  const fx4<R>* av;  // AGRAD: [M] {A_x, A_y, A_z, div A / 2} (current potential, A != 1)
+  const cx<R>* cur;  // X, Y, F, HORNER: current term -(i/2){A, grad} phi of the input states (NULL: none)
+  double* ecur;      // AGRAD: writes, stage modes read: [n][16] per-CTA partials of its <H>_n part
+  int dir;           // GRAD, AGRAD: derivative direction 0, 1, 2
   int compute_e;
   int normalize;
   int nstates;
@@ -402,7 +411,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   if (tid < 2 && n + ncl < a.nstates)
     prefetch_l2(a.phi + size_t(n + ncl) * 2 * G::M + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
   R eku = 0, ekv = 0;
-  x_pass<G, MODE == MODE_GRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
+  x_pass<G, MODE == MODE_GRAD || MODE == MODE_AGRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
   // Publish this CTA's partial <H>_n (or kinetic sums) into the slots of every
   // CTA of the cluster on the barrier that closes the x pass; afterwards each
   // CTA reads only its own shared memory, so no CTA has to outlive another.
@@ -441,6 +450,8 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   }
   double En = 0.0, Ev = 0.0;
   for (int r = 0; r < G::CS; ++r) { En += slot[r]; Ev += slot[G::CS + r]; }
+  if (a.ecur && MODE != MODE_EKIN)
+    for (int r = 0; r < G::CS; ++r) En += a.ecur[size_t(n) * 16 + r];
   En *= a.dV;
   Ev *= a.dV;
   if (MODE == MODE_EKIN) { En *= double(sin2); Ev *= double(sin2); }
@@ -485,6 +496,50 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       out[g] = o0;
       if (a.dir == 1) out[G::M + g] = mk<C>(jd, R(0));
       if (a.dir == 2) { C o1 = out[G::M + g]; o1.y = jd; out[G::M + g] = o1; }
+    }
+    return;
+  } else if constexpr (MODE == MODE_AGRAD) {
+    // buf holds d_dir u, d_dir v of the stored (unscaled) input
+    C* out = a.h0 + sbase;
+    R ep2 = 0, ec2 = 0;  // compensated partial of sum Re(phi^* G)
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const int g = gs0 + s;
+      const fx4<R> av = a.av[g];
+      const R Ad = a.dir == 0 ? av.x : (a.dir == 1 ? av.y : av.z);
+      const C du = scl(buf[sidx(s)], sin_), dv = scl(buf[G::SLAB + sidx(s)], sin_);
+      C su, sv;
+      if (a.dir == 0) {
+        su = scl(scl(in[g], sin_), av.w);
+        sv = scl(scl(in[G::M + g], sin_), av.w);
+      } else {
+        su = out[g];
+        sv = out[G::M + g];
+      }
+      su = add(su, scl(du, Ad));
+      sv = add(sv, scl(dv, Ad));
+      if (a.dir == 2) {
+        su = mul_mi(su);
+        sv = mul_mi(sv);
+        const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
+        const R t = (uu.x * su.x + uu.y * su.y + vv.x * sv.x + vv.y * sv.y) - ec2;
+        const R ns = ep2 + t;
+        ec2 = (ns - ep2) - t;
+        ep2 = ns;
+      }
+      out[g] = su;
+      out[G::M + g] = sv;
+    }
+    if (a.dir == 2) {
+      double v = double(ep2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) red[G::RED_WB + (tid >> 5)] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
+        a.ecur[size_t(n) * 16 + rank] = t;
+      }
     }
     return;
   } else {
@@ -543,6 +598,10 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
           C hm[2];
           hm[0] = sub(add(add(scl(buf[b], sin_), scl(uu, w)), mul(d, vv)), scl(uu, Er));
           hm[1] = sub(sub(sub(mulc(uu, d), scl(buf[G::SLAB + b], sin_)), scl(vv, w)), scl(vv, Er));
+          if (a.cur) {  // current term (A != 1), the same operator on both components
+            hm[0] = add(hm[0], a.cur[sbase + g]);
+            hm[1] = add(hm[1], a.cur[sbase + G::M + g]);
+          }
           const C ph[2] = {uu, vv};
 #pragma unroll
           for (int c = 0; c < 2; ++c) {

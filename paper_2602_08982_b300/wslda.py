@@ -18,7 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libwslda_td.so")
 
 FP64, MIXED = 0, 1
-SLDA_A1, BDG = 0, 1
+SLDA_A1, BDG, SLDA = 0, 1, 2
+A_ASLDA = 1.094  # A_a(0) of the ASLDA functional (Sec. 2.4)
 SCHEMES = {"AB4AM5": 0, "AB3AM4": 1, "AB5AM5": 2}
 # B of the spin-symmetric ASLDA functional (Sec. 2.4): 2^(2/3) [0.357 - 2 A(0) 2^(-5/3)], A(0) = 1.094
 B_SLDA = 2.0 ** (2.0 / 3.0) * (0.357 - 2.0 * 1.094 * 2.0 ** (-5.0 / 3.0))
@@ -40,7 +41,7 @@ class Lattice(ct.Structure):
 
 class Functional(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("B", ct.c_double), ("C", ct.c_double), ("inv_4pi_a", ct.c_double),
-                ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double)]
+                ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double), ("A", ct.c_double)]
 
 
 class Uniform(ct.Structure):
@@ -48,7 +49,8 @@ class Uniform(ct.Structure):
 
 
 class Energy(ct.Structure):
-    _fields_ = [(k, ct.c_double) for k in ("e_kin", "e_pot", "e_pair", "e_ext", "e_pair_ext", "e_total", "n_part")]
+    _fields_ = [(k, ct.c_double) for k in ("e_kin", "e_pot", "e_pair", "e_ext", "e_pair_ext", "e_total", "n_part",
+                                           "e_cur")]
 
 
 class ScfParams(ct.Structure):
@@ -137,7 +139,7 @@ def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4p
                   rho_sigma=1.0 / (6 * np.pi ** 2), delta0=0.0) -> dict:
     """Uniform plane-wave BCS solution on the lattice (wslda_uniform_solve)."""
     lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
-    fn = Functional(int(kind), float(B), 0.0, float(inv_4pi_a), 0.0, float(ec), 1e-12)
+    fn = Functional(int(kind), float(B), 0.0, float(inv_4pi_a), 0.0, float(ec), 1e-12, 1.0)
     out = Uniform()
     st = lib.wslda_uniform_solve(ct.byref(lat), ct.byref(fn), float(rho_sigma), float(delta0), ct.byref(out))
     if st:
@@ -215,9 +217,11 @@ class Context:
         self._check(lib.wslda_set_integrator(self._h, SCHEMES[scheme]))
 
     def add_box(self, shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, C=-1.0, inv_4pi_a=0.0, mu=0.0,
-                ec=-1.0, rho_floor=1e-12, nstates: int) -> int:
+                ec=-1.0, rho_floor=1e-12, A=1.0, nstates: int) -> int:
+        """kind SLDA with A != 1 carries the current terms (inverse effective mass A)."""
         lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
-        fn = Functional(int(kind), float(B), float(C), float(inv_4pi_a), float(mu), float(ec), float(rho_floor))
+        fn = Functional(int(kind), float(B), float(C), float(inv_4pi_a), float(mu), float(ec), float(rho_floor),
+                        float(A))
         r = lib.wslda_add_box(self._h, ct.byref(lat), ct.byref(fn), int(nstates))
         if r < 0:
             self._check(-r)

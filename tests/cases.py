@@ -48,11 +48,13 @@ def plane_waves(lat: o.Lattice, mu_eff: float, delta: float, idx: np.ndarray) ->
 
 
 def make_case(shape, spacing=(1.0, 1.0, 1.0), kind="slda", nstates=None, trap=0.0, kick=0.0, seed=1,
-              inv_kfa=-0.5, thermal=False, vortex=False) -> Case:
+              inv_kfa=-0.5, thermal=False, vortex=False, A=1.0) -> Case:
+    """A != 1 (kind slda) switches on the current terms; the uniform A = 1
+    seed then only supplies a start with the right density and gap scale."""
     lat = o.Lattice(*shape, *spacing)
     if kind == "slda":
         s = o.uniform_slda_seed(lat, DELTA0, RHO_S)
-        fn = o.Functional("slda", B=o.B_SLDA, C=s.C, mu=s.mu)
+        fn = o.Functional("slda", B=o.B_SLDA, C=s.C, mu=s.mu, A=float(A))
     else:
         ia = inv_kfa / (4 * np.pi)
         s = o.uniform_bdg_seed(lat, ia, RHO_S)
@@ -93,9 +95,9 @@ def gpu_context(c: Case, precision: int, scheme: str | None = None):
     ctx = W.Context(precision)
     if scheme is not None:
         ctx.set_integrator(scheme)
-    kind = W.SLDA_A1 if c.fn.kind == "slda" else W.BDG
+    kind = (W.SLDA if c.fn.currents else W.SLDA_A1) if c.fn.kind == "slda" else W.BDG
     box = ctx.add_box(c.lat.shape, (c.lat.dx, c.lat.dy, c.lat.dz), kind=kind, B=c.fn.B, C=c.fn.C,
-                      inv_4pi_a=c.fn.inv_4pi_a, mu=c.fn.mu, nstates=c.phi.shape[0])
+                      inv_4pi_a=c.fn.inv_4pi_a, mu=c.fn.mu, A=c.fn.A, nstates=c.phi.shape[0])
     ctx.set_vext(box, c.vext)
     if c.dext is not None:
         ctx.set_dext(box, c.dext)
