@@ -114,7 +114,9 @@ const char* wslda_last_error(const wslda_ctx* ctx);
 /* 1 if kernels for this lattice shape and precision are compiled in. */
 int wslda_lattice_supported(int precision, int nx, int ny, int nz);
 /* Number of compiled launch variants for the shape (0 if unsupported); the
- * environment variable WSLDA_VARIANT=<index> forces one of them. */
+ * environment variable WSLDA_VARIANT=<index> forces one of them (with
+ * WSLDA_PERSIST=0/1 fixing the launch form, WSLDA_VARIANT_Y=<index> then puts
+ * the corrector stage on another variant). */
 int wslda_lattice_variants(int precision, int nx, int ny, int nz);
 
 /* Predictor-corrector scheme of the boxes added afterwards (Sec. 3.3):

@@ -306,30 +306,28 @@ template <typename R>
 wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int kind) {
   a.err = c->err_d;
   if (b.n == 0) return WSLDA_OK;
+  const bool ym = mode == MODE_Y && b.ks_y;
+  const KernelSet* ks = ym ? b.ks_y : b.ks;
   const bool applies_h = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
                          mode == MODE_F || mode == MODE_HORNER;
   if (b.cur && applies_h) {
     // current term -(i/2){A, grad} phi of this launch's input states and its
-    // part of <H>_n: three gradient launches, read by the stage below
+    // part of <H>_n, read by the stage below. It runs on the stage's own launch
+    // variant: its <H>_n partials are per CTA of that variant's clusters.
     ProfScope pg(c, PROF_AUX);
-    for (int dir = 0; dir < 3; ++dir) {
-      StageArgs<R> g = base_args<R>(b, box_dV(b));
-      g.phi = a.phi;
-      g.sc_in = a.sc_in;
-      g.h0 = static_cast<cx<R>*>(b.cur_buf);
-      g.av = static_cast<const fx4<R>*>(b.av);
-      g.ecur = b.ecur;
-      g.dir = dir;
-      g.err = c->err_d;
-      CUDA_TRY(c, b.ks->launch[MODE_AGRAD](&g, int(b.n), b.ncl, c->cur));
-      c->launches += 1;
-    }
+    StageArgs<R> g = base_args<R>(b, box_dV(b));
+    g.phi = a.phi;
+    g.sc_in = a.sc_in;
+    g.h0 = static_cast<cx<R>*>(b.cur_buf);
+    g.av = static_cast<const fx4<R>*>(b.av);
+    g.ecur = b.ecur;
+    g.err = c->err_d;
+    CUDA_TRY(c, ks->launch[MODE_AGRAD](&g, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
+    c->launches += 1;
     a.cur = static_cast<const cx<R>*>(b.cur_buf);
     a.ecur = b.ecur;
   }
   ProfScope ps(c, kind);
-  const bool ym = mode == MODE_Y && b.ks_y;
-  const KernelSet* ks = ym ? b.ks_y : b.ks;
   CUDA_TRY(c, ks->launch[mode](&a, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
   c->launches += 1;
   const bool norm_out = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
@@ -346,20 +344,17 @@ template <typename R>
 wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
   if (b.cur) {
     // j of the states in the slot (Eq. jab3D; A != 1): per-state contributions
-    // from three gradient launches, summed over states (before the density
+    // from the gradient launch, summed over states (before the density
     // partials, which reuse the partial-sum buffer)
     if (b.n > 0) {
-      for (int dir = 0; dir < 3; ++dir) {
-        StageArgs<R> a = base_args<R>(b, box_dV(b));
-        a.phi = static_cast<cx<R>*>(b.ptr(islot));
-        a.h0 = static_cast<cx<R>*>(b.cur_buf);
-        a.sc_in = b.sc[islot];
-        a.wm = b.wm;
-        a.wp = b.wp;
-        a.dir = dir;
-        wslda_status st = launch_mode<R>(c, b, MODE_GRAD, a, PROF_DENS);
-        if (st) return st;
-      }
+      StageArgs<R> a = base_args<R>(b, box_dV(b));
+      a.phi = static_cast<cx<R>*>(b.ptr(islot));
+      a.h0 = static_cast<cx<R>*>(b.cur_buf);
+      a.sc_in = b.sc[islot];
+      a.wm = b.wm;
+      a.wp = b.wp;
+      wslda_status st = launch_mode<R>(c, b, MODE_GRAD, a, PROF_DENS);
+      if (st) return st;
       ProfScope pj(c, PROF_DENS);
       c->launches += 2;
       CUDA_TRY(c, launch_sum_tauj<R>(static_cast<const cx<R>*>(b.cur_buf), b.n, b.M, b.nchunk, b.chunk, b.part,
@@ -515,7 +510,15 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   if (v.size() == 1 && pmode >= 0) {
     b.ncl = pmode ? resident_clusters(b.ks) : 0;
     b.ks_y = b.ks;
-    b.ncl_y = b.ncl;
+    // WSLDA_VARIANT_Y=<j> puts the corrector stage on another variant (as the
+    // autotuner may), so that mixed-variant steps can be checked
+    if (const char* fy = getenv("WSLDA_VARIANT_Y")) {
+      const std::vector<const KernelSet*> all =
+          find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
+      const int i = atoi(fy);
+      if (i >= 0 && i < int(all.size())) b.ks_y = all[i];
+    }
+    b.ncl_y = pmode ? resident_clusters(b.ks_y) : 0;
     return WSLDA_OK;
   }
   const std::vector<int64_t> key = {c->prec, b.lat.nx, b.lat.ny, b.lat.nz, std::min<int64_t>(b.n, 2048),
@@ -1363,31 +1366,27 @@ wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu,
   if (rho) CUDA_TRY(c, cudaMemcpyAsync(rho, b->rho, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream));
   if (nu) CUDA_TRY(c, cudaMemcpyAsync(nu, b->nu, size_t(b->M) * 16, cudaMemcpyDeviceToHost, c->stream));
   if ((tau || j) && b->n > 0) {
-    // three gradient launches accumulate per-state contributions in the free
-    // history slot (between steps slot ih[0] holds nothing live), then a
-    // site-major sum over states; tau_d and j_d use the Nyquist-free gradient
+    // the gradient launch leaves per-state contributions in the free history
+    // slot (between steps slot ih[0] holds nothing live), then a site-major
+    // sum over states; tau_d and j_d use the Nyquist-free gradient
     wslda_status st;
     c->cur = c->stream;
-    for (int dir = 0; dir < 3; ++dir) {
-      if (c->prec == WSLDA_MIXED) {
-        StageArgs<float> a = base_args<float>(*b, box_dV(*b));
-        a.phi = static_cast<float2*>(b->ptr(b->iphi));
-        a.h0 = static_cast<float2*>(b->ptr(b->ih[0]));
-        a.sc_in = b->sc[b->iphi];
-        a.wm = b->wm;
-        a.wp = b->wp;
-        a.dir = dir;
-        if ((st = launch_mode<float>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
-      } else {
-        StageArgs<double> a = base_args<double>(*b, box_dV(*b));
-        a.phi = static_cast<double2*>(b->ptr(b->iphi));
-        a.h0 = static_cast<double2*>(b->ptr(b->ih[0]));
-        a.sc_in = b->sc[b->iphi];
-        a.wm = b->wm;
-        a.wp = b->wp;
-        a.dir = dir;
-        if ((st = launch_mode<double>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
-      }
+    if (c->prec == WSLDA_MIXED) {
+      StageArgs<float> a = base_args<float>(*b, box_dV(*b));
+      a.phi = static_cast<float2*>(b->ptr(b->iphi));
+      a.h0 = static_cast<float2*>(b->ptr(b->ih[0]));
+      a.sc_in = b->sc[b->iphi];
+      a.wm = b->wm;
+      a.wp = b->wp;
+      if ((st = launch_mode<float>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
+    } else {
+      StageArgs<double> a = base_args<double>(*b, box_dV(*b));
+      a.phi = static_cast<double2*>(b->ptr(b->iphi));
+      a.h0 = static_cast<double2*>(b->ptr(b->ih[0]));
+      a.sc_in = b->sc[b->iphi];
+      a.wm = b->wm;
+      a.wp = b->wp;
+      if ((st = launch_mode<double>(c, *b, MODE_GRAD, a, PROF_AUX))) return st;
     }
     double* tj = nullptr;
     CUDA_TRY(c, cudaMalloc(&tj, size_t(4) * b->M * 8));

@@ -25,15 +25,19 @@
 //            (Sec. 5.2.4): w- Im(v lap v^*) - w+ Im(u lap u^*) (the divergence
 //            of j by the product rule) and -(w- - w+)/2 (u lap v^* + v^* lap u)
 //            (the sum in theta_B'), stored in h0 as [n][2][M] complex.
-//   MODE_GRAD    one Cartesian derivative d_dir (symbol i k_dir, Nyquist mode
-//            zeroed) of u and v, and the per-state weighted contributions to
-//            tau and j_dir (Eqs. nab3D..jab3D), accumulated into h0.
+//   MODE_GRAD    the three Cartesian derivatives d_d of u and v (symbol
+//            i k_d, Nyquist mode zeroed) and the per-state weighted
+//            contributions to tau and j_d (Eqs. nab3D..jab3D), stored in h0.
 //   MODE_AGRAD   the current term of h (Eq. h_sigma, A != 1) of the input
-//            states, one direction per launch: S = sum_d A_d d_d phi +
-//            (div A / 2) phi is accumulated in h0 and the third launch stores
-//            -i S and the per-CTA partials of sum_r Re(phi^* (-i S)) (the
+//            states: -i S with S = sum_d A_d d_d phi + (div A / 2) phi, stored
+//            in h0, and the per-CTA partials of sum_r Re(phi^* (-i S)) (the
 //            current part of <H>_n). The stage modes add it to H phi when
 //            `cur` is set.
+//   Both derivative modes use 1D transforms along one axis per derivative
+//   (the symbol i k_d is diagonal in k_d, so the other two axes need no
+//   transform): the slab is loaded once per axis (the second and third loads
+//   come from L2), z and y locally, x across the cluster, each followed by a
+//   pointwise sweep that accumulates into h0.
 // Normalisation (Alg. 2 steps 2 and 8) is deferred: states are written as
 // computed, each CTA stores its partial norm, a small kernel turns the partials
 // into the per-state factor 1/sqrt(norm), and every consumer (the next stage,
@@ -89,7 +93,6 @@ struct StageArgs {
   const fx4<R>* av;  // AGRAD: [M] {A_x, A_y, A_z, div A / 2} (current potential, A != 1)
   const cx<R>* cur;  // X, Y, F, HORNER: current term -(i/2){A, grad} phi of the input states (NULL: none)
   double* ecur;      // AGRAD: writes, stage modes read: [n][16] per-CTA partials of its <H>_n part
-  int dir;           // GRAD, AGRAD: derivative direction 0, 1, 2
   int compute_e;
   int normalize;
   int nstates;
@@ -244,13 +247,63 @@ __device__ __forceinline__ void local_pass(typename G::C* buf, const typename G:
   }
 }
 
+// Derivative along z (AXIS 2) or y (AXIS 1) by a 1D transform of the local
+// pencils: forward, times i k_d / N_d (Nyquist mode zeroed), inverse.
+template <class G, int AXIS>
+__device__ __forceinline__ void local_deriv(typename G::C* buf, const typename G::R* ktab, const typename G::C* tw) {
+  using C = typename G::C;
+  using R = typename G::R;
+  constexpr int N = AXIS == 2 ? G::NZ : G::NY;
+  constexpr int T = AXIS == 2 ? G::TZ : G::TY;
+  constexpr int N1 = N / T;
+  constexpr int NPEN = AXIS == 2 ? 2 * G::P * G::NY : 2 * G::P * G::NZ;
+  constexpr int PER = G::BT / T;
+  constexpr int ITERS = (NPEN + PER - 1) / PER;
+  // second half of ktab: k_d / M per slot; a 1D pass is normalised by 1/N
+  constexpr int KOFF = G::NX + G::NY + G::NZ + G::NX + (AXIS == 2 ? G::NY : 0);
+  const R fs = R(double(G::M) / double(N));
+  const int j = threadIdx.x % T;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int p = it * PER + threadIdx.x / T;
+    const bool act = p < NPEN;
+    const int pp = act ? p : 0;
+    C* base;
+    int stride;
+    if constexpr (AXIS == 2) {
+      const int comp = pp / (G::P * G::NY), row = pp % (G::P * G::NY);
+      base = buf + comp * G::SLAB + row * G::ZP;
+      stride = 1;
+    } else {
+      const int comp = pp / (G::P * G::NZ), rem = pp % (G::P * G::NZ);
+      const int xl = rem / G::NZ, z = rem % G::NZ;
+      base = buf + comp * G::SLAB + xl * G::NY * G::ZP + z;
+      stride = G::ZP;
+    }
+    C x[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) x[m] = base[(j + T * m) * stride];
+    pencil_fwd<N, T>(x, j, tw);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+      const R kk = ktab[KOFF + j + T * m] * fs;
+      x[m] = mk<C>(-kk * x[m].y, kk * x[m].x);
+    }
+    pencil_inv<N, T>(x, j, tw);
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) base[(j + T * m) * stride] = x[m];
+    }
+  }
+}
+
 // x pencils across the cluster: forward, multiply by the kinetic symbol, inverse.
 // Element x of a column lives in CTA x / P at plane x % P; the CTA windows are
 // mapped once (mapa) and accessed with 32-bit ld/st.shared::cluster.
 template <class G, bool GRAD = false>
 __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* ktab, const typename G::C* tw,
                                        cg::cluster_group& cl, typename G::R& ekin_u, typename G::R& ekin_v,
-                                       int dir = 0) {
+                                       typename G::R gscale = 1) {
   using C = typename G::C;
   using R = typename G::R;
   constexpr int T = G::TX, N = G::NX, N1 = N / T;
@@ -289,12 +342,12 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
     }
     pencil_fwd<N, T>(x, j, tw);
     if constexpr (GRAD) {
-      // symbol i k_dir / M (Nyquist mode zeroed), from the second half of ktab
+      // symbol i k_x (Nyquist mode zeroed): the second half of ktab holds
+      // k_x / M, gscale turns it into the normalisation of the pass
       constexpr int K1 = G::NX + G::NY + G::NZ;
-      const R kyz1 = dir == 1 ? ktab[K1 + G::NX + y] : ktab[K1 + G::NX + G::NY + z];
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
-        const R kk = dir == 0 ? ktab[K1 + j + T * m] : kyz1;
+        const R kk = ktab[K1 + j + T * m] * gscale;
         x[m] = mk<C>(-kk * x[m].y, kk * x[m].x);
       }
     } else {
@@ -411,7 +464,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   if (tid < 2 && n + ncl < a.nstates)
     prefetch_l2(a.phi + size_t(n + ncl) * 2 * G::M + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
   R eku = 0, ekv = 0;
-  x_pass<G, MODE == MODE_GRAD || MODE == MODE_AGRAD>(buf, ktab, twx, cl, eku, ekv, a.dir);
+  x_pass<G>(buf, ktab, twx, cl, eku, ekv);
   // Publish this CTA's partial <H>_n (or kinetic sums) into the slots of every
   // CTA of the cluster on the barrier that closes the x pass; afterwards each
   // CTA reads only its own shared memory, so no CTA has to outlive another.
@@ -477,69 +530,6 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       const C bp = scl(add(mulc(uu, lv), mulc(lu, vv)), R(-0.5) * dw);  // u conj(lap v) + conj(v) lap u
       out[g] = mk<C>(divj, R(0));
       out[G::M + g] = bp;
-    }
-    return;
-  } else if constexpr (MODE == MODE_GRAD) {
-    // buf holds d_dir u, d_dir v. Per site: tau_dir = w-|dv|^2 + w+|du|^2,
-    // j_dir = w- Im(v dv^*) - w+ Im(u du^*); stored as [tau, j_x] and
-    // [j_y, j_z] in components 0 and 1 of h0, tau summed over the directions.
-    const R wmn = R(a.wm[n]), wpn = R(a.wp[n]);
-    C* out = a.h0 + sbase;
-    for (int s = tid; s < G::NS; s += G::BT) {
-      const int g = gs0 + s;
-      const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
-      const C du = scl(buf[sidx(s)], sin_), dv = scl(buf[G::SLAB + sidx(s)], sin_);
-      const R tau = wmn * (dv.x * dv.x + dv.y * dv.y) + wpn * (du.x * du.x + du.y * du.y);
-      const R jd = wmn * (vv.y * dv.x - vv.x * dv.y) - wpn * (uu.y * du.x - uu.x * du.y);
-      C o0 = a.dir == 0 ? mk<C>(R(0), jd) : out[g];
-      o0.x += tau;
-      out[g] = o0;
-      if (a.dir == 1) out[G::M + g] = mk<C>(jd, R(0));
-      if (a.dir == 2) { C o1 = out[G::M + g]; o1.y = jd; out[G::M + g] = o1; }
-    }
-    return;
-  } else if constexpr (MODE == MODE_AGRAD) {
-    // buf holds d_dir u, d_dir v of the stored (unscaled) input
-    C* out = a.h0 + sbase;
-    R ep2 = 0, ec2 = 0;  // compensated partial of sum Re(phi^* G)
-    for (int s = tid; s < G::NS; s += G::BT) {
-      const int g = gs0 + s;
-      const fx4<R> av = a.av[g];
-      const R Ad = a.dir == 0 ? av.x : (a.dir == 1 ? av.y : av.z);
-      const C du = scl(buf[sidx(s)], sin_), dv = scl(buf[G::SLAB + sidx(s)], sin_);
-      C su, sv;
-      if (a.dir == 0) {
-        su = scl(scl(in[g], sin_), av.w);
-        sv = scl(scl(in[G::M + g], sin_), av.w);
-      } else {
-        su = out[g];
-        sv = out[G::M + g];
-      }
-      su = add(su, scl(du, Ad));
-      sv = add(sv, scl(dv, Ad));
-      if (a.dir == 2) {
-        su = mul_mi(su);
-        sv = mul_mi(sv);
-        const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
-        const R t = (uu.x * su.x + uu.y * su.y + vv.x * sv.x + vv.y * sv.y) - ec2;
-        const R ns = ep2 + t;
-        ec2 = (ns - ep2) - t;
-        ep2 = ns;
-      }
-      out[g] = su;
-      out[G::M + g] = sv;
-    }
-    if (a.dir == 2) {
-      double v = double(ep2);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((tid & 31) == 0) red[G::RED_WB + (tid >> 5)] = v;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
-        a.ecur[size_t(n) * 16 + rank] = t;
-      }
     }
     return;
   } else {
@@ -663,6 +653,120 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   }
 }
 
+// MODE_GRAD / MODE_AGRAD for one state: derivatives along z, y, x in turn,
+// each from a fresh load of the input slab, each followed by its sweep.
+template <class G, int MODE>
+__device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, const int n, const int ncl) {
+  using C = typename G::C;
+  using R = typename G::R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* buf = reinterpret_cast<C*>(smem);
+  R* ktab = reinterpret_cast<R*>(buf + 2 * G::SLAB);
+  C* tws = reinterpret_cast<C*>(ktab + 2 * (G::NX + G::NY + G::NZ));
+  double* red = reinterpret_cast<double*>(tws + (G::NX + G::NY + G::NZ));
+  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = cl.block_rank();
+  const int tid = threadIdx.x;
+  const int gs0 = rank * G::NS;
+  auto sidx = [](int s) { return (s / G::NZ) * G::ZP + (s % G::NZ); };
+  const size_t sbase = size_t(n) * 2 * G::M;
+  const C* in = a.phi + sbase;
+  C* out = a.h0 + sbase;
+  const R sin_ = R(a.sc_in[n]);
+  R wmn = 0, wpn = 0;
+  if constexpr (MODE == MODE_GRAD) {
+    wmn = R(a.wm[n]);
+    wpn = R(a.wp[n]);
+  }
+  if (tid < 2 && n + ncl < a.nstates)
+    prefetch_l2(a.phi + size_t(n + ncl) * 2 * G::M + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
+  R ep = 0, ec = 0;  // AGRAD: compensated partial of sum Re(phi^* G)
+#pragma unroll 1
+  for (int d = 2; d >= 0; --d) {
+    if (d != 2) __syncthreads();  // the previous sweep has read the slab
+    for (int i = tid; i < 2 * G::NS; i += G::BT) {
+      const int comp = i / G::NS, s = i % G::NS;
+      cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (d == 2) {
+      local_deriv<G, 2>(buf, ktab, tws + G::NX + G::NY);
+    } else if (d == 1) {
+      local_deriv<G, 1>(buf, ktab, tws + G::NX);
+    } else {
+      cl.sync();  // every CTA holds its fresh slab and has finished its y sweep
+      R e0 = 0, e1 = 0;
+      x_pass<G, true>(buf, ktab, tws, cl, e0, e1, R(double(G::M) / double(G::NX)));
+      cl.sync();  // every column is back in place
+    }
+    __syncthreads();
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const int g = gs0 + s;
+      const C du = scl(buf[sidx(s)], sin_), dv = scl(buf[G::SLAB + sidx(s)], sin_);
+      const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
+      if constexpr (MODE == MODE_GRAD) {
+        // tau_d = w-|d v|^2 + w+|d u|^2, j_d = w- Im(v d v^*) - w+ Im(u d u^*),
+        // stored as {tau, j_x}, {j_y, j_z}, tau summed over the directions
+        const R tau = wmn * (dv.x * dv.x + dv.y * dv.y) + wpn * (du.x * du.x + du.y * du.y);
+        const R jd = wmn * (vv.y * dv.x - vv.x * dv.y) - wpn * (uu.y * du.x - uu.x * du.y);
+        if (d == 2) {
+          out[g] = mk<C>(tau, R(0));
+          out[G::M + g] = mk<C>(R(0), jd);
+        } else if (d == 1) {
+          C o0 = out[g];
+          o0.x += tau;
+          out[g] = o0;
+          C o1 = out[G::M + g];
+          o1.x = jd;
+          out[G::M + g] = o1;
+        } else {
+          C o0 = out[g];
+          o0.x += tau;
+          o0.y = jd;
+          out[g] = o0;
+        }
+      } else {
+        const fx4<R> av = a.av[g];
+        const R Ad = d == 0 ? av.x : (d == 1 ? av.y : av.z);
+        C su, sv;
+        if (d == 2) {
+          su = scl(uu, av.w);
+          sv = scl(vv, av.w);
+        } else {
+          su = out[g];
+          sv = out[G::M + g];
+        }
+        su = add(su, scl(du, Ad));
+        sv = add(sv, scl(dv, Ad));
+        if (d == 0) {
+          su = mul_mi(su);
+          sv = mul_mi(sv);
+          const R t = (uu.x * su.x + uu.y * su.y + vv.x * sv.x + vv.y * sv.y) - ec;
+          const R ns = ep + t;
+          ec = (ns - ep) - t;
+          ep = ns;
+        }
+        out[g] = su;
+        out[G::M + g] = sv;
+      }
+    }
+  }
+  if constexpr (MODE == MODE_AGRAD) {
+    double v = double(ep);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[G::RED_WB + (tid >> 5)] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
+      a.ecur[size_t(n) * 16 + rank] = t;
+    }
+  }
+}
+
 // PERSIST = false: one cluster per state. PERSIST = true: a cluster handles
 // states n, n + ncl, ... (ncl clusters resident at once), prefetching the next
 // state's input slab into L2 during the current one. Between states the whole
@@ -689,11 +793,13 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_cons
 #pragma unroll 1
     for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl) {
       __syncthreads();
-      stage_state<G, MODE>(a, n, ncl);
+      if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, n, ncl);
+      else stage_state<G, MODE>(a, n, ncl);
     }
   } else {
     __syncthreads();
-    stage_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
+    if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
+    else stage_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
   }
 }
 

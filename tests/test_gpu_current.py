@@ -132,6 +132,41 @@ def test_both_launch_forms_match_oracle(W, monkeypatch, launch_form_case, persis
     assert rel(rho, rho_r) < TOL[1] and rel(nu, nu_r) < TOL[1]
 
 
+@pytest.fixture(scope="module")
+def mixed_variant_case():
+    """16^3 with 300 states (compiled variants with clusters of 1 and of 2
+    CTAs) and its oracle evolution."""
+    case = _case((16, 16, 16), (1, 1, 1), 300, seed=11)
+    sysm = oracle_system(case)
+    st = o.start(sysm, _ref_states(case, 1), 0.01, False)
+    st = o.evolve(sysm, st, 0.01, 6 - st.steps)
+    rho_r, nu_r = o.densities(st.phi, case.wm, case.wp)
+    return case, rho_r, nu_r, st.phi
+
+
+@pytest.mark.parametrize("vx,vy", [(0, 2), (2, 0)])
+def test_predictor_and_corrector_on_different_variants(W, monkeypatch, mixed_variant_case, vx, vy):
+    """The autotuner may put the two stages on launch variants with different
+    cluster sizes; the current term's <H>_n partials (one per CTA) must then
+    come from a launch on the consuming stage's variant."""
+    if max(vx, vy) >= W.lattice_variants(1, 16, 16, 16):
+        pytest.skip("not enough compiled variants")
+    monkeypatch.setenv("WSLDA_PERSIST", "0")
+    monkeypatch.setenv("WSLDA_VARIANT", str(vx))
+    monkeypatch.setenv("WSLDA_VARIANT_Y", str(vy))
+    case, rho_r, nu_r, phi_r = mixed_variant_case
+    ctx, box = gpu_context(case, 1)
+    ctx.start(False, 0.01)
+    ctx.step(0.01, 3)
+    rho, nu = ctx.get_densities(box)
+    phi = ctx.get_states(box)
+    desc = ctx.get_variant(box)
+    ctx.close()
+    errs = dict(rho=rel(rho, rho_r), nu=rel(nu, nu_r), states=rel(phi, phi_r))
+    print(desc, errs)
+    assert all(v < TOL[1] for v in errs.values()), errs
+
+
 def test_ab3am4_with_currents_matches_oracle(W):
     case = _case((12, 12, 12), (1, 1, 1), 400, seed=9)
     dt, nsteps = 0.01, 6
