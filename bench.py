@@ -271,7 +271,7 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     if prec == 1:
         peak, which = measured_peaks()
         achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
-        tb = profiled_traffic() if args.integrator == "AB4AM5" else None
+        tb = profiled_traffic() if args.integrator == "AB4AM5" and args.A == 1.0 else None  # captured on A = 1
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if tb is None else tb * per_launch,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
