@@ -255,7 +255,8 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     launches = ctx.launch_count() - l0
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
-    kt = {k: ctx.get_kernel_time(k) for k in ("stage_x", "stage_y", "density", "potentials")}
+    # "aux": the current-term passes of A != 1 (nothing in the A = 1 step)
+    kt = {k: ctx.get_kernel_time(k) for k in ("stage_x", "stage_y", "density", "potentials", "aux")}
     ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
         torch.distributed.barrier()

@@ -359,8 +359,10 @@ wslda_status wslda_net_symmetrize(const float* y, int64_t nfields, int nx, int n
 
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
  * the context's stream and its duration is added to the kernel's total.
- * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction,
- * 3 potentials, 4 start-up / diagnostics. */
+ * kind: 0 stage X (predictor), 1 stage Y (corrector), 2 density reduction
+ * (with A != 1 also the per-stage current: derivative launch and sum over
+ * states), 3 potentials, 4 start-up / diagnostics and, with A != 1, the
+ * current-term launches that precede every application of H. */
 wslda_status wslda_set_profiling(wslda_ctx* ctx, int enable);
 wslda_status wslda_get_kernel_time(wslda_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 
