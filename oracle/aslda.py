@@ -29,8 +29,9 @@ normal-state energies of the unpolarised (xi_N = 2^(2/3) 0.357) and fully
 polarised (0.357 + 0.642) uniform gas; Eq. kinop-alpha equals
 -1/2 sum_d d_d (alpha d_d f) for band-limited alpha and f; at p = 0 the
 imbalanced formulation with each state's time-reversed partner reproduces the
-spin-symmetric A = 1.094 oracle (densities, potentials, f); and the energy of
-a Galilean boost changes by q.P + N q^2 / 2 with p != 0.
+spin-symmetric A = 1.094 oracle (densities, potentials, f, and AB4AM5
+evolution); and the energy of a Galilean boost changes by q.P + N q^2 / 2
+with p != 0.
 """
 from __future__ import annotations
 
