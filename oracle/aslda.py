@@ -264,6 +264,45 @@ def start_stationary(sys: ImbalancedSystem, phi0) -> t.ABMHistory:
     return t.ABMHistory(phi=phi, f=[sys.f(phi), z, z.copy(), z.copy()])
 
 
+def taylor_series(phi0, F: Fields, shift, h: float, r: int, lat: t.Lattice):
+    """sum_{k=0}^{r} (-i h)^k / k! [H - shift]^k phi0 (Eq. Taylor-exp), term by term."""
+    out = phi0.copy()
+    term = phi0
+    for k in range(1, r + 1):
+        term = apply_H(term, F, lat) - shift[:, None, None] * term
+        term = (-1j * h / k) * term
+        out = out + term
+    return out
+
+
+def taylor_step(sys: ImbalancedSystem, phi, dt: float, r: int = 5):
+    """The predictor-corrector Taylor step of Sec. 3.3 with readings T1, T2:
+    H at t, the midpoint state, H at the midpoint, the state at t + dt."""
+    lat = sys.lat
+    F0 = sys.fields(phi)
+    s0 = t.expectation(phi, apply_H(phi, F0, lat), lat)
+    mid = t.normalize(taylor_series(phi, F0, s0, 0.5 * dt, r, lat), lat)
+    Fm = sys.fields(mid)
+    s1 = t.expectation(phi, apply_H(phi, Fm, lat), lat)
+    return t.normalize(taylor_series(phi, Fm, s1, dt, r, lat), lat)
+
+
+def start(sys: ImbalancedSystem, phi0, dt: float, stationary: bool, scheme: str = "AB4AM5", r: int = 5):
+    """Start-up for an ABpAMq scheme: stationary (reading S1) or p - 1 Taylor
+    steps (readings T2, T3), with the history ordered newest first."""
+    if stationary:
+        return start_stationary(sys, phi0)
+    p = len(t.SCHEMES[scheme][0])
+    phi = t.normalize(phi0, sys.lat)
+    if sys.lam is None:
+        sys.init_regulator(phi)
+    hist = [sys.f(phi)]
+    for _ in range(p - 1):
+        phi = taylor_step(sys, phi, dt, r)
+        hist.insert(0, sys.f(phi))
+    return t.ABMHistory(phi=phi, f=hist, t=(p - 1) * dt, steps=p - 1)
+
+
 def evolve(sys: ImbalancedSystem, st: t.ABMHistory, dt: float, nsteps: int, scheme: str = "AB4AM5"):
     for _ in range(nsteps):
         st = t.abm_step(sys, st, dt, scheme)
