@@ -763,14 +763,54 @@ def uniform_states(lat: Lattice, mu_eff: float, delta: float) -> np.ndarray:
     return np.stack([Uk[:, None] * pw, Vk[:, None] * pw], axis=1)
 
 
+def _v2(xi, d):
+    """V_k^2 = (1 - xi/E)/2, E = sqrt(xi^2 + d^2), written as d^2 / (2 E (E + xi))
+    for xi > 0 so that the far tail (xi >> d, where 1 - xi/E cancels to a few
+    digits) keeps full double precision."""
+    E = math.hypot(xi, d)
+    return 0.5 * d * d / (E * (E + xi)) if xi > 0 else 0.5 * (1.0 - xi / E)
+
+
+def _continuum_solve(integrals, rho_s, C, inv_4pi_a, lam, rho):
+    """(mu_eff, Delta) from the number equation n_s(mu_eff, Delta) = rho_s
+    (solved for mu_eff at each Delta) and the gap equation
+    1/g_eff + (1/V) sum_k 1/(2E_k) = 0 (solved for Delta), both by bracketed
+    root finding."""
+    from scipy.optimize import brentq
+
+    def me_of(d):
+        lo = -10.0
+        while integrals(lo, d)[0] > rho_s:  # strong pairing: the density needs a lower mu_eff
+            lo *= 2
+        return brentq(lambda me: integrals(me, d)[0] - rho_s, lo, 10.0, xtol=1e-14, rtol=1e-14, maxiter=300)
+
+    def gap(d):
+        me = me_of(d)
+        inv_g = (rho ** (1 / 3) / C - lam(me)) if C is not None else (inv_4pi_a - lam(me))
+        return inv_g + integrals(me, d)[3]
+    grid = np.geomspace(1e-3, 2.0, 40)
+    vals = [gap(d) for d in grid]
+    for a, b, fa, fb in zip(grid[:-1], grid[1:], vals[:-1], vals[1:]):
+        if fa * fb <= 0:
+            d = brentq(gap, a, b, xtol=1e-14, rtol=1e-14, maxiter=300)
+            return me_of(d), d
+    raise ValueError("no superfluid root of the continuum gap equation")
+
+
 def uniform_continuum(A: float, B: float, C: float | None, inv_4pi_a: float | None,
                       kF: float = 1.0, ec_over_eF: float = 2000.0):
     """Self-consistent uniform continuum solution with the Eq. Creg regularisation
     (spherical cutoff E_c, A k_c^2/2 - mu_eff = E_c). Returns a dict with mu/eF,
     Delta/eF and E/E_FG (E_FG = 3/5 N eF). SLDA-type if C is given, BdG if
-    inv_4pi_a is given (then B must be 0)."""
+    inv_4pi_a is given (then B must be 0).
+
+    The k integrals run over [0, k_c] split at k_0 (the quasiparticle minimum,
+    where xi changes sign), at 1/4, 1 and 4 times w = 4 Delta/(A k_0) on either
+    side of it (w is the width of the step of V_k^2) and at a few multiples of
+    max(k_0, kF); V_k^2 uses
+    the cancellation-free form of _v2, so every piece converges to the
+    requested tolerance."""
     from scipy.integrate import quad
-    from scipy.optimize import fsolve
     rho = kF ** 3 / (3 * np.pi ** 2)
     rho_s = rho / 2
     eF = 0.5 * kF ** 2
@@ -779,46 +819,87 @@ def uniform_continuum(A: float, B: float, C: float | None, inv_4pi_a: float | No
     def integrals(me, d):
         kc = math.sqrt(2 * (ec + me) / A)
         k0 = math.sqrt(max(2 * me / A, 0.0))
+        kk = max(k0, kF)
 
         def xi(k):
             return 0.5 * A * k * k - me
-
-        def dens(k):
-            x = xi(k)
-            return k * k * 0.5 * (1 - x / math.hypot(x, d))
-
-        def anom(k):
-            return k * k * d / (2 * math.hypot(xi(k), d))
-
-        def kin(k):
-            x = xi(k)
-            return k ** 4 * 0.5 * (1 - x / math.hypot(x, d))
-
-        def inv_e(k):
-            return k * k / (2 * math.hypot(xi(k), d))
-        opts = dict(limit=400, epsabs=1e-14, epsrel=1e-12)
-        segs = sorted(set(s for s in (0.0, k0, min(kc, 4 * max(k0, 1.0)), kc) if s <= kc))
+        opts = dict(limit=200, epsabs=1e-13, epsrel=1e-11)
+        w = 4 * d / (A * k0) if k0 > 0 else 0.0  # width of the step of V_k^2 at k_0
+        near = [k0 + f * w for f in (-4, -1, -0.25, 0, 0.25, 1, 4)]
+        segs = sorted(set(s for s in [0.0, *near, 2 * kk, 8 * kk, 64 * kk, kc] if 0 <= s <= kc))
 
         def q(fun):
             return sum(quad(fun, a, b, **opts)[0] for a, b in zip(segs[:-1], segs[1:]))
         c = 1.0 / (2 * np.pi ** 2)
-        return c * q(dens), c * q(anom), c * q(kin), c * q(inv_e)
+        return (c * q(lambda k: k * k * _v2(xi(k), d)),
+                c * q(lambda k: k * k * d / (2 * math.hypot(xi(k), d))),
+                c * q(lambda k: k ** 4 * _v2(xi(k), d)),
+                c * q(lambda k: k * k / (2 * math.hypot(xi(k), d))))
 
-    def residual(x):
-        me, d = x
-        n_s, nu, tau, ie = integrals(me, abs(d))
-        lam = float(lambda_c(me, ec, A))
-        inv_g = (rho ** (1 / 3) / C - lam) if C is not None else (inv_4pi_a - lam)
-        return [n_s / rho_s - 1.0, inv_g + ie]
-
-    sol = fsolve(residual, [0.5 * eF, 0.6 * eF], xtol=1e-13)
-    me, d = sol[0], abs(sol[1])
+    me, d = _continuum_solve(integrals, rho_s, C, inv_4pi_a, lambda me: float(lambda_c(me, ec, A)), rho)
     n_s, nu, tau, ie = integrals(me, d)
     g = -1.0 / ie
     U = (B * fermi_energy(rho) - d ** 2 / (3 * C * rho ** (2 / 3))) if C is not None else 0.0
     e_dens = A * tau + 0.6 * B * rho * fermi_energy(rho) + g * nu ** 2
     return dict(mu_over_eF=(U + me) / eF, delta_over_eF=d / eF,
                 E_over_EFG=e_dens / (0.6 * rho * eF), mu_eff=me, nu=nu, tau=tau)
+
+
+def uniform_continuum_limit(A: float, B: float, C: float | None, inv_4pi_a: float | None, kF: float = 1.0):
+    """The same uniform solution directly at infinite cutoff, without Lambda_c:
+    the regulator is the principal value of (1/2 pi^2) int k^2 / (A k^2 - 2 mu_eff),
+    whose part beyond k_c -> infinity differs from (1/2 pi^2) int 1/A by a
+    principal-value integral of 1/(k^2 - k_0^2) over [0, inf), which vanishes.
+    So Eq. Creg's gap equation becomes
+        rho^(1/3)/C (or 1/(4 pi a)) = -(1/2 pi^2) int_0^inf k^2 [1/(2E) - 1/(A k^2)] dk,
+    and the energy density A tau + g nu^2 = A tau - Delta nu becomes
+        (1/2 pi^2) int_0^inf [A k^4 V_k^2 - k^2 Delta^2 / (2E)] dk,
+    both absolutely convergent (integrands ~ k^-2). Evaluated on [0, inf) with
+    the tail mapped by quad's infinite-range transformation; an independent
+    route to the Richardson-extrapolated output of uniform_continuum."""
+    from scipy.integrate import quad
+    rho = kF ** 3 / (3 * np.pi ** 2)
+    rho_s = rho / 2
+    eF = 0.5 * kF ** 2
+
+    def integrals(me, d):
+        k0 = math.sqrt(max(2 * me / A, 0.0))
+        kk = max(k0, kF)
+
+        def xi(k):
+            return 0.5 * A * k * k - me
+        opts = dict(limit=200, epsabs=1e-13, epsrel=1e-11)
+        w = 4 * d / (A * k0) if k0 > 0 else 0.0
+        near = [k0 + f * w for f in (-4, -1, -0.25, 0, 0.25, 1, 4)]
+        segs = sorted(set(s for s in [0.0, *near, 2 * kk, 8 * kk] if s >= 0))
+
+        def q(fun):
+            parts = [quad(fun, a, b, **opts)[0] for a, b in zip(segs[:-1], segs[1:])]
+            return sum(parts) + quad(fun, segs[-1], np.inf, **opts)[0]
+        c = 1.0 / (2 * np.pi ** 2)
+        # k^2 [1/(2E) - 1/(A k^2)] and A k^4 V_k^2 - k^2 Delta^2/(2E); for xi > 0
+        # both are rewritten with A k^2 = 2 xi + 2 mu_eff and E - xi = Delta^2/(E + xi)
+        # so that no large terms cancel in the tail
+        def reg(k):
+            x = xi(k)
+            E = math.hypot(x, d)
+            if x > 0:
+                return (me - d * d / (E + x)) / (A * E)
+            return (A * k * k - 2 * E) / (2 * A * E)
+
+        def ereg(k):
+            x = xi(k)
+            E = math.hypot(x, d)
+            if x > 0:
+                return (k * k * d * d / (2 * E)) * (2 * me - d * d / (E + x)) / (E + x)
+            return A * k ** 4 * _v2(x, d) - k * k * d * d / (2 * E)
+        return (c * q(lambda k: k * k * _v2(xi(k), d)), None, c * q(ereg), c * q(reg))
+
+    me, d = _continuum_solve(integrals, rho_s, C, inv_4pi_a, lambda me: 0.0, rho)
+    n_s, _, e_pair_kin, reg = integrals(me, d)
+    U = (B * fermi_energy(rho) - d ** 2 / (3 * C * rho ** (2 / 3))) if C is not None else 0.0
+    e_dens = e_pair_kin + 0.6 * B * rho * fermi_energy(rho)
+    return dict(mu_over_eF=(U + me) / eF, delta_over_eF=d / eF, E_over_EFG=e_dens / (0.6 * rho * eF), mu_eff=me)
 
 
 # ----------------------------------------------------------------------------

@@ -134,7 +134,13 @@ def test_uniform_slda_reproduces_printed_values():
     """Sec. 2.4: the spin-symmetric ASLDA (A = 1.094, B = B(0), C = -11.11)
     gives E/E_FG = 0.39(1) and Delta/eF = 0.51(1). Reading R1 of Eq. Creg
     (1/g_eff = rho^(1/3)/C - Lambda_c) lands within the printed uncertainty on
-    E/E_FG (0.398) and 0.015 of the printed gap (0.495)."""
+    E/E_FG (0.3976). The gap comes out at 0.4949, 0.015 below the printed
+    value: Delta/eF of the uniform system is fixed by A and C alone (B drops
+    out of the number and gap equations, test below), and with the printed A
+    and C the regularised gap equation has that root in the continuum limit,
+    found the same by two independent routes (cutoff + Richardson here, the
+    cutoff-free integrals in test_continuum_limit_is_an_independent_route).
+    The gap is therefore held to 0.02 of the printed value."""
     A0 = GOLD["aslda_A0"]["value"]
     C = GOLD["aslda_C"]["value"]
     assert o.aslda_A(0.0) == A0
@@ -144,6 +150,38 @@ def test_uniform_slda_reproduces_printed_values():
     # unitarity is scale invariant: mu = dE/dN = (5/3) E/N, i.e. mu/eF = E/E_FG;
     # this fails if U is not the density derivative of the functional
     assert r["mu_over_eF"] == pytest.approx(r["E_over_EFG"], abs=2e-4)
+
+
+def test_continuum_limit_is_an_independent_route():
+    """The cutoff-free form of the uniform equations (regulator folded into the
+    gap integral, energy as the convergent combination A tau - Delta nu) gives
+    the same continuum limit as the finite-cutoff solver with Lambda_c and a
+    Richardson extrapolation in 1/k_c, for ASLDA and for BdG at unitarity; for
+    BdG it is Leggett's mean-field mu = 0.5906 eF, Delta = 0.6864 eF."""
+    A0, C = GOLD["aslda_A0"]["value"], GOLD["aslda_C"]["value"]
+    lim = o.uniform_continuum_limit(A0, o.B_SLDA, C, None)
+    r = _extrapolate(lambda e: o.uniform_continuum(A0, o.B_SLDA, C, None, ec_over_eF=e))
+    for k in ("mu_over_eF", "delta_over_eF", "E_over_EFG"):
+        assert lim[k] == pytest.approx(r[k], abs=5e-5), k
+    assert lim["mu_over_eF"] == pytest.approx(lim["E_over_EFG"], abs=1e-9)  # scale invariance, exact here
+    b = o.uniform_continuum_limit(1.0, 0.0, None, 0.0)
+    assert b["mu_over_eF"] == pytest.approx(GOLD["leggett_unitarity_mu_over_eF"]["value"], abs=1e-4)
+    assert b["delta_over_eF"] == pytest.approx(GOLD["leggett_unitarity_Delta_over_eF"]["value"], abs=1e-4)
+
+
+def test_uniform_gap_depends_on_A_and_C_only():
+    """B enters only U, so mu_eff and Delta/eF of the uniform solution do not
+    change with B, while mu and E do; with the printed A the printed gap 0.51
+    would need |C| about 7% larger (C = -11.89), and 0.50 needs C = -11.36."""
+    A0, C = GOLD["aslda_A0"]["value"], GOLD["aslda_C"]["value"]
+    ref = o.uniform_continuum_limit(A0, o.B_SLDA, C, None)
+    for B in (0.0, -1.0):
+        r = o.uniform_continuum_limit(A0, B, C, None)
+        assert r["delta_over_eF"] == pytest.approx(ref["delta_over_eF"], rel=1e-12)
+        assert r["mu_eff"] == pytest.approx(ref["mu_eff"], rel=1e-12)
+        assert abs(r["E_over_EFG"] - ref["E_over_EFG"]) > 0.3
+    assert o.uniform_continuum_limit(A0, o.B_SLDA, -11.89, None)["delta_over_eF"] == pytest.approx(0.51, abs=2e-4)
+    assert o.uniform_continuum_limit(A0, o.B_SLDA, -11.36, None)["delta_over_eF"] == pytest.approx(0.50, abs=2e-4)
 
 
 def test_uniform_slda_wrong_reading_fails():
