@@ -3,17 +3,30 @@
 
 Metric: state-site updates per second = states x lattice sites x steps / time,
 one update being one quasiparticle state at one lattice site advanced by one
-full predictor + corrector step. The workload is a 32^3 periodic lattice in a
-harmonic trap V = 1/2 w^2 r^2 (w = 0.05) with 32768 quasiparticle states.
+full predictor + corrector step.
 
-Default run (N = 1): the mixed-precision step (complex float states and FFTs,
-double reductions) is timed with CUDA events on the library's stream over K
-steps after W warm-up steps; the plain FP64 step on the same states is timed
-the same way and reported beside it, with the relative density difference
-between the two. Per-kernel CUDA events give the stage-X kernel's duration for
-the roofline. The end-to-end number goes through the public API with pinned
-host buffers: load_states (host -> device), start, K steps each followed by a
-density read (device -> host) and a final get_states (device -> host).
+Default run (N = 1):
+  * value: the mixed-precision step (complex float states and FFTs, double
+    reductions) on the elongated-trap workload: a 24 x 24 x 96 lattice in a
+    harmonic trap w = (0.064, 0.064, 0.016), all 55296 quasiparticle states,
+    a vortex line imprinted on Delta, Taylor start; K steps timed with CUDA
+    events on the library's stream after W warm-up steps. Per-kernel CUDA
+    events give the stage-X kernel's duration for its roofline; the whole
+    step's algorithmic traffic (10 state passes) gives the step roofline.
+  * fp64: the plain FP64 step on the 32^3 trap (w = 0.05, 32768 states),
+    against the FP64 FMA rate measured on the same GPU in the same run.
+  * batched: 64 independent cubic boxes 12^3..24^3 (BdG, all states), four
+    steps per CUDA graph, boxes on forked streams.
+  * mixed_vs_oracle: the mixed path against the CPU oracle on a bounded
+    sample of the main workload (same lattice, trap and vortex, a subset of
+    the states as the whole system), after 100 steps, with the energy drift.
+  * energy_drift: drift of E_tot - mu N over the timed run.
+  * cufft: the kinetic-term transforms of one stage (forward 3D FFT of u and
+    v, multiply by k^2/2, inverse) done with cuFFT (through torch.fft) on the
+    main workload, timed as a comparison only.
+  * e2e: the mixed job end to end through the ABI with pinned host buffers:
+    load_states_f32 (host -> device), start, K steps each followed by a
+    density read (device -> host) and a final get_states_f32.
 `--impl reference` times the CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -36,8 +49,16 @@ sys.path.insert(0, ROOT)
 METRIC = "TD step state-site updates/s, mixed FP32 vs plain FP64 at ≤1e-5 rel density err"
 UNIT = "state-site updates/s"
 FALLBACK_HBM_GBS = 6400.0
-FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate (SM count x FP64 units x clock)
+FP64_NOMINAL_TFLOPS = 1.25   # nominal B300 FP64 rate, used only if the measurement fails
 RHO_SIGMA = 1.0 / (6 * math.pi ** 2)
+# workloads: (lattice, states, trap frequencies, vortex imprint)
+WORKLOADS = {
+    "elongated": dict(shape=(24, 24, 96), nstates=55296, omega=(0.064, 0.064, 0.016), vortex=True,
+                      text="24x24x96 elongated harmonic trap w=(0.064, 0.064, 0.016) with a vortex line "
+                           "imprinted on Delta, all 55296 quasiparticle states"),
+    "cube32": dict(shape=(32, 32, 32), nstates=32768, omega=0.05, vortex=False,
+                   text="32x32x32 periodic lattice, harmonic trap w=0.05, all 32768 quasiparticle states"),
+}
 
 
 def _omega(text):
@@ -51,17 +72,26 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--shape", default="32,32,32")
-    p.add_argument("--nstates", type=int, default=32768)
-    p.add_argument("--omega", type=_omega, default=0.05,
+    p.add_argument("--workload", default="elongated", choices=sorted(WORKLOADS),
+                   help="main (mixed) workload; --shape / --nstates / --omega override its fields")
+    p.add_argument("--fp64-workload", default="cube32", choices=sorted(WORKLOADS),
+                   help="workload of the plain FP64 arm")
+    p.add_argument("--shape", default=None)
+    p.add_argument("--nstates", type=int, default=None)
+    p.add_argument("--omega", type=_omega, default=None,
                    help="trap frequency, or wx,wy,wz for an anisotropic trap")
+    p.add_argument("--vortex", type=int, default=None, help="1/0: imprint a vortex line on Delta")
     p.add_argument("--dt", type=float, default=0.007)
     p.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--batched", action="store_true",
-                   help="also time the batched workload: 64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched workload (64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps)")
+    p.add_argument("--no-oracle-check", action="store_true", help="skip the mixed-vs-oracle sample")
+    p.add_argument("--oracle-states", type=int, default=32)
+    p.add_argument("--oracle-steps", type=int, default=100)
+    p.add_argument("--no-cufft", action="store_true")
     p.add_argument("--integrator", default="AB4AM5", choices=["AB4AM5", "AB3AM4", "AB5AM5"],
                    help="predictor-corrector scheme of Sec. 3.3 (AB4AM5 is Alg. 2)")
     p.add_argument("--init", default="quench", choices=["quench", "scf"],
@@ -159,18 +189,48 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ workloads
+def resolve(args, name):
+    """The workload `name` with the command-line overrides applied."""
+    w = dict(WORKLOADS[name])
+    if name == args.workload:
+        if args.shape:
+            w["shape"] = tuple(int(v) for v in args.shape.split(","))
+        if args.nstates:
+            w["nstates"] = args.nstates
+        if args.omega is not None:
+            w["omega"] = args.omega
+        if args.vortex is not None:
+            w["vortex"] = bool(args.vortex)
+        if args.shape or args.nstates or args.omega is not None or args.vortex is not None:
+            s = w["shape"]
+            w["text"] = (f"{s[0]}x{s[1]}x{s[2]} periodic lattice, harmonic trap w={w['omega']}"
+                         f"{', vortex line imprinted on Delta' if w['vortex'] else ''}, {w['nstates']} quasiparticle states")
+    return w
+
+
 # ------------------------------------------------------------------ GPU arms
-def make_box(W, prec, shape, nstates, omega, stream, scheme="AB4AM5", mu=None, A=1.0):
-    """A != 1: the SLDA functional with its current terms (same B, C, mu and
-    uniform seed as the A = 1 workload)."""
+def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0):
+    """A context with one box of the workload (SLDA with the uniform seed's
+    B, C, mu; A != 1 adds the current terms)."""
     from paper_2602_08982_b300 import inputs
+    shape = wl["shape"]
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(prec, stream=stream)
     ctx.set_integrator(scheme)
     box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"],
-                      mu=u["mu"] if mu is None else mu, A=A, nstates=nstates)
-    ctx.set_vext(box, inputs.harmonic_trap(shape, omega))
+                      mu=u["mu"] if mu is None else mu, A=A, nstates=wl["nstates"])
+    ctx.set_vext(box, inputs.harmonic_trap(shape, wl["omega"]))
     return ctx, box, u
+
+
+def fill_workload(W, ctx, box, u, wl):
+    """Uniform plane-wave BCS states of the lattice (Delta0 = 0.5 eF), with the
+    vortex phase imprinted on u when the workload has one (reading P2)."""
+    from paper_2602_08982_b300 import inputs
+    ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+    if wl["vortex"]:
+        ctx.imprint_phase(box, 0, inputs.vortex_phase(wl["shape"]))
 
 
 HISTORY_READS = {"AB3AM4": 2, "AB4AM5": 3, "AB5AM5": 4}
@@ -191,10 +251,17 @@ def stage_x_algorithmic(prec, shape, scheme="AB4AM5", cur=False):
     return bytes_per, flops_per
 
 
+def step_algorithmic_bytes(prec, scheme="AB4AM5"):
+    """State passes of a whole step per state-site: stage X (1 + D reads, 3
+    writes) and stage Y (2 reads, 1 write); AB4AM5: 10 passes, 160 B mixed."""
+    csize = 8 if prec == 1 else 16
+    return (1 + HISTORY_READS[scheme] + 3 + 3) * 2 * csize
+
+
 SCF_START = {}
 
 
-def scf_start(W, args, shape):
+def scf_start(W, args, wl):
     """Trapped start from a static self-consistent solve (Alg. 1) of the
     workload's SLDA system with a particle-number target (Eq. update-mu),
     modified Broyden mixing and single-precision leading iterations; the
@@ -202,11 +269,12 @@ def scf_start(W, args, shape):
     if "phi" in SCF_START:
         return SCF_START
     from paper_2602_08982_b300 import inputs
+    shape = wl["shape"]
     M = shape[0] * shape[1] * shape[2]
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(W.FP64)
     b = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=M)
-    ctx.set_vext(b, inputs.harmonic_trap(shape, args.omega))
+    ctx.set_vext(b, inputs.harmonic_trap(shape, wl["omega"]))
     t0 = time.perf_counter()
     res, _ = ctx.static_solve(b, np.full(M, u["U"]), np.full(M, u["delta"]), method="broyden", mixing=0.5,
                               eps_energy=1e-6, max_iters=args.scf_iters, n_target=args.scf_n, a_mu=0.5,
@@ -220,18 +288,17 @@ def scf_start(W, args, shape):
     return SCF_START
 
 
-def run_arm(W, torch, prec, args, shape, rank, world, dev):
+def run_arm(W, torch, prec, args, wl, rank, world, dev):
     stream = torch.cuda.current_stream()
+    shape, nstates = wl["shape"], wl["nstates"]
     if args.init == "scf":
-        start = scf_start(W, args, shape)
-        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
-                               mu=start["info"]["mu"], A=args.A)
+        start = scf_start(W, args, wl)
+        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, mu=start["info"]["mu"], A=args.A)
         ctx.load_states(box, start["phi"])
         ctx.start(True, args.dt)               # a static solution: stationary start
     else:
-        ctx, box, u = make_box(W, prec, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
-                               A=args.A)
-        ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, A=args.A)
+        fill_workload(W, ctx, box, u, wl)
         if args.friction:
             fa, fb, fg = (float(x) for x in args.friction.split(","))
             M = shape[0] * shape[1] * shape[2]
@@ -260,44 +327,64 @@ def run_arm(W, torch, prec, args, shape, rank, world, dev):
     ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
         torch.distributed.barrier()
+    de, dn = ctx.check_conservation(box, float("inf"), float("inf"))
+    _, steps_done = ctx.get_time()
     rho, nu = ctx.get_densities(box)
     ctx.close()
     M = shape[0] * shape[1] * shape[2]
-    units = float(args.nstates) * M * args.steps
+    units = float(nstates) * M * args.steps
     value = job_rate(units, world, ms * 1e-3)
     bx, fx = stage_x_algorithmic(prec, shape, args.integrator, args.A != 1.0)
     x_ms, x_n = kt["stage_x"]
     x_avg = x_ms / max(x_n, 1)
-    per_launch = float(args.nstates) * M
+    y_ms, y_n = kt["stage_y"]
+    y_avg = y_ms / max(y_n, 1)
+    per_launch = float(nstates) * M
+    hbm, which = measured_peaks()
     if prec == 1:
-        peak, which = measured_peaks()
         achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
         tb = profiled_traffic() if args.integrator == "AB4AM5" and args.A == 1.0 else None  # captured on A = 1
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None if tb is None else tb * per_launch,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
-                "peak_source": which, "algorithmic_bytes_per_state_site": bx}
+                "peak_source": which, "algorithmic_bytes_per_state_site": bx,
+                "stage_y": {"achieved": 48.0 * per_launch / (y_avg * 1e-3) / 1e9,
+                            "frac": 48.0 * per_launch / (y_avg * 1e-3) / 1e9 / hbm,
+                            "algorithmic_bytes_per_state_site": 48}}
     else:
+        try:
+            peak, src = W.measure_fp64_rate(5), "of measured (FP64 FMA microbenchmark on this GPU, this run)"
+        except W.WsldaError:
+            peak, src = FP64_NOMINAL_TFLOPS, "nominal FP64 rate (measurement failed)"
         achieved = fx * per_launch / (x_avg * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation), FP64",
-                "peak_source": "nominal FP64 rate", "algorithmic_flops_per_state_site": fx}
+                "peak_source": src, "algorithmic_flops_per_state_site": fx}
+    sb = step_algorithmic_bytes(prec, args.integrator)
+    step_gbs = sb * per_launch / (ms / args.steps * 1e-3) / 1e9
     share = {k: kt[k][0] / ms for k in kt}
     roof["launch_variant"] = variant
     return dict(value=value, ms_per_step=ms / args.steps, roofline=roof, clocks=ck, launches=launches,
-                kernel_ms=kt, kernel_share=share, rho=rho, nu=nu)
+                kernel_ms=kt, kernel_share=share, rho=rho, nu=nu,
+                step_roofline={"bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": step_gbs / hbm, "peak_source": which,
+                               "algorithmic_bytes_per_state_site": sb,
+                               "scope": "whole step: stage X + stage Y state passes (density and potential "
+                                        "kernels add traffic the algorithmic figure does not count)"},
+                energy_drift={"rel_e_tot_minus_mu_n": de, "rel_n": dn, "after_steps": steps_done,
+                              "since": "wslda_start (t = 0 states)"})
 
 
-def run_e2e(W, torch, args, shape, world):
+def run_e2e(W, torch, args, wl, world):
     """Mixed path end to end through the ABI with pinned host buffers: the
     states travel as complex64, the precision the mixed path stores them in."""
     stream = torch.cuda.current_stream()
-    ctx, box, u = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
-                           A=args.A)
-    ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+    shape, nstates = wl["shape"], wl["nstates"]
+    ctx, box, u = make_box(W, W.MIXED, wl, stream.cuda_stream, args.integrator, A=args.A)
+    fill_workload(W, ctx, box, u, wl)
     M = shape[0] * shape[1] * shape[2]
-    host = torch.empty((args.nstates, 2, M), dtype=torch.complex64, pin_memory=True)
+    host = torch.empty((nstates, 2, M), dtype=torch.complex64, pin_memory=True)
     host_np = host.numpy()
     ctx.get_states_f32(box, host_np)  # untimed: the job's input now lives in pinned host memory
     ctx.close()
@@ -305,8 +392,7 @@ def run_e2e(W, torch, args, shape, world):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
-    ctx, box, _ = make_box(W, W.MIXED, shape, args.nstates, args.omega, stream.cuda_stream, args.integrator,
-                           A=args.A)
+    ctx, box, _ = make_box(W, W.MIXED, wl, stream.cuda_stream, args.integrator, A=args.A)
     ctx.load_states_f32(box, host_np)
     ctx.start(False, args.dt)
     for _ in range(args.steps):
@@ -317,7 +403,7 @@ def run_e2e(W, torch, args, shape, world):
     sec = time.perf_counter() - t0
     ctx.close()
     sec = max_over_ranks(sec, world, "cuda")
-    units = float(args.nstates) * M * args.steps
+    units = float(nstates) * M * args.steps
     nbytes = host.numel() * 8
     del host
     return {"value": job_rate(units, world, sec), "unit": UNIT,
@@ -383,12 +469,93 @@ def run_batched(W, torch, args):
                               "algorithmic_bytes_per_state_site": 160, "scope": "whole step (10 state passes)"}}
 
 
+def run_cufft(torch, wl, args, our_stage_ms):
+    """The kinetic-term transforms of one stage on the main workload with
+    cuFFT (torch.fft): for chunks of states, forward 3D FFT of u and v,
+    multiplication by k^2/2 (1/M folded in), inverse 3D FFT. A library
+    comparison only; the product path never calls it."""
+    shape, nstates = wl["shape"], wl["nstates"]
+    M = shape[0] * shape[1] * shape[2]
+    chunk = min(nstates, 2048)
+    dev = torch.device("cuda")
+    ks = [torch.fft.fftfreq(n, d=1.0 / (2 * math.pi), device=dev, dtype=torch.float64) for n in shape]
+    k2 = (ks[0][:, None, None] ** 2 + ks[1][None, :, None] ** 2 + ks[2][None, None, :] ** 2)
+    sym = (0.5 * k2).to(torch.float32)
+    x = torch.randn((chunk, 2) + tuple(shape), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def once():
+        y = torch.fft.fftn(x, dim=(-3, -2, -1))
+        y.mul_(sym)
+        return torch.fft.ifftn(y, dim=(-3, -2, -1))
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_chunk = e0.elapsed_time(e1) / reps
+    stage_ms = per_chunk * nstates / chunk
+    del x
+    torch.cuda.empty_cache()
+    return {"ms_per_stage": stage_ms, "chunk_states": chunk,
+            "what": "forward 3D FFT of u and v, times k^2/2, inverse 3D FFT (cuFFT plans via torch.fft, "
+                    "complex64), states in chunks; the transform work of one stage, nothing else",
+            "our_stage_x_ms": our_stage_ms[0], "our_stage_y_ms": our_stage_ms[1],
+            "our_stage_y_over_cufft_transforms": our_stage_ms[1] / stage_ms}
+
+
+def run_oracle_check(W, torch, args, wl):
+    """The mixed path against the FP64 CPU oracle on a bounded sample of the
+    main workload: the same lattice, trap and vortex imprint with a seeded
+    subset of the uniform plane-wave states as the whole system, both started
+    from the same double states (Taylor start), args.oracle_steps steps in all.
+    Errors are N1's: max-norm relative differences of rho and nu, and of the
+    energy; the drift is that of E_tot - mu N from t = 0."""
+    n, nsteps = args.oracle_states, args.oracle_steps
+    t0 = time.perf_counter()
+    o, sysm, phi, lat = oracle_sample(wl, n, args.A)
+    sysm.init_regulator(phi)
+    e0 = sysm.energy(phi)
+    st = o.start(sysm, phi, args.dt, False)
+    st = o.evolve(sysm, st, args.dt, nsteps - st.steps)
+    rho_r, nu_r = o.densities(st.phi, np.ones(n), np.zeros(n))
+    e_r = sysm.energy(st.phi)
+    cpu_sec = time.perf_counter() - t0
+    ctx = W.Context(W.MIXED, stream=torch.cuda.current_stream().cuda_stream)
+    box = ctx.add_box(lat.shape, kind=W.SLDA if args.A != 1.0 else W.SLDA_A1, B=sysm.fn.B, C=sysm.fn.C,
+                      mu=sysm.fn.mu, A=args.A, nstates=n)
+    ctx.set_vext(box, sysm.vext)
+    ctx.load_states(box, phi)
+    ctx.start(False, args.dt)
+    ctx.step(args.dt, nsteps - ctx.get_time()[1])
+    rho, nu = ctx.get_densities(box)
+    e = ctx.get_energy(box)
+    ctx.close()
+    mu = sysm.fn.mu
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+    ec0 = e0["e_total"] - mu * e0["n_part"]
+    return {"rel_err_rho": rel(rho, rho_r), "rel_err_nu": rel(nu, nu_r),
+            "rel_err_e_total": abs(e["e_total"] - e_r["e_total"]) / abs(e_r["e_total"]),
+            "energy_drift_mixed": abs(e["e_total"] - mu * e["n_part"] - ec0) / abs(ec0),
+            "energy_drift_oracle": abs(e_r["e_total"] - mu * e_r["n_part"] - ec0) / abs(ec0),
+            "after_steps": nsteps, "states": n, "tolerance": 1e-5, "oracle_seconds": cpu_sec,
+            "sample": f"{n} seeded plane-wave states of the {lat.nx}x{lat.ny}x{lat.nz} workload lattice (same trap"
+                      f"{' and vortex' if wl['vortex'] else ''}) as the whole system, Taylor start, dt={args.dt}"}
+
+
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(shape, omega, n, A=1.0):
+def oracle_sample(wl, n, A=1.0):
     """CPU-oracle system for the workload's lattice and trap, with n of its
-    uniform plane-wave states (seeded choice of momenta)."""
+    uniform plane-wave states (seeded choice of momenta), vortex imprinted on
+    u when the workload has one."""
     from oracle import tdslda as o
     from paper_2602_08982_b300 import inputs
+    shape = wl["shape"]
     lat = o.Lattice(*shape)
     seed = o.uniform_slda_seed(lat, 0.25, RHO_SIGMA)
     fn = o.Functional("slda", B=o.B_SLDA, C=seed.C, mu=seed.mu, A=float(A))
@@ -402,7 +569,9 @@ def oracle_sample(shape, omega, n, A=1.0):
     pw = np.einsum("ni,nj,nk->nijk", *e).reshape(n, lat.M) / np.sqrt(lat.volume)
     Uk, Vk, _ = o.bcs_amplitudes(0.5 * (kx[ix] ** 2 + ky[iy] ** 2 + kz[iz] ** 2) - seed.mu_eff, seed.delta)
     phi = np.stack([Uk[:, None] * pw, Vk[:, None] * pw], axis=1)
-    return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, omega)), phi, lat
+    if wl["vortex"]:
+        phi[:, 0, :] *= inputs.vortex_phase(shape)[None, :]
+    return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, wl["omega"])), phi, lat
 
 
 def oracle_stepper(o, scheme):
@@ -413,14 +582,15 @@ def oracle_stepper(o, scheme):
             (lambda sysm, st, dt: o.abm_step(sysm, st, dt, scheme)))
 
 
-def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
+def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
     """The oracle as it stands, on a bounded sample of the workload: the same
     lattice and trap with a subset of the uniform plane-wave states, timed over
     whole ABM steps after a stationary start."""
+    shape = wl["shape"]
     max_states = min(max_states, shape[0] * shape[1] * shape[2])
     n = min(64, max_states)
     while True:
-        o, sysm, phi, lat = oracle_sample(shape, omega, n, A)
+        o, sysm, phi, lat = oracle_sample(wl, n, A)
         start, step = oracle_stepper(o, scheme)
         st = start(sysm, phi, dt)
         t0 = time.perf_counter()
@@ -439,7 +609,7 @@ def cpu_oracle_rate(shape, omega, dt, seconds, max_states=2048, scheme="AB4AM5",
                       f"steps after a stationary start, {sec:.1f} s"}
 
 
-def reference_arm(args, shape):
+def reference_arm(args, wl):
     rank, world, _ = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -449,8 +619,8 @@ def reference_arm(args, shape):
             return
     # each step: one oracle step of the scheme over a bounded sample of the
     # states, sized so that one step takes about a second
-    n = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds / 4, scheme=args.integrator, A=args.A)["n"]
-    o, sysm, phi, lat = oracle_sample(shape, args.omega, n, args.A)
+    n = cpu_oracle_rate(wl, args.dt, args.cpu_seconds / 4, scheme=args.integrator, A=args.A)["n"]
+    o, sysm, phi, lat = oracle_sample(wl, n, args.A)
     start, step = oracle_stepper(o, args.integrator)
     st = start(sysm, phi, args.dt)
     for _ in range(args.warmup):
@@ -463,7 +633,7 @@ def reference_arm(args, shape):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": workload_config(args, shape, "fp64 oracle (CPU)"),
+            "config": workload_config(args, wl, "fp64 oracle (CPU)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{n} states of the workload per step, {args.steps} steps, {sec:.1f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -473,24 +643,26 @@ def reference_arm(args, shape):
         dist.barrier()
 
 
-def workload_config(args, shape, precision):
-    return {"workload": f"TDSLDA {args.integrator} step, {shape[0]}x{shape[1]}x{shape[2]} periodic lattice, harmonic trap "
-                        f"w={args.omega}, {args.nstates} quasiparticle states",
-            "lattice": list(shape), "nstates": args.nstates, "trap_omega": args.omega, "dt": args.dt,
+def workload_config(args, wl, precision):
+    shape = wl["shape"]
+    return {"workload": f"TDSLDA {args.integrator} step, {wl['text']}",
+            "lattice": list(shape), "nstates": wl["nstates"], "trap_omega": wl["omega"], "vortex": wl["vortex"],
+            "dt": args.dt,
             "functional": (f"SLDA with current terms (A={args.A}), " if args.A != 1.0 else "SLDA (A=1), ")
                           + "B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
             "init": ("states of a static self-consistent solve (fixed N, Broyden), stationary start"
                      if args.init == "scf" else
                      "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start"),
-            "friction": args.friction, "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
+            "friction": args.friction, "precision": precision,
+            "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
 def main():
     args = parse()
-    shape = tuple(int(v) for v in args.shape.split(","))
+    wl = resolve(args, args.workload)
     if args.impl == "reference":
-        reference_arm(args, shape)
+        reference_arm(args, wl)
         return
     rank, world, local = dist_env()
     import torch
@@ -499,34 +671,46 @@ def main():
     torch.cuda.set_device(local)
     from paper_2602_08982_b300 import wslda as W
 
+    solo = rank == 0 and world == 1
     cpu = None
-    if rank == 0 and not args.no_cpu and world == 1:
-        cpu = cpu_oracle_rate(shape, args.omega, args.dt, args.cpu_seconds, scheme=args.integrator, A=args.A)
+    if solo and not args.no_cpu:
+        cpu = cpu_oracle_rate(wl, args.dt, args.cpu_seconds, scheme=args.integrator, A=args.A)
     arms = {}
     if args.precision in ("both", "mixed"):
-        arms["mixed"] = run_arm(W, torch, W.MIXED, args, shape, rank, world, local)
+        arms["mixed"] = run_arm(W, torch, W.MIXED, args, wl, rank, world, local)
+    cufft = None
+    if "mixed" in arms and not args.no_cufft and solo:
+        xm, xn = arms["mixed"]["kernel_ms"]["stage_x"]
+        ym, yn = arms["mixed"]["kernel_ms"]["stage_y"]
+        cufft = run_cufft(torch, wl, args, (xm / max(xn, 1), ym / max(yn, 1)))
+    wl64 = resolve(args, args.fp64_workload) if args.precision == "both" else wl
     if args.precision in ("both", "fp64"):
-        arms["fp64"] = run_arm(W, torch, W.FP64, args, shape, rank, world, local)
-    e2e = None if args.no_e2e else run_e2e(W, torch, args, shape, world)
-    batched = run_batched(W, torch, args) if args.batched else None
+        arms["fp64"] = run_arm(W, torch, W.FP64, args, wl64, rank, world, local)
+    e2e = None if args.no_e2e else run_e2e(W, torch, args, wl, world)
+    batched = None if args.no_batched else run_batched(W, torch, args)
+    check = None
+    if solo and not args.no_oracle_check and "mixed" in arms:
+        check = run_oracle_check(W, torch, args, wl)
     main_arm = arms.get("mixed") or arms["fp64"]
     line = {"metric": METRIC, "value": main_arm["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_arm["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "mixed" in arms else "f64",
             "data": "synthetic",
-            "config": workload_config(args, shape, "mixed: complex64 states and FFTs, f64 accumulation"
+            "config": workload_config(args, wl, "mixed: complex64 states and FFTs, f64 accumulation"
                                       if "mixed" in arms else "fp64"),
-            "roofline": main_arm["roofline"], "gpu_launches": main_arm["launches"], "clocks": main_arm["clocks"],
-            "kernel_share": main_arm["kernel_share"]}
+            "roofline": main_arm["roofline"], "step_roofline": main_arm["step_roofline"],
+            "gpu_launches": main_arm["launches"], "clocks": main_arm["clocks"],
+            "kernel_share": main_arm["kernel_share"], "energy_drift": main_arm["energy_drift"]}
     if "fp64" in arms and "mixed" in arms:
         a = arms["fp64"]
         line["fp64"] = {"value": a["value"], "ms_per_step": a["ms_per_step"], "roofline": a["roofline"],
-                        "gpu_launches": a["launches"], "clocks": a["clocks"], "kernel_share": a["kernel_share"]}
-        m = arms["mixed"]
-        line["mixed_vs_fp64"] = {
-            "rel_density_err_rho": float(np.abs(m["rho"] - a["rho"]).max() / np.abs(a["rho"]).max()),
-            "rel_density_err_nu": float(np.abs(m["nu"] - a["nu"]).max() / np.abs(a["nu"]).max()),
-            "after_steps": 3 + args.warmup + args.steps}
+                        "step_roofline": a["step_roofline"], "gpu_launches": a["launches"], "clocks": a["clocks"],
+                        "kernel_share": a["kernel_share"], "energy_drift": a["energy_drift"],
+                        "config": workload_config(args, wl64, "fp64: complex128 states and FFTs")}
+    if check:
+        line["mixed_vs_oracle"] = check
+    if cufft:
+        line["cufft"] = cufft
     if e2e:
         line["e2e"] = e2e
     if "info" in SCF_START:

@@ -253,6 +253,25 @@ wslda_status wslda_uniform_solve(const wslda_lattice* lat, const wslda_functiona
  * Weights are set to T = 0. Replaces wslda_load_states. */
 wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, double delta, const int64_t* kidx);
 
+/* Multiply component `comp` (0 = u, 1 = v) of every loaded state of the box
+ * by a site-dependent complex factor phase[r] ([M] complex, host or device),
+ * before wslda_start. With phase = e^{i theta(r)} on u this imprints the
+ * phase theta on nu = sum u v^* and hence on Delta = -g_eff nu while leaving
+ * rho and the normalisation unchanged: the vortex-line start of the
+ * elongated-trap workload (theta the azimuthal angle about a line along z;
+ * vortex dynamics is among the applications of Sec. 6). Factors of modulus
+ * other than 1 are applied as given (the states are then not normalised).
+ * The product is formed in double and rounded to the stored precision. */
+wslda_status wslda_imprint_phase(wslda_ctx* ctx, int box, int comp, const double* phase, int on_device);
+
+/* FP64 fused multiply-add throughput of the current CUDA device in TFLOP/s
+ * (2 flops per FMA), the best of `reps` timed launches of a kernel of
+ * independent FMA chains over every SM (CUDA events on the legacy default
+ * stream, after one warm-up launch). A hardware microbenchmark, not part of
+ * the method: it is the measured peak against which the FP64 step's
+ * ALU-bound stage kernels are reported. Changes no device setting. */
+wslda_status wslda_measure_fp64_rate(int reps, double* tflops);
+
 /* Static self-consistent solve (Alg. 1, Sec. 3.2) of a trapped, spin-symmetric
  * T = 0 system, whose positive-energy eigenstates then become the box's states
  * (ready for wslda_start). Iteration i applies the map K of Alg. 1 to the
@@ -317,7 +336,9 @@ wslda_status wslda_static_solve(wslda_ctx* ctx, int box, const double* U0, const
  *    loads the library holds it until the process exits); lattices with more
  *    than 699050 sites (3 M > 2^21 doubles) are rejected with WSLDA_ENOMEM.
  *  - The first call on a device resolves that array's device address (a
- *    one-time set-up); make that first call before any stream capture.
+ *    one-time set-up); make that first call before any stream capture. The
+ *    address is kept for the life of the process: do not call this entry
+ *    point after a cudaDeviceReset of that device.
  *  - The work is queued on `stream` (a cudaStream_t, NULL = default stream)
  *    and the call returns without waiting. All calls share the one scratch
  *    array, so calls that overlap on the GPU (other streams, other threads)

@@ -1140,6 +1140,38 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, dou
   return WSLDA_OK;
 }
 
+wslda_status wslda_imprint_phase(wslda_ctx* c, int box, int comp, const double* phase, int on_device) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !phase || (comp != 0 && comp != 1)) return fail(c, WSLDA_EINVAL, "imprint_phase: bad box, component or pointer");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "imprint_phase before the states are loaded");
+  if (c->started) return fail(c, WSLDA_ESTATE, "imprint_phase after wslda_start");
+  const size_t bytes = size_t(b->M) * 16;
+  const double* dph = phase;
+  void* tmp = nullptr;
+  if (!on_device) {
+    for (size_t i = 0; i < 2 * size_t(b->M); ++i)
+      if (!std::isfinite(phase[i])) return fail(c, WSLDA_ENAN, "imprint_phase: non-finite phase");
+    CUDA_TRY(c, cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, phase, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return fail(c, WSLDA_ECUDA, std::string("imprint_phase: ") + cudaGetErrorString(e));
+    }
+    dph = static_cast<const double*>(tmp);
+  }
+  // the deferred normalisation factor multiplies the whole state, so it commutes with the phase
+  cudaError_t e = c->prec == WSLDA_MIXED
+                      ? launch_imprint<float>(static_cast<float2*>(b->slot[b->iphi]), b->n, b->M, comp, dph, c->stream)
+                      : launch_imprint<double>(static_cast<double2*>(b->slot[b->iphi]), b->n, b->M, comp, dph,
+                                               c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(c, WSLDA_ECUDA, std::string("imprint_phase: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return WSLDA_OK;
+}
+
 namespace {
 // max |x[i] - x[mirror(i)]| over the reflections i -> N - i (mod N) of each axis
 double mirror_asymmetry(const double* x, int stride, const wslda_lattice& l) {

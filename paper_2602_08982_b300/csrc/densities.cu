@@ -456,6 +456,20 @@ __global__ void rescale_kernel(const S* src, D* dst, int64_t n, const double* sc
   d.y = decltype(d.y)(f * double(c.y));
   dst[i] = d;
 }
+// Component `comp` of every state times a site-dependent complex factor:
+// dst[n][comp][r] *= phase[r] (phase interleaved doubles, product in double).
+template <typename R>
+__global__ void imprint_kernel(cx<R>* __restrict__ states, int64_t nstates, int M, int comp,
+                               const double* __restrict__ phase) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nstates * M) return;
+  const int64_t n = i / M;
+  const int r = int(i % M);
+  cx<R>& z = states[(2 * n + comp) * M + r];
+  const double a = double(z.x), b = double(z.y), c = phase[2 * r], d = phase[2 * r + 1];
+  z.x = R(a * c - b * d);
+  z.y = R(a * d + b * c);
+}
 __global__ void fill_kernel(double* p, double v, int64_t n) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -492,6 +506,16 @@ template cudaError_t launch_rescale<float2, double2>(const float2*, double2*, in
                                                      int64_t, int*, cudaStream_t);
 template cudaError_t launch_rescale<double2, float2>(const double2*, float2*, int64_t, const double*, int64_t,
                                                      int64_t, int*, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_imprint(cx<R>* states, int64_t nstates, int M, int comp, const double* phase, cudaStream_t s) {
+  const int64_t total = nstates * M;
+  if (total == 0) return cudaSuccess;
+  imprint_kernel<R><<<unsigned((total + 255) / 256), 256, 0, s>>>(states, nstates, M, comp, phase);
+  return cudaGetLastError();
+}
+template cudaError_t launch_imprint<float>(float2*, int64_t, int, int, const double*, cudaStream_t);
+template cudaError_t launch_imprint<double>(double2*, int64_t, int, int, const double*, cudaStream_t);
 
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;

@@ -188,6 +188,9 @@ template <typename R>
 cudaError_t launch_widen(const cx<R>* src, double* dst, int64_t ncomplex, const double* sc, int64_t first,
                          int64_t per_state, cudaStream_t s);
 cudaError_t launch_fill(double* p, double v, int64_t n, cudaStream_t s);
+// Component comp (0 = u, 1 = v) of every state times phase[r] ([M] complex double).
+template <typename R>
+cudaError_t launch_imprint(cx<R>* states, int64_t nstates, int M, int comp, const double* phase, cudaStream_t s);
 // dst = sc[state] * src (sc NULL: 1), complex float <-> double; non-finite src sets err bit 1.
 template <typename S, typename D>
 cudaError_t launch_rescale(const S* src, D* dst, int64_t n, const double* sc, int64_t first, int64_t per_state,

@@ -25,7 +25,9 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 // Device address of the scratch array, resolved once per device. In host
 // code the symbol name only stands in for the array; the kernel must be given
-// this address.
+// this address. The cached address belongs to the device's primary context:
+// after cudaDeviceReset (which ends that context and unloads the module) it is
+// stale, so the entry point must not be used across a device reset.
 constexpr int kMaxDevices = 64;
 double* g_scratch_dev[kMaxDevices] = {};
 std::mutex g_scratch_mutex;

@@ -116,6 +116,8 @@ def _load():
         "wslda_net_adam": (I, [P, D, P]),
         "wslda_net_symmetrize": (I, [P, I64, I, I, I, P, P]),
         "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
+        "wslda_imprint_phase": (I, [P, I, I, P, I]),
+        "wslda_measure_fp64_rate": (I, [I, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -147,12 +149,44 @@ def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4p
     return {k: getattr(out, k) for k, _ in Uniform._fields_}
 
 
+def measure_fp64_rate(reps: int = 5) -> float:
+    """FP64 FMA throughput of the current device in TFLOP/s (wslda_measure_fp64_rate)."""
+    out = ct.c_double()
+    st = lib.wslda_measure_fp64_rate(int(reps), ct.byref(out))
+    if st:
+        raise WsldaError(st, "wslda_measure_fp64_rate failed")
+    return out.value
+
+
 def densities_noalloc(precision: int, uv, rho, nu, shape, w_minus=None, w_plus=None, stream: int = 0):
     """rho and nu of device states into device outputs without any device
-    allocation (wslda_densities_noalloc). All arguments are torch CUDA tensors;
-    the work is queued on `stream` and not waited for."""
+    allocation (wslda_densities_noalloc). All arguments are torch CUDA tensors
+    on the current device: uv [n][2][M] complex64 (MIXED) or complex128 (FP64),
+    rho >= M and nu >= 2 M float64 elements, weights >= n float64 elements.
+    They are checked here, because the C call takes raw device pointers and
+    cannot see their sizes. The work is queued on `stream` and not waited for."""
+    import torch
+    M = int(shape[0]) * int(shape[1]) * int(shape[2])
+    want = torch.complex64 if precision == MIXED else torch.complex128
+    if precision not in (FP64, MIXED):
+        raise ValueError("precision must be FP64 or MIXED")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    named = [("uv", uv), ("rho", rho), ("nu", nu), ("w_minus", w_minus), ("w_plus", w_plus)]
+    for name, t in named:
+        if t is None:
+            continue
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.device == dev):
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if uv.dtype != want or uv.dim() != 3 or uv.shape[1] != 2 or uv.shape[2] != M:
+        raise ValueError(f"uv must be a {want} tensor of shape (n, 2, {M})")
+    n = int(uv.shape[0])
+    for name, t, need in (("rho", rho, M), ("nu", nu, 2 * M), ("w_minus", w_minus, n), ("w_plus", w_plus, n)):
+        if t is not None and (t.dtype != torch.float64 or t.numel() < need):
+            raise ValueError(f"{name} must hold at least {need} float64 values")
     ptr = lambda t: ct.c_void_p(t.data_ptr()) if t is not None else None
-    st = lib.wslda_densities_noalloc(int(precision), ptr(uv), ptr(w_minus), ptr(w_plus), int(uv.shape[0]),
+    st = lib.wslda_densities_noalloc(int(precision), ptr(uv), ptr(w_minus), ptr(w_plus), n,
                                      int(shape[0]), int(shape[1]), int(shape[2]), ptr(rho), ptr(nu),
                                      ct.c_void_p(stream))
     if st:
@@ -267,6 +301,14 @@ class Context:
         p, keep = _ptr(out, np.complex64, _is_device(out))
         self._check(lib.wslda_get_states_f32(self._h, box, p, int(_is_device(out))))
         return out
+
+    def imprint_phase(self, box: int, comp: int, phase):
+        """Multiply component comp (0 = u, 1 = v) of every state by phase[r]."""
+        dev = _is_device(phase)
+        if not dev:
+            phase = np.ascontiguousarray(phase, dtype=np.complex128)
+        p, keep = _ptr(phase, np.complex128, dev)
+        self._check(lib.wslda_imprint_phase(self._h, box, int(comp), p, int(dev)))
 
     def fill_uniform_states(self, box: int, mu_eff: float, delta: float, kidx=None):
         p, keep = _ptr(kidx, np.int64, False)

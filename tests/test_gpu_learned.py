@@ -68,29 +68,40 @@ def test_symmetrize_matches_mirror_average():
     net.close()
 
 
+HELD_OUT = (5000, 5001, 5002, 5003, 5004)  # fixed before any run; every trap is counted
+
+
 def test_trained_network_cuts_static_iterations():
-    """Train on solved 12^3 traps, then start held-out traps from the network's
-    fields and from the uniform system's: plain linear mixing needs fewer
-    iterations from the network's start."""
+    """Train on solved 12^3 traps, then start the fixed held-out traps from the
+    network's fields and from the uniform system's, with plain linear mixing.
+    A solve that reaches the iteration cap is a result, not an exclusion: it
+    counts as the cap in the means and as a failure in the convergence count.
+    The network's start must converge on at least as many traps, need fewer
+    iterations on average over all of them, and at least 20% fewer on the
+    traps that both starts solve."""
     import torch
     from paper_2602_08982_b300 import learned as L
     from paper_2602_08982_b300 import wslda as W
     shape = (12, 12, 12)
+    cap = 400
     X, T, _ = L.dataset(shape, 32, seed=1000)
     net = W.Net(shape, hidden=32, max_batch=8)
     L.init_params(net, 77)
     losses = L.train(net, torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda"), steps=400, batch=8,
                      lr=2e-3, seed=5)
     assert losses[-1] < 0.2 * losses[0]
-    base, learned = [], []
-    for seed in (5000, 5001, 5003):
+    rows = []
+    for seed in HELD_OUT:
         om, a = L.draw_trap(seed, 0.1, 0.2)
-        n0, ok0 = L.iterations(shape, om, a, eps=1e-5, max_iters=400)
+        n0, ok0 = L.iterations(shape, om, a, eps=1e-5, max_iters=cap)
         U, D = L.predict(net, L.net_input(shape, om, a))
         # the BdG functional has no mean field: only Delta is taken from the network
-        n1, ok1 = L.iterations(shape, om, a, U0=np.zeros_like(U), D0=D, eps=1e-5, max_iters=400)
-        assert ok0 and ok1
-        base.append(n0)
-        learned.append(n1)
+        n1, ok1 = L.iterations(shape, om, a, U0=np.zeros_like(U), D0=D, eps=1e-5, max_iters=cap)
+        rows.append((seed, n0 if ok0 else cap, ok0, n1 if ok1 else cap, ok1))
     net.close()
-    assert np.mean(learned) < 0.8 * np.mean(base), (base, learned)
+    print("held-out traps (seed, uniform iters, converged, network iters, converged):", rows)
+    assert sum(r[4] for r in rows) >= sum(r[2] for r in rows), rows
+    assert np.mean([r[3] for r in rows]) < np.mean([r[1] for r in rows]), rows
+    both = [r for r in rows if r[2] and r[4]]
+    assert len(both) >= 3, rows
+    assert np.mean([r[3] for r in both]) < 0.8 * np.mean([r[1] for r in both]), rows

@@ -6,6 +6,8 @@ FFTs, double reductions) within 1e-5 relative. Cases span several tiles and
 ragged state counts, anisotropic lattices and spacings, thermal weights, both
 functionals, cluster sizes 1-16 and pencils split over 1, 2 and 4 lanes.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -130,30 +132,23 @@ def test_uniform_seed_is_stationary_16cubed(W, prec):
     assert rel(phi, case.phi) < (1e-12 if prec == 0 else 1e-5)
 
 
-@pytest.fixture(scope="module")
-def c1_reference():
-    """Oracle for the plain FP64 uniform unitary gas on 16^3 (all 4096 states),
-    seeded 1e-3 pairing perturbation, Taylor start, 20 steps of dt = 0.01."""
-    case = make_case((16, 16, 16), kick=1e-3, seed=1)
-    sysm, st = oracle_evolve(case, 0.01, 20, False)
-    rho, nu = o.densities(st.phi, case.wm, case.wp)
-    return case, rho, nu, sysm.energy(st.phi), st.phi
-
-
 @pytest.mark.parametrize("prec", [0, 1])
-def test_c1_config_16cubed_20_steps(W, c1_reference, prec):
-    """FP64 within 1e-12; the mixed path, started from the same double states
-    (its rounding to complex float included), within 1e-5."""
-    case, rho_r, nu_r, e_r, phi_r = c1_reference
+def test_c1_config_16cubed_20_steps(W, prec):
+    """The plain FP64 uniform unitary gas on 16^3 (all 4096 states), seeded
+    1e-3 pairing perturbation, Taylor start, 20 steps of dt = 0.01, against
+    the stored oracle run (tests/golden/c1_100steps.npz, step 20): FP64 within
+    1e-12; the mixed path, started from the same double states (its rounding
+    to complex float included), within 1e-5."""
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "c1_100steps.npz"))
+    case = make_case((16, 16, 16), kick=1e-3, seed=1)
     ctx, box = gpu_context(case, prec)
     ctx.start(False, 0.01)
     ctx.step(0.01, 17)
     rho, nu = ctx.get_densities(box)
     e = ctx.get_energy(box)
-    phi = ctx.get_states(box)
     ctx.close()
-    errs = dict(rho=rel(rho, rho_r), nu=rel(nu, nu_r), states=rel(phi, phi_r),
-                e_total=abs(e["e_total"] - e_r["e_total"]) / abs(e_r["e_total"]))
+    errs = dict(rho=rel(rho, g["rho_20"]), nu=rel(nu, g["nu_20"]),
+                e_total=abs(e["e_total"] - float(g["e_total_20"])) / abs(float(g["e_total_20"])))
     print("c1", prec, errs)
     assert all(v < TOL[prec] for v in errs.values()), errs
 

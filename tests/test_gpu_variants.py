@@ -55,3 +55,47 @@ def test_variant_matches_oracle(prec, shape, variant, persist, monkeypatch):
     rho, nu = ctx.get_densities(box)
     ctx.close()
     assert rel(rho, r) < tol and rel(nu, n) < tol, desc
+
+
+SCHEME_SHAPES = [(24, 24, 96), (32, 32, 32)]
+
+
+@functools.lru_cache(maxsize=None)
+def _scheme_reference(shape, scheme, prec):
+    c = make_case(shape, nstates=24, kick=0.05, trap=0.06, seed=181 + shape[0], vortex=shape[2] == 96)
+    ref_in = c.phi if prec == 0 else c.phi.astype(np.complex64).astype(np.complex128)
+    from cases import oracle_system
+    sysm = oracle_system(c)
+    st = o.start_scheme(sysm, ref_in, 0.01, False, scheme)
+    st = o.evolve_scheme(sysm, st, 0.01, 2, scheme)
+    return c, o.densities(st.phi, c.wm, c.wp)
+
+
+def _scheme_cases():
+    from paper_2602_08982_b300 import wslda as W
+    out = []
+    for prec in (W.MIXED, W.FP64):
+        for s in SCHEME_SHAPES:
+            for v in range(W.lattice_variants(prec, *s)):
+                for scheme in ("AB3AM4", "AB5AM5"):
+                    for p in (0, 1):
+                        out.append((prec, s, v, scheme, p))
+    return out
+
+
+@pytest.mark.parametrize("prec,shape,variant,scheme,persist", _scheme_cases())
+def test_scheme_variant_matches_oracle(prec, shape, variant, scheme, persist, monkeypatch):
+    """AB3AM4 / AB5AM5 predictor stages (two and four history reads) on every
+    cluster variant of the large lattices, Taylor start and two steps."""
+    from paper_2602_08982_b300 import wslda as W
+    c, (r, n) = _scheme_reference(shape, scheme, prec)
+    tol = 1e-5 if prec == W.MIXED else 1e-12
+    monkeypatch.setenv("WSLDA_VARIANT", str(variant))
+    monkeypatch.setenv("WSLDA_PERSIST", str(persist))
+    ctx, box = gpu_context(c, prec, scheme)
+    ctx.start(False, 0.01)
+    ctx.step(0.01, 2)
+    desc = ctx.get_variant(box)
+    rho, nu = ctx.get_densities(box)
+    ctx.close()
+    assert rel(rho, r) < tol and rel(nu, n) < tol, desc

@@ -51,8 +51,35 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     import torch
     from paper_2602_08982_b300 import wslda as W
     dev = torch.device("cuda")
-    uv = torch.zeros((1, 2, 8), dtype=torch.complex64, device=dev)
-    out = torch.zeros(8, dtype=torch.float64, device=dev)
+    shape = (128, 128, 64)
+    M = shape[0] * shape[1] * shape[2]
+    uv = torch.zeros((1, 2, M), dtype=torch.complex64, device=dev)
+    rho = torch.zeros(M, dtype=torch.float64, device=dev)
+    nu = torch.zeros(2 * M, dtype=torch.float64, device=dev)
     with pytest.raises(W.WsldaError) as e:
-        W.densities_noalloc(W.MIXED, uv, out, out, (128, 128, 64))
+        W.densities_noalloc(W.MIXED, uv, rho, nu, shape)
     assert e.value.status == 2
+
+
+def test_noalloc_binding_checks_shapes_and_dtypes():
+    """The C call takes raw device pointers, so the binding refuses tensors
+    whose dtype, shape or length would make the kernels step outside them."""
+    import torch
+    from paper_2602_08982_b300 import wslda as W
+    dev = torch.device("cuda")
+    shape = (8, 8, 8)
+    M = 512
+    uv = torch.zeros((3, 2, M), dtype=torch.complex64, device=dev)
+    rho = torch.zeros(M, dtype=torch.float64, device=dev)
+    nu = torch.zeros(2 * M, dtype=torch.float64, device=dev)
+    bad = [
+        (W.FP64, uv, rho, nu, None),                                   # complex64 states for FP64
+        (W.MIXED, uv[:, :, :256], rho, nu, None),                      # wrong site count
+        (W.MIXED, uv, rho[:100], nu, None),                            # rho too short
+        (W.MIXED, uv, rho, nu[:M], None),                              # nu too short
+        (W.MIXED, uv, rho, nu, torch.ones(2, dtype=torch.float64, device=dev)),  # weights too short
+        (W.MIXED, uv.cpu(), rho, nu, None),                            # host tensor
+    ]
+    for prec, u, r, n, w in bad:
+        with pytest.raises(ValueError):
+            W.densities_noalloc(prec, u, r, n, shape, w, w)
