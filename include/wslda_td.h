@@ -60,7 +60,8 @@ typedef enum { WSLDA_FP64 = 0, WSLDA_MIXED = 1 } wslda_precision;
 typedef enum {
   WSLDA_FUNC_SLDA_A1 = 0, /* SLDA with A forced to 1 (Sec. 2.4, last paragraph) */
   WSLDA_FUNC_BDG = 1,     /* BdG: A = 1, B = 0, coupling 4 pi a (Eq. HBdG) */
-  WSLDA_FUNC_SLDA = 2     /* SLDA-type with a constant A (field A), current terms included */
+  WSLDA_FUNC_SLDA = 2,    /* SLDA-type with a constant A (field A), current terms included */
+  WSLDA_FUNC_ASLDA = 3    /* spin-imbalanced ASLDA (Sec. 2.4): A_a(p), A_b(p), B(p) printed, C given */
 } wslda_functional_kind;
 
 /* Periodic lattice (Sec. 3.1). Every n must be even; see
@@ -83,10 +84,24 @@ typedef struct {
  *        at rho_floor in these terms. A = 1 gives slda_a1. Static solves and
  *        the dissipative terms are not available for it (WSLDA_EUNSUPPORTED).
  *  bdg : 1/g_eff = inv_4pi_a - Lambda_c,     U = 0
+ *  aslda (spin-imbalanced, Secs. 2.3-2.4): the states are those of Eq. HpsiEpsi
+ *        over the whole spectrum, phi_n = (u_{n,a}, v_{n,b}) with the weights
+ *        w_plus = f(E_n) for u and w_minus = f(-E_n) for v; densities of
+ *        Eqs. na3D..jb3D (rho_a = sum f(E)|u|^2, rho_b = sum f(-E)|v|^2,
+ *        nu = 1/2 sum (f(-E) - f(E)) u v^*, tau_s and j_s the same way with
+ *        Nyquist-free gradients), all reduced at every stage; A_a(p) = A_b(-p)
+ *        and B(p) as printed, p = (rho_a - rho_b)/(rho_a + rho_b), C = C
+ *        (the ASLDA value is -11.11); potentials V_s = dE/d rho_s (with the
+ *        p-derivative terms), alpha_s = A_s(p), current potentials
+ *        (1 - A_s) j_s / rho_s; the kinetic operator -1/2 grad.alpha_s grad of
+ *        Eq. kinop-alpha; mu = mu_a on the u row, mu_b on the v row; one V_ext
+ *        for both species; Lambda_c with the spin averages of Sec. 2.6. B and
+ *        A are not read. Static solves and the dissipative terms are not
+ *        available for it (WSLDA_EUNSUPPORTED).
  *  Delta = -g_eff nu (Eq. Delta). mu is the chemical potential on the diagonal
  *  of H. ec <= 0 selects the zone-corner cutoff (pi^2/2)(1/dx^2+1/dy^2+1/dz^2).
  *  rho_floor bounds rho from below inside the potentials only. A is read for
- *  kind slda only. */
+ *  kind slda only, mu_b for kind aslda only. */
 typedef struct {
   int kind;
   double B, C;
@@ -95,6 +110,7 @@ typedef struct {
   double ec;
   double rho_floor;
   double A;
+  double mu_b;
 } wslda_functional;
 
 /* Energy terms of Sec. 3.2. e_kin is A times the sum of the kinetic
@@ -189,6 +205,19 @@ wslda_status wslda_get_states_f32(wslda_ctx* ctx, int box, float* uv, int on_dev
  * tau [M] and j [3][M] (Eqs. nab3D..jab3D, gradients with the Nyquist mode
  * zeroed) are computed when the pointers are not NULL. Host pointers. */
 wslda_status wslda_get_densities(wslda_ctx* ctx, int box, double* rho, double* nu, double* tau, double* j);
+
+/* Per-species densities of an aslda box (host pointers, each nullable):
+ * rho_a, rho_b [M], nu [M complex], tau_a, tau_b [M], j_a, j_b [3][M]
+ * (Eqs. na3D..jb3D with the box's frozen weights). For other kinds
+ * WSLDA_EINVAL. (wslda_get_densities on an aslda box gives rho = (rho_a + rho_b)/2
+ * and nu, and no tau or j.) */
+wslda_status wslda_get_spin_densities(wslda_ctx* ctx, int box, double* rho_a, double* rho_b, double* nu,
+                                      double* tau_a, double* tau_b, double* j_a, double* j_b);
+
+/* Per-species potentials of an aslda box (host pointers, each nullable):
+ * V_a, V_b [M] (dE/d rho_s, without V_ext and mu) and Delta [M complex]
+ * (without Delta_ext). For other kinds WSLDA_EINVAL. */
+wslda_status wslda_get_spin_fields(wslda_ctx* ctx, int box, double* V_a, double* V_b, double* delta);
 
 /* Potentials built from the current densities: U [M] and Delta [M complex]
  * (without Delta_ext). Host pointers. */

@@ -83,6 +83,16 @@ struct Box {
   void* av = nullptr;
   double* ecur = nullptr;
   double* d1 = nullptr;
+  // spin-imbalanced ASLDA: the second species' densities {tau, j}, rho, V,
+  // current potential; the alpha fields {alpha_a/2, alpha_b/2}; the first
+  // columns of the Eq. D2 matrices; per-site scratch of the potentials; the
+  // v-part density partials; zero weights (double and working precision)
+  bool aslda = false;
+  double mu_b = 0.0;
+  double *tauj_b = nullptr, *rho_b = nullptr, *U_b = nullptr, *d2 = nullptr, *af = nullptr, *part_b = nullptr;
+  void *av_b = nullptr, *alf = nullptr;
+  double* wzero = nullptr;
+  void* wzero_r = nullptr;
   bool loaded = false;
   void* ptr(int i) const { return slot[i]; }
 };
@@ -308,27 +318,36 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   if (b.n == 0) return WSLDA_OK;
   const bool ym = mode == MODE_Y && b.ks_y;
   const KernelSet* ks = ym ? b.ks_y : b.ks;
-  const bool applies_h = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
-                         mode == MODE_F || mode == MODE_HORNER;
-  if (b.cur && applies_h) {
+  const bool gen = b.cur && applies_h(mode);
+  if (gen) {
     // current term -(i/2){A, grad} phi of this launch's input states and its
     // part of <H>_n, read by the stage below. It runs on the stage's own launch
     // variant: its <H>_n partials are per CTA of that variant's clusters.
+    // Spin-imbalanced ASLDA: each row its own current potential, then the
+    // transformed alpha phi parts of Eq. kinop-alpha added to the same buffer.
     ProfScope pg(c, PROF_AUX);
     StageArgs<R> g = base_args<R>(b, box_dV(b));
     g.phi = a.phi;
     g.sc_in = a.sc_in;
     g.h0 = static_cast<cx<R>*>(b.cur_buf);
     g.av = static_cast<const fx4<R>*>(b.av);
+    g.av2 = static_cast<const fx4<R>*>(b.av_b);
+    g.alf = static_cast<const cx<R>*>(b.alf);
     g.ecur = b.ecur;
     g.err = c->err_d;
-    CUDA_TRY(c, ks->launch[MODE_AGRAD](&g, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
+    CUDA_TRY(c, ks->launch[MODE_AGRAD](&g, int(b.n), 0, c->cur));
     c->launches += 1;
+    if (b.aslda) {
+      CUDA_TRY(c, ks->launch[MODE_KALPHA](&g, int(b.n), 0, c->cur));
+      c->launches += 1;
+    }
     a.cur = static_cast<const cx<R>*>(b.cur_buf);
     a.ecur = b.ecur;
+    a.alf = static_cast<const cx<R>*>(b.alf);
   }
   ProfScope ps(c, kind);
-  CUDA_TRY(c, ks->launch[mode](&a, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
+  if (gen) CUDA_TRY(c, ks->launch_gen[mode](&a, int(b.n), 0, c->cur));
+  else CUDA_TRY(c, ks->launch[mode](&a, int(b.n), ym ? b.ncl_y : b.ncl, c->cur));
   c->launches += 1;
   const bool norm_out = mode == MODE_X || mode == MODE_X3 || mode == MODE_X5 || mode == MODE_Y ||
                         (mode == MODE_HORNER && a.normalize);
@@ -340,8 +359,53 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
 }
 
 // densities of slot `islot` -> potentials -> H fields
+// Spin-imbalanced ASLDA: {tau, j} and the density partials of the u part
+// (weights 0, f(E)) and of the v part (f(-E), 0), then the potentials and the
+// fields of H.
+template <typename R>
+wslda_status refresh_aslda(wslda_ctx* c, Box& b, int islot, int init_lam) {
+  const double* wsets[2][2] = {{b.wzero, b.wp}, {b.wm, b.wzero}};
+  const void* rsets[2][2] = {{b.wzero_r, b.wp_r}, {b.wm_r, b.wzero_r}};
+  double* tj[2] = {b.tauj, b.tauj_b};
+  double* parts[2] = {b.part, b.part_b};
+  for (int sp = 0; sp < 2; ++sp) {
+    if (b.n > 0) {
+      StageArgs<R> a = base_args<R>(b, box_dV(b));
+      a.phi = static_cast<cx<R>*>(b.ptr(islot));
+      a.h0 = static_cast<cx<R>*>(b.cur_buf);
+      a.sc_in = b.sc[islot];
+      a.wm = wsets[sp][0];
+      a.wp = wsets[sp][1];
+      wslda_status st = launch_mode<R>(c, b, MODE_GRAD, a, PROF_DENS);
+      if (st) return st;
+      ProfScope pj(c, PROF_DENS);
+      c->launches += 3;
+      // the v-part partial buffer is the scratch of the sum (the u-part partials are kept)
+      CUDA_TRY(c, launch_sum_tauj<R>(static_cast<const cx<R>*>(b.cur_buf), b.n, b.M, b.nchunk, b.chunk, b.part_b,
+                                     tj[sp], tj[sp] + b.M, c->cur));
+      CUDA_TRY(c, launch_density_partial<R>(static_cast<const cx<R>*>(b.ptr(islot)), b.sc[islot],
+                                            static_cast<const R*>(rsets[sp][0]), static_cast<const R*>(rsets[sp][1]),
+                                            b.n, b.M, b.nchunk, b.chunk, parts[sp], c->cur));
+    } else {
+      CUDA_TRY(c, cudaMemsetAsync(tj[sp], 0, size_t(4) * b.M * 8, c->cur));
+      CUDA_TRY(c, cudaMemsetAsync(parts[sp], 0, size_t(3) * b.M * b.nchunk * sizeof(double), c->cur));
+    }
+  }
+  ProfScope ps2(c, PROF_POT);
+  c->launches += 2;
+  CUDA_TRY(c, launch_aslda_potentials(b.part, b.part_b, b.nchunk, b.M, b.tauj, b.tauj_b, b.vext, b.fdev.mu, b.mu_b,
+                                      b.fdev.C, b.fdev.ec, b.fdev.rho_floor, b.lam, init_lam, b.rho, b.rho_b, b.nu,
+                                      b.U, b.U_b, b.delta, b.af, c->cur));
+  CUDA_TRY(c, launch_aslda_fields<R>(b.lat.nx, b.lat.ny, b.lat.nz, b.af, b.U, b.U_b, b.delta, b.vext, b.dext,
+                                     b.fdev.mu, b.mu_b, b.d1, b.d2, static_cast<fx4<R>*>(b.WD),
+                                     static_cast<cx<R>*>(b.alf), static_cast<fx4<R>*>(b.av),
+                                     static_cast<fx4<R>*>(b.av_b), c->cur));
+  return WSLDA_OK;
+}
+
 template <typename R>
 wslda_status refresh_fields_t(wslda_ctx* c, Box& b, int islot, int init_lam) {
+  if (b.aslda) return refresh_aslda<R>(c, b, islot, init_lam);
   if (b.cur) {
     // j of the states in the slot (Eq. jab3D; A != 1): per-state contributions
     // from the gradient launch, summed over states (before the density
@@ -504,7 +568,8 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   // WSLDA_VARIANT=<i> fixes the variant, WSLDA_PERSIST=0/1 the launch form
   const char* forced = getenv("WSLDA_VARIANT");
   const char* pers = getenv("WSLDA_PERSIST");
-  const int pmode = pers ? (atoi(pers) ? 1 : 0) : -1;
+  // boxes with the current terms run their H stages one cluster per state
+  const int pmode = b.cur ? 0 : (pers ? (atoi(pers) ? 1 : 0) : -1);
   std::vector<const KernelSet*> v = find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
   if (forced) v.assign(1, b.ks);
   if (v.size() == 1 && pmode >= 0) {
@@ -601,6 +666,13 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
 // Energy terms of the current states into h[0..6] (fields must be current).
 template <typename R>
 wslda_status compute_energy(wslda_ctx* c, Box& b, double* h) {
+  if (b.aslda) {  // every term from the per-species densities of the last refresh
+    CUDA_TRY(c, launch_aslda_energy(b.M, b.rho, b.rho_b, b.nu, b.tauj, b.tauj_b, b.lam, b.vext, b.dext, b.fdev.C,
+                                    b.fdev.rho_floor, box_dV(b), b.out8, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(h, b.out8, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return WSLDA_OK;
+  }
   StageArgs<R> a = base_args<R>(b, box_dV(b));
   a.phi = static_cast<cx<R>*>(b.ptr(b.iphi));
   a.sc_in = b.sc[b.iphi];
@@ -614,15 +686,20 @@ wslda_status compute_energy(wslda_ctx* c, Box& b, double* h) {
   return WSLDA_OK;
 }
 
+// E_tot - mu N (Eq. E_tot), with mu_a N_a + mu_b N_b for the spin-imbalanced box
+double conserved_energy(const Box& b, const double* h) {
+  return b.aslda ? h[5] - b.fn.mu * h[8] - b.mu_b * h[9] : h[5] - b.fn.mu * h[6];
+}
+
 template <typename R>
 wslda_status start_box(wslda_ctx* c, Box& b, int stationary, double dt) {
   wslda_status st;
   if ((st = refresh_fields(c, b, b.iphi, 1))) return st;
   {
     // reference values of the conservation diagnostics (Sec. 4.5.1)
-    double h[8];
+    double h[16];
     if ((st = compute_energy<R>(c, b, h))) return st;
-    b.e0 = h[5] - b.fn.mu * h[6];
+    b.e0 = conserved_energy(b, h);
     b.n0 = h[6];
   }
   if ((st = autotune_box<R>(c, b, dt))) return st;
@@ -835,7 +912,7 @@ wslda_status wslda_set_friction(wslda_ctx* c, int box, double alpha, double beta
   CHECK_CTX(c);
   Box* b = get_box(c, box);
   if (!b) return fail(c, WSLDA_EINVAL, "set_friction: bad box");
-  if (b->cur) return fail(c, WSLDA_EUNSUPPORTED, "set_friction: functional with A != 1 not supported");
+  if (b->cur) return fail(c, WSLDA_EUNSUPPORTED, "set_friction: functional with A != 1 (or ASLDA) not supported");
   if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma) || !(rho0 > 0.0) ||
       !(n_req > 0.0) || !std::isfinite(rho0) || !std::isfinite(n_req))
     return fail(c, WSLDA_EINVAL, "set_friction: coefficients must be finite, rho0 and n_req > 0");
@@ -885,8 +962,11 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   if (lat->nx <= 0 || lat->ny <= 0 || lat->nz <= 0 || (lat->nx | lat->ny | lat->nz) & 1)
     return -fail(c, WSLDA_EINVAL, "lattice sizes must be positive and even");
   if (!(lat->dx > 0 && lat->dy > 0 && lat->dz > 0)) return -fail(c, WSLDA_EINVAL, "lattice spacings must be > 0");
-  if (fn->kind != WSLDA_FUNC_SLDA_A1 && fn->kind != WSLDA_FUNC_BDG && fn->kind != WSLDA_FUNC_SLDA)
+  if (fn->kind != WSLDA_FUNC_SLDA_A1 && fn->kind != WSLDA_FUNC_BDG && fn->kind != WSLDA_FUNC_SLDA &&
+      fn->kind != WSLDA_FUNC_ASLDA)
     return -fail(c, WSLDA_EINVAL, "unknown functional kind");
+  if (fn->kind == WSLDA_FUNC_ASLDA && (!std::isfinite(fn->mu) || !std::isfinite(fn->mu_b)))
+    return -fail(c, WSLDA_EINVAL, "ASLDA needs finite mu (species a) and mu_b");
   if (fn->kind != WSLDA_FUNC_BDG && !(fn->C != 0.0)) return -fail(c, WSLDA_EINVAL, "SLDA needs C != 0");
   if (fn->kind == WSLDA_FUNC_SLDA && !(fn->A > 0.0 && std::isfinite(fn->A)))
     return -fail(c, WSLDA_EINVAL, "SLDA needs a finite A > 0");
@@ -905,8 +985,10 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.csize = prec ? 8 : 16;
   const size_t rsize = prec ? 4 : 8;
   b.fdev.kind = fn->kind == WSLDA_FUNC_BDG ? 1 : 0;
-  b.fdev.A = fn->kind == WSLDA_FUNC_SLDA ? fn->A : 1.0;
-  b.cur = fn->kind == WSLDA_FUNC_SLDA && fn->A != 1.0;
+  b.fdev.A = fn->kind == WSLDA_FUNC_SLDA ? fn->A : 1.0;  // ASLDA: unit symbol, alpha applied per site
+  b.aslda = fn->kind == WSLDA_FUNC_ASLDA;
+  b.mu_b = b.aslda ? fn->mu_b : fn->mu;
+  b.cur = (fn->kind == WSLDA_FUNC_SLDA && fn->A != 1.0) || b.aslda;
   b.fdev.B = fn->B;
   b.fdev.C = fn->C;
   b.fdev.inv_4pi_a = fn->inv_4pi_a;
@@ -921,7 +1003,9 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
                              size_t(nstates) * (8 * 26 + rsize * 2) + 4096;
   const int D = c->scheme_depth;
   const size_t need = size_t(D + 2 + (b.cur ? 1 : 0)) * state_bytes + field_bytes +
-                      (b.cur ? size_t(M) * (32 + 4 * rsize) + size_t(nstates) * 128 : 0);
+                      (b.cur ? size_t(M) * (32 + 4 * rsize) + size_t(nstates) * 128 : 0) +
+                      (b.aslda ? size_t(M) * (8 * 14 + rsize * 6) + size_t(4) * M * 8 * b.nchunk +
+                                     size_t(nstates) * (8 + rsize) : 0);
   size_t freeb = 0, totalb = 0;
   CUDA_TRY_NEG(c, cudaMemGetInfo(&freeb, &totalb));
   const size_t margin = size_t(1) << 30;
@@ -966,13 +1050,27 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   ALLOC(b.Ebuf, std::max<int64_t>(nstates, 1) * 8);
   ALLOC(b.npart, std::max<int64_t>(nstates, 1) * 16 * 8);
   ALLOC(b.ekin2, std::max<int64_t>(nstates, 1) * 16);
-  ALLOC(b.out8, 8 * 8);
+  ALLOC(b.out8, 16 * 8);
   if (b.cur) {
     ALLOC(b.cur_buf, std::max<size_t>(state_bytes, 16));
     ALLOC(b.tauj, size_t(4) * M * 8);
     ALLOC(b.av, size_t(4) * M * rsize);
     ALLOC(b.ecur, std::max<int64_t>(nstates, 1) * 16 * 8);
     ALLOC(b.d1, size_t(lat->nx + lat->ny + lat->nz) * 8);
+  }
+  if (b.aslda) {
+    ALLOC(b.tauj_b, size_t(4) * M * 8);
+    ALLOC(b.rho_b, M * 8);
+    ALLOC(b.U_b, M * 8);
+    ALLOC(b.d2, size_t(lat->nx + lat->ny + lat->nz) * 8);
+    ALLOC(b.af, size_t(8) * M * 8);
+    ALLOC(b.part_b, size_t(4) * M * 8 * b.nchunk);
+    ALLOC(b.av_b, size_t(4) * M * rsize);
+    ALLOC(b.alf, size_t(2) * M * rsize);
+    ALLOC(b.wzero, std::max<int64_t>(nstates, 1) * 8);
+    ALLOC(b.wzero_r, std::max<int64_t>(nstates, 1) * rsize);
+    CUDA_TRY_NEG(c, cudaMemsetAsync(b.wzero, 0, std::max<int64_t>(nstates, 1) * 8, c->stream));
+    CUDA_TRY_NEG(c, cudaMemsetAsync(b.wzero_r, 0, std::max<int64_t>(nstates, 1) * rsize, c->stream));
   }
 #undef ALLOC
   CUDA_TRY_NEG(c, cudaMemsetAsync(b.vext, 0, M * 8, c->stream));
@@ -1003,6 +1101,27 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
       }
     }
     CUDA_TRY_NEG(c, cudaMemcpyAsync(b.d1, d1.data(), d1.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY_NEG(c, cudaStreamSynchronize(c->stream));
+  }
+  if (b.aslda) {
+    // first column of the periodic second-derivative matrix of Eq. D2 (the
+    // Laplacian of H, Nyquist mode kept): c_j = -(1/N) sum_m k_m^2 cos(2 pi m j / N)
+    std::vector<double> d2;
+    const int ns[3] = {lat->nx, lat->ny, lat->nz};
+    const double ds[3] = {lat->dx, lat->dy, lat->dz};
+    for (int ax = 0; ax < 3; ++ax) {
+      const int N = ns[ax];
+      for (int jj = 0; jj < N; ++jj) {
+        double acc = 0.0;
+        for (int m = 0; m < N; ++m) {
+          const int f = m <= N / 2 ? m : m - N;
+          const double k = 2.0 * M_PI * f / (N * ds[ax]);
+          acc -= k * k * cos(2.0 * M_PI * double((int64_t(m) * jj) % N) / double(N));
+        }
+        d2.push_back(acc / N);
+      }
+    }
+    CUDA_TRY_NEG(c, cudaMemcpyAsync(b.d2, d2.data(), d2.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY_NEG(c, cudaStreamSynchronize(c->stream));
   }
   std::vector<double> tw(2 * naxis);
@@ -1200,7 +1319,8 @@ wslda_status wslda_static_solve(wslda_ctx* c, int box, const double* U0, const d
   if (!b || !U0 || !delta0 || !p || !out) return fail(c, WSLDA_EINVAL, "static_solve: bad box or null pointer");
   if (c->started) return fail(c, WSLDA_ESTATE, "static_solve after wslda_start");
   if (b->n != b->M) return fail(c, WSLDA_EINVAL, "static_solve: the box must hold nstates = M states");
-  if (b->fdev.A != 1.0) return fail(c, WSLDA_EUNSUPPORTED, "static_solve: functional with A != 1 not built");
+  if (b->fdev.A != 1.0 || b->aslda)
+    return fail(c, WSLDA_EUNSUPPORTED, "static_solve: functional with A != 1 (or ASLDA) not built");
   if (!(p->mixing > 0.0 && p->mixing <= 1.0) || p->max_iters < 1 || !(p->eps_energy >= 0.0) ||
       !std::isfinite(p->e_ref) || !std::isfinite(p->n_target) || !std::isfinite(p->a_mu) ||
       (p->n_target > 0 && !(p->eps_npart > 0.0)) || (p->method != 0 && p->method != 1) ||
@@ -1395,6 +1515,18 @@ wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu,
     wslda_status st = refresh_fields(c, *b, b->iphi, 1);
     if (st) return st;
   }
+  if (b->aslda) {  // spin average of rho; tau and j per species come from wslda_get_spin_densities
+    if (tau || j) return fail(c, WSLDA_EINVAL, "get_densities: tau / j of an ASLDA box: use get_spin_densities");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (rho) {
+      std::vector<double> ra(b->M), rb(b->M);
+      CUDA_TRY(c, cudaMemcpy(ra.data(), b->rho, size_t(b->M) * 8, cudaMemcpyDeviceToHost));
+      CUDA_TRY(c, cudaMemcpy(rb.data(), b->rho_b, size_t(b->M) * 8, cudaMemcpyDeviceToHost));
+      for (int i = 0; i < b->M; ++i) rho[i] = 0.5 * (ra[i] + rb[i]);
+    }
+    if (nu) CUDA_TRY(c, cudaMemcpy(nu, b->nu, size_t(b->M) * 16, cudaMemcpyDeviceToHost));
+    return WSLDA_OK;
+  }
   if (rho) CUDA_TRY(c, cudaMemcpyAsync(rho, b->rho, size_t(b->M) * 8, cudaMemcpyDeviceToHost, c->stream));
   if (nu) CUDA_TRY(c, cudaMemcpyAsync(nu, b->nu, size_t(b->M) * 16, cudaMemcpyDeviceToHost, c->stream));
   if ((tau || j) && b->n > 0) {
@@ -1438,6 +1570,45 @@ wslda_status wslda_get_densities(wslda_ctx* c, int box, double* rho, double* nu,
   return WSLDA_OK;
 }
 
+wslda_status wslda_get_spin_densities(wslda_ctx* c, int box, double* rho_a, double* rho_b, double* nu,
+                                      double* tau_a, double* tau_b, double* j_a, double* j_b) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !b->aslda) return fail(c, WSLDA_EINVAL, "get_spin_densities: bad box or not an ASLDA box");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_spin_densities before load_states");
+  if (!c->started) {
+    wslda_status st = refresh_fields(c, *b, b->iphi, 1);
+    if (st) return st;
+  }
+  const size_t M = size_t(b->M);
+  const std::pair<double*, const double*> cp[4] = {{rho_a, b->rho}, {rho_b, b->rho_b}, {tau_a, b->tauj},
+                                                   {tau_b, b->tauj_b}};
+  for (int i = 0; i < 4; ++i)
+    if (cp[i].first) CUDA_TRY(c, cudaMemcpyAsync(cp[i].first, cp[i].second, M * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (nu) CUDA_TRY(c, cudaMemcpyAsync(nu, b->nu, M * 16, cudaMemcpyDeviceToHost, c->stream));
+  if (j_a) CUDA_TRY(c, cudaMemcpyAsync(j_a, b->tauj + M, 3 * M * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (j_b) CUDA_TRY(c, cudaMemcpyAsync(j_b, b->tauj_b + M, 3 * M * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
+wslda_status wslda_get_spin_fields(wslda_ctx* c, int box, double* V_a, double* V_b, double* delta) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b || !b->aslda) return fail(c, WSLDA_EINVAL, "get_spin_fields: bad box or not an ASLDA box");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_spin_fields before load_states");
+  if (!c->started) {
+    wslda_status st = refresh_fields(c, *b, b->iphi, 1);
+    if (st) return st;
+  }
+  const size_t M = size_t(b->M);
+  if (V_a) CUDA_TRY(c, cudaMemcpyAsync(V_a, b->U, M * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (V_b) CUDA_TRY(c, cudaMemcpyAsync(V_b, b->U_b, M * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (delta) CUDA_TRY(c, cudaMemcpyAsync(delta, b->delta, M * 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return WSLDA_OK;
+}
+
 wslda_status wslda_get_fields(wslda_ctx* c, int box, double* U, double* delta) {
   CHECK_CTX(c);
   Box* b = get_box(c, box);
@@ -1460,7 +1631,7 @@ wslda_status wslda_get_energy(wslda_ctx* c, int box, wslda_energy* out) {
   if (!b->loaded) return fail(c, WSLDA_ESTATE, "get_energy before load_states");
   wslda_status st;
   if (!c->started && (st = refresh_fields(c, *b, b->iphi, 1))) return st;
-  double h[8];
+  double h[16];
   st = c->prec == WSLDA_MIXED ? compute_energy<float>(c, *b, h) : compute_energy<double>(c, *b, h);
   if (st) return st;
   collect_profile(c);
@@ -1512,10 +1683,10 @@ wslda_status wslda_check_conservation(wslda_ctx* c, int box, double e_tol, doubl
   Box* b = get_box(c, box);
   if (!b) return fail(c, WSLDA_EINVAL, "check_conservation: bad box");
   if (!c->started) return fail(c, WSLDA_ESTATE, "check_conservation before wslda_start");
-  double h[8];
+  double h[16];
   wslda_status st = c->prec == WSLDA_MIXED ? compute_energy<float>(c, *b, h) : compute_energy<double>(c, *b, h);
   if (st) return st;
-  const double e = h[5] - b->fn.mu * h[6];
+  const double e = conserved_energy(*b, h);
   const double rel_e = std::fabs(e - b->e0) / std::max(std::fabs(b->e0), 1e-300);
   const double rel_n = std::fabs(h[6] - b->n0) / std::max(std::fabs(b->n0), 1e-300);
   if (de) *de = rel_e;

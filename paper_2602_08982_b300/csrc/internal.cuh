@@ -22,6 +22,9 @@ struct KernelSet {
   int cs, bt, tx, ty, tz, minb;
   size_t smem;
   LaunchFn launch[NMODES];
+  // the modes that apply H, compiled for the general functional (current
+  // term, per-site alpha; one cluster per state); NULL for the other modes
+  LaunchFn launch_gen[NMODES];
   const void* fn[NMODES];
 };
 
@@ -31,9 +34,9 @@ struct Registrar {
   explicit Registrar(const KernelSet& k) { registry().push_back(k); }
 };
 
-template <class G, int MODE, bool PERSIST>
+template <class G, int MODE, bool PERSIST, bool GEN = false>
 cudaError_t launch_stage_as(const StageArgs<typename G::R>& a, int ncl, cudaStream_t s) {
-  auto kern = stage_kernel<G, MODE, PERSIST>;
+  auto kern = stage_kernel<G, MODE, PERSIST, GEN>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::smem_bytes));
@@ -66,6 +69,13 @@ cudaError_t launch_stage(const void* args, int nstates, int nclusters, cudaStrea
   if (nclusters > 0 && nclusters < nstates) return launch_stage_as<G, MODE, true>(a, nclusters, s);
   return launch_stage_as<G, MODE, false>(a, nstates, s);
 }
+// general-functional instance: always one cluster per state
+template <class G, int MODE>
+cudaError_t launch_stage_gen(const void* args, int nstates, int, cudaStream_t s) {
+  StageArgs<typename G::R> a = *static_cast<const StageArgs<typename G::R>*>(args);
+  a.nstates = nstates;
+  return launch_stage_as<G, MODE, false, true>(a, nstates, s);
+}
 
 template <class G>
 KernelSet make_set() {
@@ -84,6 +94,14 @@ KernelSet make_set() {
   k.launch[MODE_X5] = launch_stage<G, MODE_X5>;
   k.launch[MODE_LAP] = launch_stage<G, MODE_LAP>;
   k.launch[MODE_AGRAD] = launch_stage<G, MODE_AGRAD>;
+  k.launch[MODE_KALPHA] = launch_stage<G, MODE_KALPHA>;
+  for (int m = 0; m < NMODES; ++m) k.launch_gen[m] = nullptr;
+  k.launch_gen[MODE_X] = launch_stage_gen<G, MODE_X>;
+  k.launch_gen[MODE_Y] = launch_stage_gen<G, MODE_Y>;
+  k.launch_gen[MODE_F] = launch_stage_gen<G, MODE_F>;
+  k.launch_gen[MODE_HORNER] = launch_stage_gen<G, MODE_HORNER>;
+  k.launch_gen[MODE_X3] = launch_stage_gen<G, MODE_X3>;
+  k.launch_gen[MODE_X5] = launch_stage_gen<G, MODE_X5>;
   k.fn[MODE_X] = (const void*)stage_kernel<G, MODE_X, false>;
   k.fn[MODE_Y] = (const void*)stage_kernel<G, MODE_Y, false>;
   k.fn[MODE_F] = (const void*)stage_kernel<G, MODE_F, false>;
@@ -94,6 +112,7 @@ KernelSet make_set() {
   k.fn[MODE_X5] = (const void*)stage_kernel<G, MODE_X5, false>;
   k.fn[MODE_LAP] = (const void*)stage_kernel<G, MODE_LAP, false>;
   k.fn[MODE_AGRAD] = (const void*)stage_kernel<G, MODE_AGRAD, false>;
+  k.fn[MODE_KALPHA] = (const void*)stage_kernel<G, MODE_KALPHA, false>;
   return k;
 }
 
@@ -161,6 +180,23 @@ cudaError_t launch_energy(int M, int64_t nstates, FunctionalDev fn, const double
                           const double* delta, const double* vext, const double* dext, const double* ekin2,
                           const double* wm, const double* wp, const double* j, double dV, double* out8,
                           cudaStream_t s);
+
+// Spin-imbalanced ASLDA (aslda.cu): per-site potentials from the u-part and
+// v-part density partials and {tau, j} of each species, then the fields of H
+// that need neighbouring sites (lap alpha, div A), and the energy terms.
+cudaError_t launch_aslda_potentials(const double* part_a, const double* part_b, int nchunk, int M, const double* tj_a,
+                                    const double* tj_b, const double* vext, double mu_a, double mu_b, double C,
+                                    double ec, double rho_floor, double* lam, int init_lam, double* rho_a,
+                                    double* rho_b, double* nu, double* Va, double* Vb, double* delta, double* af,
+                                    cudaStream_t s);
+template <typename R>
+cudaError_t launch_aslda_fields(int nx, int ny, int nz, const double* af, const double* Va, const double* Vb,
+                                const double* delta, const double* vext, const double* dext, double mu_a, double mu_b,
+                                const double* d1, const double* d2, fx4<R>* WD, cx<R>* alf, fx4<R>* av_a,
+                                fx4<R>* av_b, cudaStream_t s);
+cudaError_t launch_aslda_energy(int M, const double* rho_a, const double* rho_b, const double* nu, const double* tj_a,
+                                const double* tj_b, const double* lam, const double* vext, const double* dext, double C,
+                                double rho_floor, double dV, double* out8, cudaStream_t s);
 
 // Plane-wave states of a uniform solution (uniform.cu); dst is float2 or double2.
 cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,

@@ -33,6 +33,13 @@
 //            in h0, and the per-CTA partials of sum_r Re(phi^* (-i S)) (the
 //            current part of <H>_n). The stage modes add it to H phi when
 //            `cur` is set.
+//   MODE_KALPHA  the part of the kinetic term of Eq. kinop-alpha that needs a
+//            transform of the product alpha phi (spin-imbalanced ASLDA, alpha
+//            varying in space): adds +1/2 T(alpha_a u) to the u row and
+//            -1/2 T(alpha_b v) to the v row of h0 (which holds the current term
+//            already), and adds Re sum_r [u^* T(alpha_a u) - v^* T(alpha_b v)]
+//            (its whole kinetic part of <H>_n, T being Hermitian) to the per-CTA
+//            partials in ecur. T = -1/2 lap with the Nyquist mode kept.
 //   Both derivative modes use 1D transforms along one axis per derivative
 //   (the symbol i k_d is diagonal in k_d, so the other two axes need no
 //   transform): the slab is loaded once per axis (the second and third loads
@@ -63,8 +70,12 @@ template <typename R> using fx4 = typename fx4_of<R>::type;
 // MODE_X3 / MODE_X5: the predictor stage of AB3AM4 / AB5AM5 (MODE_X is AB4AM5's).
 enum Mode : int {
   MODE_X = 0, MODE_Y = 1, MODE_F = 2, MODE_HORNER = 3, MODE_EKIN = 4, MODE_GRAD = 5, MODE_X3 = 6, MODE_X5 = 7,
-  MODE_LAP = 8, MODE_AGRAD = 9, NMODES = 10
+  MODE_LAP = 8, MODE_AGRAD = 9, MODE_KALPHA = 10, NMODES = 11
 };
+// Modes that apply H (the only ones with a general-functional instance).
+__host__ __device__ constexpr bool applies_h(int m) {
+  return m == MODE_X || m == MODE_Y || m == MODE_F || m == MODE_HORNER || m == MODE_X3 || m == MODE_X5;
+}
 
 template <typename R>
 struct StageArgs {
@@ -90,9 +101,11 @@ struct StageArgs {
   double ycoef;      // Y: coefficient of the new term of the corrector (251/720 for AM5, 9/24 for AM4)
   const double* wm;  // GRAD: frozen weights f(-E_n), f(E_n)
   const double* wp;
-  const fx4<R>* av;  // AGRAD: [M] {A_x, A_y, A_z, div A / 2} (current potential, A != 1)
+  const fx4<R>* av;  // AGRAD: [M] {A_x, A_y, A_z, div A / 2} (current potential, A != 1) of the u row
+  const fx4<R>* av2; // AGRAD: the same for the v row (NULL: av; spin-imbalanced ASLDA: A_b)
+  const cx<R>* alf;  // KALPHA and the general H modes: [M] {alpha_a / 2, alpha_b / 2} (NULL: constant A)
   const cx<R>* cur;  // X, Y, F, HORNER: current term -(i/2){A, grad} phi of the input states (NULL: none)
-  double* ecur;      // AGRAD: writes, stage modes read: [n][16] per-CTA partials of its <H>_n part
+  double* ecur;      // AGRAD, KALPHA: write / add, stage modes read: [n][16] per-CTA partials of their <H>_n part
   int compute_e;
   int normalize;
   int nstates;
@@ -389,7 +402,13 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
 
 // One state of a stage, inlined into the kernel (so that the arguments stay
 // kernel parameters, read where they are used).
-template <class G, int MODE>
+// GEN = false: the kinetic term is A T with a constant A folded into the
+// symbol, one potential W for both rows, and no current term (A = 1, BdG).
+// GEN = true adds, when the pointers are set, the current term `cur` and its
+// <H>_n partials `ecur`; with `alf` (spin-imbalanced ASLDA) the rows take
+// alpha_a/2 T u and -alpha_b/2 T v, the v row its own W_b (fourth field), and
+// the kinetic part of <H>_n comes from the KALPHA partials instead of Parseval.
+template <class G, int MODE, bool GEN>
 __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, const int n, const int ncl) {
   using C = typename G::C;
   using R = typename G::R;
@@ -423,6 +442,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   // before the wait for the slab, so both round trips overlap.
   constexpr bool XM = MODE == MODE_X || MODE == MODE_X3 || MODE == MODE_X5;  // a predictor stage
   const bool need_e = XM || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
+  const bool spin2 = GEN && a.alf != nullptr;  // per-site alpha, W_b in the fourth field
   constexpr int UPMAX = G::MINB >= 3 ? 4 : 16;  // fewer under a tight register budget
   constexpr int UP = (G::NS + G::BT - 1) / G::BT < UPMAX ? (G::NS + G::BT - 1) / G::BT : UPMAX;
   fx4<R> wd[UP];
@@ -446,7 +466,8 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       if (s < G::NS) {
         const C u = scl(buf[sidx(s)], sin_), v = scl(buf[G::SLAB + sidx(s)], sin_);
         const C dv = mul(mk<C>(wd[k].y, wd[k].z), v);
-        const R t = (wd[k].x * (u.x * u.x + u.y * u.y - v.x * v.x - v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
+        const R wb = spin2 ? wd[k].w : wd[k].x;
+        const R t = (wd[k].x * (u.x * u.x + u.y * u.y) - wb * (v.x * v.x + v.y * v.y) + R(2) * (u.x * dv.x + u.y * dv.y)) - ec;
         const R ns = ep + t;
         ec = (ns - ep) - t;
         ep = ns;
@@ -455,6 +476,15 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   }
 
   __syncthreads();  // the slab is read above before the z pass overwrites it
+  if constexpr (MODE == MODE_KALPHA) {
+    // the transform acts on alpha_a u and alpha_b v
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const cx<R> al = a.alf[gs0 + s];
+      buf[sidx(s)] = scl(buf[sidx(s)], R(2) * al.x);
+      buf[G::SLAB + sidx(s)] = scl(buf[G::SLAB + sidx(s)], R(2) * al.y);
+    }
+    __syncthreads();
+  }
   const R sin2 = sin_ * sin_;
   local_pass<G, 2, false>(buf, twz);
   __syncthreads();
@@ -470,7 +500,8 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   // CTA reads only its own shared memory, so no CTA has to outlive another.
   double* slot = red + G::RED_E;
   {
-    double v0 = MODE == MODE_EKIN ? double(eku) : double(ep) + (double(eku) - double(ekv)) * double(sin2);
+    double v0 = MODE == MODE_EKIN ? double(eku)
+                : (spin2 ? double(ep) : double(ep) + (double(eku) - double(ekv)) * double(sin2));
     double v1 = double(ekv);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -503,8 +534,9 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   }
   double En = 0.0, Ev = 0.0;
   for (int r = 0; r < G::CS; ++r) { En += slot[r]; Ev += slot[G::CS + r]; }
-  if (a.ecur && MODE != MODE_EKIN)
-    for (int r = 0; r < G::CS; ++r) En += a.ecur[size_t(n) * 16 + r];
+  if constexpr (GEN)
+    if (a.ecur)
+      for (int r = 0; r < G::CS; ++r) En += a.ecur[size_t(n) * 16 + r];
   En *= a.dV;
   Ev *= a.dV;
   if (MODE == MODE_EKIN) { En *= double(sin2); Ev *= double(sin2); }
@@ -530,6 +562,32 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       const C bp = scl(add(mulc(uu, lv), mulc(lu, vv)), R(-0.5) * dw);  // u conj(lap v) + conj(v) lap u
       out[g] = mk<C>(divj, R(0));
       out[G::M + g] = bp;
+    }
+    return;
+  } else if constexpr (MODE == MODE_KALPHA) {
+    // buf holds T(alpha phi) of the stored (unscaled) slab
+    C* out = a.h0 + sbase;
+    R kp = 0, kc = 0;  // compensated partial of Re sum [u^* T(alpha_a u) - v^* T(alpha_b v)]
+    for (int s = tid; s < G::NS; s += G::BT) {
+      const int g = gs0 + s;
+      const C uu = scl(in[g], sin_), vv = scl(in[G::M + g], sin_);
+      const C tu = scl(buf[sidx(s)], sin_), tv = scl(buf[G::SLAB + sidx(s)], sin_);
+      out[g] = add(out[g], scl(tu, R(0.5)));
+      out[G::M + g] = sub(out[G::M + g], scl(tv, R(0.5)));
+      const R t = (uu.x * tu.x + uu.y * tu.y - vv.x * tv.x - vv.y * tv.y) - kc;
+      const R ns = kp + t;
+      kc = (ns - kp) - t;
+      kp = ns;
+    }
+    double v = double(kp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[G::RED_WB + (tid >> 5)] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < G::NW; ++i) t += red[G::RED_WB + i];
+      a.ecur[size_t(n) * 16 + rank] += t;  // the current-term launch wrote this CTA's slot
     }
     return;
   } else {
@@ -584,13 +642,24 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
           const C uu = scl(u[k], sin_), vv = scl(v[k], sin_);
           const R w = wd[k].x;
           const C d = mk<C>(wd[k].y, wd[k].z);
-          // (H - <H>_n) phi for both components (Eq. dpsidt-Hpsi, A = 1)
+          // (H - <H>_n) phi for both components (Eq. dpsidt-Hpsi; A T phi from the symbol)
+          R ka = sin_, kb = sin_, wb = w;
+          if constexpr (GEN) {
+            if (spin2) {  // Eq. kinop-alpha: alpha/2 T on each row, W_b on the v row
+              const cx<R> al = a.alf[g];
+              ka *= al.x;
+              kb *= al.y;
+              wb = wd[k].w;
+            }
+          }
           C hm[2];
-          hm[0] = sub(add(add(scl(buf[b], sin_), scl(uu, w)), mul(d, vv)), scl(uu, Er));
-          hm[1] = sub(sub(sub(mulc(uu, d), scl(buf[G::SLAB + b], sin_)), scl(vv, w)), scl(vv, Er));
-          if (a.cur) {  // current term (A != 1), the same operator on both components
-            hm[0] = add(hm[0], a.cur[sbase + g]);
-            hm[1] = add(hm[1], a.cur[sbase + G::M + g]);
+          hm[0] = sub(add(add(scl(buf[b], ka), scl(uu, w)), mul(d, vv)), scl(uu, Er));
+          hm[1] = sub(sub(sub(mulc(uu, d), scl(buf[G::SLAB + b], kb)), scl(vv, wb)), scl(vv, Er));
+          if constexpr (GEN) {
+            if (a.cur) {  // current term (and with alf the transformed alpha phi parts)
+              hm[0] = add(hm[0], a.cur[sbase + g]);
+              hm[1] = add(hm[1], a.cur[sbase + G::M + g]);
+            }
           }
           const C ph[2] = {uu, vv};
 #pragma unroll
@@ -729,17 +798,19 @@ __device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, c
         }
       } else {
         const fx4<R> av = a.av[g];
+        const fx4<R> bv = a.av2 ? a.av2[g] : av;  // the v row's current potential
         const R Ad = d == 0 ? av.x : (d == 1 ? av.y : av.z);
+        const R Bd = d == 0 ? bv.x : (d == 1 ? bv.y : bv.z);
         C su, sv;
         if (d == 2) {
           su = scl(uu, av.w);
-          sv = scl(vv, av.w);
+          sv = scl(vv, bv.w);
         } else {
           su = out[g];
           sv = out[G::M + g];
         }
         su = add(su, scl(du, Ad));
-        sv = add(sv, scl(dv, Ad));
+        sv = add(sv, scl(dv, Bd));
         if (d == 0) {
           su = mul_mi(su);
           sv = mul_mi(sv);
@@ -774,7 +845,7 @@ __device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, c
 // slab and the reduction slots only after the next state's first cluster
 // barrier. (The one-state form is a separate instance because the loop makes
 // the compiler keep per-state invariants in registers.)
-template <class G, int MODE, bool PERSIST>
+template <class G, int MODE, bool PERSIST, bool GEN = false>
 __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_constant__ StageArgs<typename G::R> a) {
   using C = typename G::C;
   using R = typename G::R;
@@ -794,12 +865,12 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_cons
     for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl) {
       __syncthreads();
       if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, n, ncl);
-      else stage_state<G, MODE>(a, n, ncl);
+      else stage_state<G, MODE, GEN>(a, n, ncl);
     }
   } else {
     __syncthreads();
     if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
-    else stage_state<G, MODE>(a, blockIdx.x / G::CS, ncl);
+    else stage_state<G, MODE, GEN>(a, blockIdx.x / G::CS, ncl);
   }
 }
 

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libwslda_td.so")
 
 FP64, MIXED = 0, 1
-SLDA_A1, BDG, SLDA = 0, 1, 2
+SLDA_A1, BDG, SLDA, ASLDA = 0, 1, 2, 3
 A_ASLDA = 1.094  # A_a(0) of the ASLDA functional (Sec. 2.4)
 SCHEMES = {"AB4AM5": 0, "AB3AM4": 1, "AB5AM5": 2}
 # B of the spin-symmetric ASLDA functional (Sec. 2.4): 2^(2/3) [0.357 - 2 A(0) 2^(-5/3)], A(0) = 1.094
@@ -41,7 +41,8 @@ class Lattice(ct.Structure):
 
 class Functional(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("B", ct.c_double), ("C", ct.c_double), ("inv_4pi_a", ct.c_double),
-                ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double), ("A", ct.c_double)]
+                ("mu", ct.c_double), ("ec", ct.c_double), ("rho_floor", ct.c_double), ("A", ct.c_double),
+                ("mu_b", ct.c_double)]
 
 
 class Uniform(ct.Structure):
@@ -86,6 +87,8 @@ def _load():
         "wslda_get_states": (I, [P, I, P, I]),
         "wslda_get_densities": (I, [P, I, P, P, P, P]),
         "wslda_get_fields": (I, [P, I, P, P]),
+        "wslda_get_spin_densities": (I, [P, I, P, P, P, P, P, P, P]),
+        "wslda_get_spin_fields": (I, [P, I, P, P, P]),
         "wslda_get_energy": (I, [P, I, ct.POINTER(Energy)]),
         "wslda_eval_f": (I, [P, I, P]),
         "wslda_save": (I, [P, ct.c_char_p]),
@@ -141,7 +144,7 @@ def uniform_solve(shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, inv_4p
                   rho_sigma=1.0 / (6 * np.pi ** 2), delta0=0.0) -> dict:
     """Uniform plane-wave BCS solution on the lattice (wslda_uniform_solve)."""
     lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
-    fn = Functional(int(kind), float(B), 0.0, float(inv_4pi_a), 0.0, float(ec), 1e-12, 1.0)
+    fn = Functional(int(kind), float(B), 0.0, float(inv_4pi_a), 0.0, float(ec), 1e-12, 1.0, 0.0)
     out = Uniform()
     st = lib.wslda_uniform_solve(ct.byref(lat), ct.byref(fn), float(rho_sigma), float(delta0), ct.byref(out))
     if st:
@@ -251,11 +254,12 @@ class Context:
         self._check(lib.wslda_set_integrator(self._h, SCHEMES[scheme]))
 
     def add_box(self, shape, spacing=(1.0, 1.0, 1.0), *, kind=SLDA_A1, B=0.0, C=-1.0, inv_4pi_a=0.0, mu=0.0,
-                ec=-1.0, rho_floor=1e-12, A=1.0, nstates: int) -> int:
-        """kind SLDA with A != 1 carries the current terms (inverse effective mass A)."""
+                ec=-1.0, rho_floor=1e-12, A=1.0, mu_b=None, nstates: int) -> int:
+        """kind SLDA with A != 1 carries the current terms (inverse effective mass A);
+        kind ASLDA is the spin-imbalanced functional with mu (species a) and mu_b."""
         lat = Lattice(*[int(v) for v in shape], *[float(v) for v in spacing])
         fn = Functional(int(kind), float(B), float(C), float(inv_4pi_a), float(mu), float(ec), float(rho_floor),
-                        float(A))
+                        float(A), float(mu if mu_b is None else mu_b))
         r = lib.wslda_add_box(self._h, ct.byref(lat), ct.byref(fn), int(nstates))
         if r < 0:
             self._check(-r)
@@ -365,6 +369,24 @@ class Context:
                                             t.ctypes.data_as(ct.c_void_p) if tau else None,
                                             j.ctypes.data_as(ct.c_void_p) if current else None))
         return (rho, nu) if not (tau or current) else (rho, nu, t, j)
+
+    def get_spin_densities(self, box: int) -> dict:
+        """Per-species densities of an ASLDA box: rho_a, rho_b, nu, tau_a, tau_b, j_a, j_b."""
+        M = self._M(box)
+        out = {"rho_a": np.empty(M), "rho_b": np.empty(M), "nu": np.empty(M, dtype=np.complex128),
+               "tau_a": np.empty(M), "tau_b": np.empty(M), "j_a": np.empty((3, M)), "j_b": np.empty((3, M))}
+        p = lambda k: out[k].ctypes.data_as(ct.c_void_p)
+        self._check(lib.wslda_get_spin_densities(self._h, box, p("rho_a"), p("rho_b"), p("nu"), p("tau_a"),
+                                                 p("tau_b"), p("j_a"), p("j_b")))
+        return out
+
+    def get_spin_fields(self, box: int):
+        """(V_a, V_b, Delta) of an ASLDA box."""
+        M = self._M(box)
+        Va, Vb, D = np.empty(M), np.empty(M), np.empty(M, dtype=np.complex128)
+        self._check(lib.wslda_get_spin_fields(self._h, box, Va.ctypes.data_as(ct.c_void_p),
+                                              Vb.ctypes.data_as(ct.c_void_p), D.ctypes.data_as(ct.c_void_p)))
+        return Va, Vb, D
 
     def get_fields(self, box: int):
         M = self._M(box)
