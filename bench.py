@@ -108,6 +108,9 @@ def parse():
                         "(1.094 = A_a(0) of the ASLDA functional)")
     p.add_argument("--stationary", action="store_true",
                    help="stationary start instead of the Taylor start (short profiling runs)")
+    p.add_argument("--aslda", action="store_true",
+                   help="spin-imbalanced ASLDA (Secs. 2.3-2.4): half the states and their partners (whole "
+                        "spectrum), mu_a != mu_b, v weights halved (polarised); FP64 arm off by default")
     return p.parse_args()
 
 
@@ -210,25 +213,42 @@ def resolve(args, name):
 
 
 # ------------------------------------------------------------------ GPU arms
-def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0):
+ASLDA_DMU = (0.02, -0.02)  # mu_a - mu, mu_b - mu of the spin-imbalanced workload
+
+
+def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0, aslda=False):
     """A context with one box of the workload (SLDA with the uniform seed's
-    B, C, mu; A != 1 adds the current terms)."""
+    B, C, mu; A != 1 adds the current terms; aslda: the spin-imbalanced
+    functional with C = -11.11 and mu_a, mu_b around the seed's mu)."""
     from paper_2602_08982_b300 import inputs
     shape = wl["shape"]
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(prec, stream=stream)
     ctx.set_integrator(scheme)
-    box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"],
-                      mu=u["mu"] if mu is None else mu, A=A, nstates=wl["nstates"])
+    m = u["mu"] if mu is None else mu
+    if aslda:
+        box = ctx.add_box(shape, kind=W.ASLDA, C=-11.11, mu=m + ASLDA_DMU[0], mu_b=m + ASLDA_DMU[1],
+                          nstates=wl["nstates"])
+    else:
+        box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=m, A=A,
+                          nstates=wl["nstates"])
     ctx.set_vext(box, inputs.harmonic_trap(shape, wl["omega"]))
     return ctx, box, u
 
 
-def fill_workload(W, ctx, box, u, wl):
+def fill_workload(W, ctx, box, u, wl, aslda=False):
     """Uniform plane-wave BCS states of the lattice (Delta0 = 0.5 eF), with the
-    vortex phase imprinted on u when the workload has one (reading P2)."""
+    vortex phase imprinted on u when the workload has one (reading P2). An
+    ASLDA box gets half the states and their partners, and the weights of its
+    v rows halved (a polarised start)."""
     from paper_2602_08982_b300 import inputs
     ctx.fill_uniform_states(box, u["mu_eff"], u["delta"])
+    if aslda:
+        n = wl["nstates"]
+        h = n // 2
+        wm = np.concatenate([np.full(h, 0.5), np.zeros(n - h)])
+        wp = np.concatenate([np.zeros(h), np.ones(n - h)])
+        ctx.set_weights(box, wm, wp)
     if wl["vortex"]:
         ctx.imprint_phase(box, 0, inputs.vortex_phase(wl["shape"]))
 
@@ -297,8 +317,8 @@ def run_arm(W, torch, prec, args, wl, rank, world, dev):
         ctx.load_states(box, start["phi"])
         ctx.start(True, args.dt)               # a static solution: stationary start
     else:
-        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, A=args.A)
-        fill_workload(W, ctx, box, u, wl)
+        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, A=args.A, aslda=args.aslda)
+        fill_workload(W, ctx, box, u, wl, args.aslda)
         if args.friction:
             fa, fb, fg = (float(x) for x in args.friction.split(","))
             M = shape[0] * shape[1] * shape[2]
@@ -334,7 +354,7 @@ def run_arm(W, torch, prec, args, wl, rank, world, dev):
     M = shape[0] * shape[1] * shape[2]
     units = float(nstates) * M * args.steps
     value = job_rate(units, world, ms * 1e-3)
-    bx, fx = stage_x_algorithmic(prec, shape, args.integrator, args.A != 1.0)
+    bx, fx = stage_x_algorithmic(prec, shape, args.integrator, args.A != 1.0 or args.aslda)
     x_ms, x_n = kt["stage_x"]
     x_avg = x_ms / max(x_n, 1)
     y_ms, y_n = kt["stage_y"]
@@ -574,6 +594,24 @@ def oracle_sample(wl, n, A=1.0):
     return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, wl["omega"])), phi, lat
 
 
+def oracle_sample_aslda(wl, n):
+    """Spin-imbalanced oracle system of the ASLDA workload: n/2 of the uniform
+    states and their partners, weights as fill_workload sets them; returns
+    (start, step) closures over it and the lattice."""
+    from oracle import aslda as a
+    o, sysm, phi, lat = oracle_sample(wl, max(1, n // 2))
+    h = phi.shape[0]
+    u, v = phi[:, 0], phi[:, 1]
+    phi2 = np.concatenate([phi, np.stack([np.conj(v), -np.conj(u)], axis=1)])
+    fm = np.concatenate([np.full(h, 0.5), np.zeros(h)])
+    fp = np.concatenate([np.zeros(h), np.ones(h)])
+    m = sysm.fn.mu
+    sys_i = a.ImbalancedSystem(lat, a.ASLDA(mu_a=m + ASLDA_DMU[0], mu_b=m + ASLDA_DMU[1]), sysm.vext, sysm.vext, fp, fm)
+    start = lambda dt: a.start(sys_i, phi2, dt, True)
+    step = lambda st, dt: o.abm_step(sys_i, st, dt, "AB4AM5")
+    return start, step, lat, 2 * h
+
+
 def oracle_stepper(o, scheme):
     """(start, step) of the oracle for the scheme: Alg. 2 itself for AB4AM5."""
     if scheme == "AB4AM5":
@@ -582,7 +620,17 @@ def oracle_stepper(o, scheme):
             (lambda sysm, st, dt: o.abm_step(sysm, st, dt, scheme)))
 
 
-def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
+def sample_stepper(wl, n, dt, scheme, A, aslda):
+    """(state, step, lattice, states) of the oracle on n states of the workload."""
+    if aslda:
+        start, step, lat, n = oracle_sample_aslda(wl, n)
+        return start(dt), (lambda st: step(st, dt)), lat, n
+    o, sysm, phi, lat = oracle_sample(wl, n, A)
+    start, step = oracle_stepper(o, scheme)
+    return start(sysm, phi, dt), (lambda st: step(sysm, st, dt)), lat, n
+
+
+def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0, aslda=False):
     """The oracle as it stands, on a bounded sample of the workload: the same
     lattice and trap with a subset of the uniform plane-wave states, timed over
     whole ABM steps after a stationary start."""
@@ -590,11 +638,9 @@ def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
     max_states = min(max_states, shape[0] * shape[1] * shape[2])
     n = min(64, max_states)
     while True:
-        o, sysm, phi, lat = oracle_sample(wl, n, A)
-        start, step = oracle_stepper(o, scheme)
-        st = start(sysm, phi, dt)
+        st, step, lat, n = sample_stepper(wl, n, dt, scheme, A, aslda)
         t0 = time.perf_counter()
-        st = step(sysm, st, dt)
+        st = step(st)
         one = time.perf_counter() - t0
         if one * 4 > seconds or n >= max_states:
             break
@@ -602,7 +648,7 @@ def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0):
     k = max(1, int(seconds / max(one, 1e-3)))
     t0 = time.perf_counter()
     for _ in range(k):
-        st = step(sysm, st, dt)
+        st = step(st)
     sec = time.perf_counter() - t0
     return {"value": n * lat.M * k / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "n": n,
             "sample": f"{n} of the workload's states on the same {shape[0]}x{shape[1]}x{shape[2]} trap, {k} {scheme} "
@@ -619,15 +665,14 @@ def reference_arm(args, wl):
             return
     # each step: one oracle step of the scheme over a bounded sample of the
     # states, sized so that one step takes about a second
-    n = cpu_oracle_rate(wl, args.dt, args.cpu_seconds / 4, scheme=args.integrator, A=args.A)["n"]
-    o, sysm, phi, lat = oracle_sample(wl, n, args.A)
-    start, step = oracle_stepper(o, args.integrator)
-    st = start(sysm, phi, args.dt)
+    n = cpu_oracle_rate(wl, args.dt, args.cpu_seconds / 4, scheme=args.integrator, A=args.A,
+                        aslda=args.aslda)["n"]
+    st, step, lat, n = sample_stepper(wl, n, args.dt, args.integrator, args.A, args.aslda)
     for _ in range(args.warmup):
-        st = step(sysm, st, args.dt)
+        st = step(st)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        st = step(sysm, st, args.dt)
+        st = step(st)
     sec = time.perf_counter() - t0
     value = n * lat.M * args.steps / sec
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -645,6 +690,15 @@ def reference_arm(args, wl):
 
 def workload_config(args, wl, precision):
     shape = wl["shape"]
+    if args.aslda:
+        return {"workload": f"spin-imbalanced ASLDA TDSLDA {args.integrator} step, {wl['text']} "
+                            f"({wl['nstates'] // 2} plane-wave states and their partners)",
+                "lattice": list(shape), "nstates": wl["nstates"], "trap_omega": wl["omega"], "vortex": wl["vortex"],
+                "dt": args.dt, "functional": "ASLDA: A(p), B(p) as printed, C = -11.11, "
+                                             f"mu_a - mu = {ASLDA_DMU[0]}, mu_b - mu = {ASLDA_DMU[1]}",
+                "init": "uniform plane-wave BCS states with partners, v weights halved (polarised), Taylor start",
+                "precision": precision, "l2": "inputs larger than L2 (state buffers >> 126 MB), no flush needed",
+                "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
     return {"workload": f"TDSLDA {args.integrator} step, {wl['text']}",
             "lattice": list(shape), "nstates": wl["nstates"], "trap_omega": wl["omega"], "vortex": wl["vortex"],
             "dt": args.dt,
@@ -660,6 +714,12 @@ def workload_config(args, wl, precision):
 
 def main():
     args = parse()
+    if args.aslda:  # the spin-imbalanced line: its own workload, the mixed arm and its CPU baseline
+        if args.workload == "elongated" and not args.shape:
+            args.workload = "cube32"
+        args.no_e2e = args.no_batched = args.no_oracle_check = args.no_cufft = True
+        if args.precision == "both":
+            args.precision = "mixed"
     wl = resolve(args, args.workload)
     if args.impl == "reference":
         reference_arm(args, wl)
@@ -674,7 +734,7 @@ def main():
     solo = rank == 0 and world == 1
     cpu = None
     if solo and not args.no_cpu:
-        cpu = cpu_oracle_rate(wl, args.dt, args.cpu_seconds, scheme=args.integrator, A=args.A)
+        cpu = cpu_oracle_rate(wl, args.dt, args.cpu_seconds, scheme=args.integrator, A=args.A, aslda=args.aslda)
     arms = {}
     if args.precision in ("both", "mixed"):
         arms["mixed"] = run_arm(W, torch, W.MIXED, args, wl, rank, world, local)

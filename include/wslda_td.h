@@ -279,8 +279,16 @@ wslda_status wslda_uniform_solve(const wslda_lattice* lat, const wslda_functiona
 /* Fill a box with the positive-energy plane-wave states of a uniform solution
  * (mu_eff, delta > 0), computed on the device. State i takes the flattened
  * k index kidx[i] (host int64 [n]) or i when kidx is NULL (then n <= M).
- * Weights are set to T = 0. Replaces wslda_load_states. */
+ * Weights are set to T = 0. Replaces wslda_load_states. An aslda box (whole
+ * spectrum) takes n/2 such states (n even; kidx then has n/2 entries) followed
+ * by their negative-energy partners [v^*, -u^*], with the T = 0 weights of
+ * both signs of E. */
 wslda_status wslda_fill_uniform_states(wslda_ctx* ctx, int box, double mu_eff, double delta, const int64_t* kidx);
+
+/* Replace the frozen weights (Sec. 2.5) of the loaded states, before
+ * wslda_start: w_minus = f(-E_n), w_plus = f(E_n), host [n] doubles (NULL:
+ * the T = 0 values 1 and 0). Non-finite weights give WSLDA_ENAN. */
+wslda_status wslda_set_weights(wslda_ctx* ctx, int box, const double* w_minus, const double* w_plus);
 
 /* Multiply component `comp` (0 = u, 1 = v) of every loaded state of the box
  * by a site-dependent complex factor phase[r] ([M] complex, host or device),

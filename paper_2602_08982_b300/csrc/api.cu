@@ -1229,22 +1229,29 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, dou
   if (!b) return fail(c, WSLDA_EINVAL, "fill_uniform_states: bad box");
   if (c->started) return fail(c, WSLDA_ESTATE, "fill_uniform_states after wslda_start");
   if (!(delta > 0.0) || !std::isfinite(mu_eff)) return fail(c, WSLDA_EINVAL, "fill_uniform_states: need delta > 0");
-  if (!kidx && b->n > b->M) return fail(c, WSLDA_EINVAL, "more states than lattice momenta");
+  // an ASLDA box takes n/2 positive-energy states and their partners
+  const int64_t nk = b->aslda ? b->n / 2 : b->n;
+  if (b->aslda && (b->n & 1)) return fail(c, WSLDA_EINVAL, "fill_uniform_states: an ASLDA box needs an even count");
+  if (!kidx && nk > b->M) return fail(c, WSLDA_EINVAL, "more states than lattice momenta");
   int64_t* kd = nullptr;
-  if (kidx && b->n > 0) {
-    for (int64_t i = 0; i < b->n; ++i)
+  if (kidx && nk > 0) {
+    for (int64_t i = 0; i < nk; ++i)
       if (kidx[i] < 0 || kidx[i] >= b->M) return fail(c, WSLDA_EINVAL, "k index out of range");
-    CUDA_TRY(c, cudaMalloc(&kd, size_t(b->n) * 8));
-    CUDA_TRY(c, cudaMemcpyAsync(kd, kidx, size_t(b->n) * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMalloc(&kd, size_t(nk) * 8));
+    CUDA_TRY(c, cudaMemcpyAsync(kd, kidx, size_t(nk) * 8, cudaMemcpyHostToDevice, c->stream));
   }
   cudaError_t e = launch_fill_plane_waves(b->slot[b->iphi], c->prec == WSLDA_MIXED, b->lat, mu_eff, delta, kd, b->n,
-                                          c->stream);
+                                          b->aslda ? 1 : 0, c->stream);
   if (e == cudaSuccess) e = launch_fill(b->sc[b->iphi], 1.0, std::max<int64_t>(b->n, 1), c->stream);
   cudaError_t e2 = cudaStreamSynchronize(c->stream);
   if (kd) cudaFree(kd);
   if (e != cudaSuccess || e2 != cudaSuccess)
     return fail(c, WSLDA_ECUDA, std::string("fill_uniform_states: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   std::vector<double> wm(std::max<int64_t>(b->n, 1), 1.0), wp(std::max<int64_t>(b->n, 1), 0.0);
+  for (int64_t i = nk; i < b->n; ++i) {  // T = 0: the partners (E < 0) have f(E) = 1, f(-E) = 0
+    wm[i] = 0.0;
+    wp[i] = 1.0;
+  }
   CUDA_TRY(c, cudaMemcpyAsync(b->wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(b->wp, wp.data(), wp.size() * 8, cudaMemcpyHostToDevice, c->stream));
   if (c->prec == WSLDA_MIXED) {
@@ -1257,6 +1264,15 @@ wslda_status wslda_fill_uniform_states(wslda_ctx* c, int box, double mu_eff, dou
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   b->loaded = true;
   return WSLDA_OK;
+}
+
+wslda_status wslda_set_weights(wslda_ctx* c, int box, const double* w_minus, const double* w_plus) {
+  CHECK_CTX(c);
+  Box* b = get_box(c, box);
+  if (!b) return fail(c, WSLDA_EINVAL, "set_weights: bad box");
+  if (!b->loaded) return fail(c, WSLDA_ESTATE, "set_weights before the states are loaded");
+  if (c->started) return fail(c, WSLDA_ESTATE, "set_weights after wslda_start");
+  return set_weights(c, *b, w_minus, w_plus);
 }
 
 wslda_status wslda_imprint_phase(wslda_ctx* c, int box, int comp, const double* phase, int on_device) {

@@ -200,7 +200,7 @@ cudaError_t launch_aslda_energy(int M, const double* rho_a, const double* rho_b,
 
 // Plane-wave states of a uniform solution (uniform.cu); dst is float2 or double2.
 cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,
-                                    const int64_t* kidx_dev, int64_t n, cudaStream_t s);
+                                    const int64_t* kidx_dev, int64_t n, int partners, cudaStream_t s);
 
 // Static self-consistent solve (scf.cu): the box buffers it reads and writes.
 struct ScfBox {

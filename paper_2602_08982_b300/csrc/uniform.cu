@@ -72,13 +72,20 @@ double solve_mu_eff(const std::vector<double>& e, double d, double vol, double r
   return 0.5 * (lo + hi);
 }
 
+// partners = 0: n states (U_k, V_k) e^{ik.r}/sqrt(V). partners = 1: states
+// n/2 .. n-1 are the negative-energy partners [v^*, -u^*] of states 0 .. n/2-1
+// (the whole spectrum of the spin-imbalanced problem, Eq. HpsiEpsi).
 __global__ void fill_plane_waves(double2* out_d, float2* out_f, int nx, int ny, int nz, double dx, double dy,
-                                 double dz, double mu_eff, double delta, const int64_t* kidx, int64_t n) {
+                                 double dz, double mu_eff, double delta, const int64_t* kidx, int64_t n,
+                                 int partners) {
   const int64_t M = int64_t(nx) * ny * nz;
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= n * M) return;
   const int64_t st = idx / M, r = idx % M;
-  const int64_t k = kidx ? kidx[st] : st;
+  const int64_t half = partners ? n / 2 : n;
+  const bool partner = partners && st >= half;
+  const int64_t sk = partner ? st - half : st;
+  const int64_t k = kidx ? kidx[sk] : sk;
   const int lx = int(k / (int64_t(ny) * nz)), ly = int((k / nz) % ny), lz = int(k % nz);
   const int ix = int(r / (int64_t(ny) * nz)), iy = int((r / nz) % ny), iz = int(r % nz);
   auto kv = [](int l, int nn, double d) {
@@ -97,12 +104,15 @@ __global__ void fill_plane_waves(double2* out_d, float2* out_f, int nx, int ny, 
   double s, c;
   sincospi(2.0 * frac, &s, &c);
   const int64_t base = st * 2 * M + r;
+  // partner: u = conj(V_k e^{ik.r}) = V_k e^{-ik.r}, v = -conj(U_k e^{ik.r}) = -U_k e^{-ik.r}
+  const double ur = partner ? Vk * c : Uk * c, ui = partner ? -Vk * s : Uk * s;
+  const double vr = partner ? -Uk * c : Vk * c, vi = partner ? Uk * s : Vk * s;
   if (out_d) {
-    out_d[base] = make_double2(Uk * c, Uk * s);
-    out_d[base + M] = make_double2(Vk * c, Vk * s);
+    out_d[base] = make_double2(ur, ui);
+    out_d[base + M] = make_double2(vr, vi);
   } else {
-    out_f[base] = make_float2(float(Uk * c), float(Uk * s));
-    out_f[base + M] = make_float2(float(Vk * c), float(Vk * s));
+    out_f[base] = make_float2(float(ur), float(ui));
+    out_f[base + M] = make_float2(float(vr), float(vi));
   }
 }
 
@@ -110,13 +120,13 @@ __global__ void fill_plane_waves(double2* out_d, float2* out_f, int nx, int ny, 
 
 namespace wslda {
 cudaError_t launch_fill_plane_waves(void* dst, int is_float, const wslda_lattice& lat, double mu_eff, double delta,
-                                    const int64_t* kidx_dev, int64_t n, cudaStream_t s) {
+                                    const int64_t* kidx_dev, int64_t n, int partners, cudaStream_t s) {
   const int64_t M = int64_t(lat.nx) * lat.ny * lat.nz;
   const int64_t total = n * M;
   if (total == 0) return cudaSuccess;
   fill_plane_waves<<<unsigned((total + 255) / 256), 256, 0, s>>>(
       is_float ? nullptr : static_cast<double2*>(dst), is_float ? static_cast<float2*>(dst) : nullptr, lat.nx,
-      lat.ny, lat.nz, lat.dx, lat.dy, lat.dz, mu_eff, delta, kidx_dev, n);
+      lat.ny, lat.nz, lat.dx, lat.dy, lat.dz, mu_eff, delta, kidx_dev, n, partners);
   return cudaGetLastError();
 }
 }  // namespace wslda

@@ -99,6 +99,7 @@ def _load():
         "wslda_set_profiling": (I, [P, I]),
         "wslda_uniform_solve": (I, [ct.POINTER(Lattice), ct.POINTER(Functional), D, D, ct.POINTER(Uniform)]),
         "wslda_fill_uniform_states": (I, [P, I, D, D, P]),
+        "wslda_set_weights": (I, [P, I, P, P]),
         "wslda_get_kernel_time": (I, [P, I, DP, ct.POINTER(I64)]),
         "wslda_get_variant": (I, [P, I, ct.c_char_p, I]),
         "wslda_set_graph": (I, [P, I, I]),
@@ -305,6 +306,12 @@ class Context:
         p, keep = _ptr(out, np.complex64, _is_device(out))
         self._check(lib.wslda_get_states_f32(self._h, box, p, int(_is_device(out))))
         return out
+
+    def set_weights(self, box: int, w_minus=None, w_plus=None):
+        """Frozen weights f(-E_n), f(E_n) of the loaded states (None: T = 0)."""
+        pm, km = _ptr(w_minus, np.float64, False)
+        pp, kp = _ptr(w_plus, np.float64, False)
+        self._check(lib.wslda_set_weights(self._h, box, pm, pp))
 
     def imprint_phase(self, box: int, comp: int, phase):
         """Multiply component comp (0 = u, 1 = v) of every state by phase[r]."""

@@ -137,3 +137,31 @@ def test_aslda_rejects_static_solve_and_friction():
         ctx.set_friction(box, 1.0)
     assert e.value.status == 8
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_aslda_uniform_fill_is_states_and_partners(prec):
+    """fill_uniform_states on an ASLDA box: n/2 plane-wave states, then their
+    partners [v^*, -u^*], with the T = 0 weights of both signs of E (the
+    densities then equal those of the spin-symmetric states: p = 0)."""
+    from cases import plane_waves
+    from paper_2602_08982_b300 import wslda as W
+    lat = o.Lattice(12, 12, 12)
+    seed = o.uniform_slda_seed(lat, 0.25, 1.0 / (6 * np.pi ** 2))
+    h = 150
+    kidx = np.sort(np.argsort(inputs.uniform01(606, lat.M))[:h]).astype(np.int64)
+    pw = plane_waves(lat, seed.mu_eff, seed.delta, kidx)
+    ref = np.concatenate([pw, np.stack([np.conj(pw[:, 1]), -np.conj(pw[:, 0])], axis=1)])
+    ctx = W.Context(prec)
+    box = ctx.add_box(lat.shape, kind=W.ASLDA, C=-11.11, mu=seed.mu, mu_b=seed.mu, nstates=2 * h)
+    ctx.fill_uniform_states(box, seed.mu_eff, seed.delta, kidx)
+    got = ctx.get_states(box)
+    d = ctx.get_spin_densities(box)
+    ctx.close()
+    assert rel(got, ref) < (1e-12 if prec == 0 else 2e-7)
+    fp = np.concatenate([np.zeros(h), np.ones(h)])
+    fm = np.concatenate([np.ones(h), np.zeros(h)])
+    dr = a.densities(ref, fp, fm, lat)
+    tol = TOL[prec]
+    assert rel(d["rho_a"], dr.rho_a) < tol and rel(d["rho_b"], dr.rho_b) < tol and rel(d["nu"], dr.nu) < tol
+    assert rel(dr.rho_a, dr.rho_b) < 1e-13
