@@ -238,7 +238,9 @@ def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0, aslda=False):
 
 def fill_workload(W, ctx, box, u, wl, aslda=False):
     """Uniform plane-wave BCS states of the lattice (Delta0 = 0.5 eF), with the
-    vortex phase imprinted on u when the workload has one (reading P2). An
+    vortex phase imprinted when the workload has one (reading P2: u e^{i theta/2},
+    v e^{-i theta/2}, a gauge transform that keeps the state set and its
+    partners complete and orthonormal, so the energy stays conserved). An
     ASLDA box gets half the states and their partners, and the weights of its
     v rows halved (a polarised start)."""
     from paper_2602_08982_b300 import inputs
@@ -249,8 +251,10 @@ def fill_workload(W, ctx, box, u, wl, aslda=False):
         wm = np.concatenate([np.full(h, 0.5), np.zeros(n - h)])
         wp = np.concatenate([np.zeros(h), np.ones(n - h)])
         ctx.set_weights(box, wm, wp)
-    if wl["vortex"]:
-        ctx.imprint_phase(box, 0, inputs.vortex_phase(wl["shape"]))
+    if wl["vortex"]:  # reading P2: u e^{i theta/2}, v e^{-i theta/2}
+        half = inputs.vortex_phase(wl["shape"], winding=0.5)
+        ctx.imprint_phase(box, 0, half)
+        ctx.imprint_phase(box, 1, np.conj(half))
 
 
 HISTORY_READS = {"AB3AM4": 2, "AB4AM5": 3, "AB5AM5": 4}
@@ -590,7 +594,9 @@ def oracle_sample(wl, n, A=1.0):
     Uk, Vk, _ = o.bcs_amplitudes(0.5 * (kx[ix] ** 2 + ky[iy] ** 2 + kz[iz] ** 2) - seed.mu_eff, seed.delta)
     phi = np.stack([Uk[:, None] * pw, Vk[:, None] * pw], axis=1)
     if wl["vortex"]:
-        phi[:, 0, :] *= inputs.vortex_phase(shape)[None, :]
+        half = inputs.vortex_phase(shape, winding=0.5)
+        phi[:, 0, :] *= half[None, :]
+        phi[:, 1, :] *= np.conj(half)[None, :]
     return o, o.TDSystem(lat, fn, vext=inputs.harmonic_trap(lat.shape, wl["omega"])), phi, lat
 
 

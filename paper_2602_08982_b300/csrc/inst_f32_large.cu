@@ -12,3 +12,4 @@ WSLDA_INSTANCE(float, 12, 12, 48, 1, 288, 1, 1, 2)
 WSLDA_INSTANCE(float, 24, 24, 96, 8, 288, 1, 1, 4)
 WSLDA_INSTANCE(float, 24, 24, 96, 12, 256, 1, 1, 4, 2)
 WSLDA_INSTANCE(float, 24, 24, 96, 12, 192, 1, 1, 4, 3)
+WSLDA_INSTANCE(float, 24, 24, 96, 12, 384, 1, 1, 4, 2)

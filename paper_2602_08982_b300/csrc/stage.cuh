@@ -141,7 +141,11 @@ struct Geometry {
   // sites per thread per batch in the epilogues (fewer under a tight register budget)
   static constexpr int U = sizeof(R_) == 4 ? (MINB_ >= 3 ? 2 : 4) : 2;
   static constexpr int P = NX / CS;         // x-planes per CTA
-  static constexpr int ZP = NZ + 1;         // odd row pitch (N even)
+  // Row pitch TZ x (an odd number >= NZ / TZ): the TZ lanes of a z pencil read
+  // consecutive elements and the rows of a warp start TZ elements apart modulo
+  // the bank period, so a z pass touches each bank once per wavefront (TZ = 1:
+  // an odd pitch; TZ = 4, NZ = 96: 100).
+  static constexpr int ZP = TZ * ((NZ / TZ) % 2 == 0 ? NZ / TZ + 1 : NZ / TZ);
   static constexpr int SLAB = P * NY * ZP;  // complex elements per component
   static constexpr int NS = P * NY * NZ;    // sites per CTA
   static constexpr int M = NX * NY * NZ;
@@ -233,6 +237,8 @@ __device__ __forceinline__ void local_pass(typename G::C* buf, const typename G:
   const int j = threadIdx.x % T;
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
+    // a warp whose pencils all lie past the end has nothing to do (warp-uniform)
+    if (it * PER + int(threadIdx.x & ~31u) / T >= NPEN) break;
     const int p = it * PER + threadIdx.x / T;
     const bool act = p < NPEN;
     const int pp = act ? p : 0;
@@ -278,6 +284,8 @@ __device__ __forceinline__ void local_deriv(typename G::C* buf, const typename G
   const int j = threadIdx.x % T;
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
+    // a warp whose pencils all lie past the end has nothing to do (warp-uniform)
+    if (it * PER + int(threadIdx.x & ~31u) / T >= NPEN) break;
     const int p = it * PER + threadIdx.x / T;
     const bool act = p < NPEN;
     const int pp = act ? p : 0;
@@ -330,6 +338,7 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
   for (int r = 0; r < G::CS; ++r) win[r] = dsmem_addr(buf, unsigned(r));
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
+    if (it * PER + int(threadIdx.x & ~31u) / T >= G::NCOL) break;  // warp-uniform: no column left
     const int q = rank * G::NCOL + it * PER + threadIdx.x / T;
     const bool act = (it * PER + threadIdx.x / T) < G::NCOL;
     const int qq = act ? q : rank * G::NCOL;

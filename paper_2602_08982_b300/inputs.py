@@ -67,12 +67,15 @@ def pairing_kick(shape, seed: int, amplitude: float) -> np.ndarray:
     return amplitude * complex_noise(shape, seed)
 
 
-def vortex_phase(shape, spacing=(1.0, 1.0, 1.0)) -> np.ndarray:
-    """exp(i theta(x, y)) for a straight vortex line along z whose core sits half a
-    cell off the central site, flattened [M] complex."""
+def vortex_phase(shape, spacing=(1.0, 1.0, 1.0), winding: float = 1.0) -> np.ndarray:
+    """exp(i winding theta(x, y)) for a straight vortex line along z whose core
+    sits half a cell off the central site, theta in (-pi, pi], flattened [M]
+    complex. winding = 1/2 gives the factor that multiplies u (and its
+    conjugate v) in the vortex start: the product u v^*, hence the pairing
+    field, then winds once around the line."""
     x, y, _ = centered_coords(shape, spacing)
     theta = np.arctan2(y - 0.5 * spacing[1], x - 0.5 * spacing[0])
-    ph = np.exp(1j * theta)
+    ph = np.exp(1j * winding * theta)
     return np.ascontiguousarray(np.broadcast_to(ph, tuple(shape)).reshape(-1))
 
 

@@ -65,8 +65,10 @@ def make_case(shape, spacing=(1.0, 1.0, 1.0), kind="slda", nstates=None, trap=0.
         r = inputs.uniform01(seed + 1000, lat.M)
         idx = np.sort(np.argsort(r)[:nstates])
     phi = plane_waves(lat, s.mu_eff, s.delta, idx)
-    if vortex:
-        phi[:, 0, :] *= inputs.vortex_phase(lat.shape, (lat.dx, lat.dy, lat.dz))[None, :]
+    if vortex:  # reading P2: u e^{i theta/2}, v e^{-i theta/2}, so nu winds once
+        half = inputs.vortex_phase(lat.shape, (lat.dx, lat.dy, lat.dz), 0.5)
+        phi[:, 0, :] *= half[None, :]
+        phi[:, 1, :] *= np.conj(half)[None, :]
     vext = inputs.harmonic_trap(lat.shape, trap, (lat.dx, lat.dy, lat.dz)) if trap else np.zeros(lat.M)
     dext = inputs.pairing_kick(lat.shape, seed, kick * s.delta) if kick else None
     n = len(idx)

@@ -432,3 +432,35 @@ def test_other_schemes_converge_at_their_order(scheme, order):
         errs.append(max(np.abs(r - r_ex).max() / np.abs(r_ex).max(), np.abs(n - n_ex).max() / np.abs(n_ex).max()))
     ratio = errs[0] / errs[1]
     assert 2 ** order * 0.6 < ratio < 2 ** order * 1.6, (errs, ratio)
+
+
+def test_vortex_start_keeps_the_energy_conserved():
+    """Reading P2. All states of a trapped uniform gas with the vortex start
+    u e^{i theta/2}, v e^{-i theta/2} (a site-diagonal unitary map of every
+    state and of its partner [v^*, -u^*], so the set stays complete): E - mu N
+    is conserved to integrator order. Imprinting e^{i theta} on u alone gives
+    the pairing field the same winding but breaks the completeness of the
+    state set with its partners: E - mu N then drifts at a rate that does not
+    shrink with dt."""
+    from cases import make_case, oracle_system
+    shape = (6, 6, 16)
+    drifts = {}
+    for mode in ("half", "u_only"):
+        for dt, n in ((0.01, 8), (0.005, 16)):
+            c = make_case(shape, seed=8, vortex=mode == "half")
+            if mode == "u_only":
+                c.phi[:, 0, :] *= inputs.vortex_phase(shape)[None, :]
+            c.vext = inputs.harmonic_trap(shape, (0.12, 0.12, 0.04))
+            sysm = oracle_system(c)
+            sysm.init_regulator(c.phi)
+            e0 = sysm.energy(c.phi)
+            st = o.start(sysm, c.phi, dt, False)
+            st = o.evolve(sysm, st, dt, n - st.steps)
+            e = sysm.energy(st.phi)
+            E0, E = e0["e_total"] - c.fn.mu * e0["n_part"], e["e_total"] - c.fn.mu * e["n_part"]
+            drifts[mode, dt] = abs(E - E0) / abs(E0)
+            rho, nu = o.densities(c.phi, c.wm, c.wp)
+            winding = np.angle(nu.reshape(shape)[:, :, 0])
+            assert np.ptp(winding) > 5.5  # the pairing field winds around the line
+    assert drifts["half", 0.01] < 1e-7 and drifts["half", 0.005] < drifts["half", 0.01]
+    assert drifts["u_only", 0.01] > 1e-4 and drifts["u_only", 0.005] > 0.5 * drifts["u_only", 0.01]

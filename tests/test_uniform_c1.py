@@ -93,20 +93,22 @@ def test_fill_uniform_states_matches_oracle(prec, shape, spacing, nsub):
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", [0, 1])
 def test_imprint_phase_matches_host_imprint(prec):
-    """A vortex phase imprinted on u in the library equals the same phase
-    applied to the oracle's states on the host (reading P2)."""
+    """The vortex start imprinted in the library (u e^{i theta/2}, v e^{-i theta/2},
+    reading P2) equals the same factors applied to the oracle's states."""
     from paper_2602_08982_b300 import wslda as W
     shape = (12, 12, 48)
     lat = o.Lattice(*shape)
     seed = o.uniform_slda_seed(lat, DELTA0, RHO_S)
     kidx = np.sort(np.argsort(inputs.uniform01(404, lat.M))[:120]).astype(np.int64)
-    ph = inputs.vortex_phase(shape)
+    ph = inputs.vortex_phase(shape, winding=0.5)
     ref = plane_waves(lat, seed.mu_eff, seed.delta, kidx)
     ref[:, 0, :] *= ph[None, :]
+    ref[:, 1, :] *= np.conj(ph)[None, :]
     ctx = W.Context(prec)
     box = ctx.add_box(shape, kind=W.SLDA_A1, B=o.B_SLDA, C=seed.C, mu=seed.mu, nstates=len(kidx))
     ctx.fill_uniform_states(box, seed.mu_eff, seed.delta, kidx)
     ctx.imprint_phase(box, 0, ph)
+    ctx.imprint_phase(box, 1, np.conj(ph))
     got = ctx.get_states(box)
     ctx.close()
     assert rel(got, ref) < (1e-12 if prec == 0 else 3e-7)
