@@ -138,8 +138,10 @@ struct Geometry {
   static constexpr int NX = NX_, NY = NY_, NZ = NZ_, CS = CS_, BT = BT_;
   static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
   static constexpr int MINB = MINB_;        // CTAs per SM the register budget is sized for
+  // a budget of at most ~85 registers per thread (3 CTAs per SM, or 2 of 384+ threads)
+  static constexpr bool TIGHT = MINB_ >= 3 || BT_ * MINB_ >= 768;
   // sites per thread per batch in the epilogues (fewer under a tight register budget)
-  static constexpr int U = sizeof(R_) == 4 ? (MINB_ >= 3 ? 2 : 4) : 2;
+  static constexpr int U = sizeof(R_) == 4 ? (TIGHT ? 2 : 4) : 2;
   static constexpr int P = NX / CS;         // x-planes per CTA
   // Row pitch TZ x (an odd number >= NZ / TZ): the TZ lanes of a z pencil read
   // consecutive elements and the rows of a warp start TZ elements apart modulo
@@ -238,7 +240,7 @@ __device__ __forceinline__ void local_pass(typename G::C* buf, const typename G:
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
     // a warp whose pencils all lie past the end has nothing to do (warp-uniform)
-    if (it * PER + int(threadIdx.x & ~31u) / T >= NPEN) break;
+    if (it == ITERS - 1 && ITERS * PER > NPEN && (ITERS - 1) * PER + int(threadIdx.x & ~31u) / T >= NPEN) continue;
     const int p = it * PER + threadIdx.x / T;
     const bool act = p < NPEN;
     const int pp = act ? p : 0;
@@ -285,7 +287,7 @@ __device__ __forceinline__ void local_deriv(typename G::C* buf, const typename G
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
     // a warp whose pencils all lie past the end has nothing to do (warp-uniform)
-    if (it * PER + int(threadIdx.x & ~31u) / T >= NPEN) break;
+    if (it == ITERS - 1 && ITERS * PER > NPEN && (ITERS - 1) * PER + int(threadIdx.x & ~31u) / T >= NPEN) continue;
     const int p = it * PER + threadIdx.x / T;
     const bool act = p < NPEN;
     const int pp = act ? p : 0;
@@ -338,7 +340,8 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
   for (int r = 0; r < G::CS; ++r) win[r] = dsmem_addr(buf, unsigned(r));
 #pragma unroll 1
   for (int it = 0; it < ITERS; ++it) {
-    if (it * PER + int(threadIdx.x & ~31u) / T >= G::NCOL) break;  // warp-uniform: no column left
+    // warp-uniform: no column left for this warp in the last round
+    if (it == ITERS - 1 && ITERS * PER > G::NCOL && (ITERS - 1) * PER + int(threadIdx.x & ~31u) / T >= G::NCOL) continue;
     const int q = rank * G::NCOL + it * PER + threadIdx.x / T;
     const bool act = (it * PER + threadIdx.x / T) < G::NCOL;
     const int qq = act ? q : rank * G::NCOL;
@@ -452,7 +455,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   constexpr bool XM = MODE == MODE_X || MODE == MODE_X3 || MODE == MODE_X5;  // a predictor stage
   const bool need_e = XM || MODE == MODE_Y || MODE == MODE_F || (MODE == MODE_HORNER && a.compute_e);
   const bool spin2 = GEN && a.alf != nullptr;  // per-site alpha, W_b in the fourth field
-  constexpr int UPMAX = G::MINB >= 3 ? 4 : 16;  // fewer under a tight register budget
+  constexpr int UPMAX = G::TIGHT ? 4 : 16;  // fewer under a tight register budget
   constexpr int UP = (G::NS + G::BT - 1) / G::BT < UPMAX ? (G::NS + G::BT - 1) / G::BT : UPMAX;
   fx4<R> wd[UP];
   auto load_wd = [&](int s0) {
