@@ -835,6 +835,7 @@ wslda_status check_device_error(wslda_ctx* c) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (h & 1) return fail(c, WSLDA_ENAN, "a state norm became non-finite or zero");
   if (h & 2) return fail(c, WSLDA_ENAN, "non-finite value in the loaded states");
+  if (h & 4) return fail(c, WSLDA_ETIMEOUT, "a stage kernel's bounded wait for its slab copies gave up");
   return WSLDA_OK;
 }
 

@@ -158,6 +158,10 @@ struct Geometry {
   // reduction scratch (doubles): warp partials A [0,32) and B [32,64), per-CTA
   // slots of the <H>_n / kinetic sums [64, 96)
   static constexpr int RED_WA = 0, RED_WB = 32, RED_E = 64, RED_N = 96;
+  static constexpr int RED_BAR = 104;  // 8-byte slot of the slab-load mbarrier
+  // slab rows are 16-byte aligned in both memories: the slab arrives as one
+  // bulk copy per row (TMA unit) on an mbarrier instead of per-element cp.async
+  static constexpr bool BULK = (ZP * sizeof(C)) % 16 == 0 && (NZ * sizeof(C)) % 16 == 0;
   static_assert(NX % CS == 0, "cluster must split x evenly");
   static_assert((2 * NY * NZ) % CS == 0, "columns must split evenly");
   static_assert(BT % 32 == 0 && BT % TX == 0 && BT % TY == 0 && BT % TZ == 0, "block");
@@ -224,6 +228,36 @@ __device__ __forceinline__ void st_dsmem(unsigned addr, double2 v) {
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// mbarrier-completed bulk copies (global -> shared, one row each).
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+  return ok != 0;
+}
+// Bounded wait for a phase of the barrier. Copies from valid global rows
+// always complete; should the bound ever be reached, bit 2 of the error word
+// is set (the host reports a timeout) and the wait continues, again bounded,
+// so that no copy is left in flight into this CTA's shared memory on exit.
+__device__ __forceinline__ void mbar_wait(unsigned bar, unsigned phase, int* err) {
+  for (int round = 0; round < 2; ++round) {
+    for (int it = 0; it < (1 << 22); ++it)
+      if (mbar_try_wait(bar, phase)) return;
+    if (err && round == 0 && threadIdx.x == 0) atomicOr(err, 4);
+  }
 }
 
 // Local pencils along z (rows) or y, forward or inverse, over both components.
@@ -421,7 +455,8 @@ __device__ __forceinline__ void x_pass(typename G::C* buf, const typename G::R* 
 // alpha_a/2 T u and -alpha_b/2 T v, the v row its own W_b (fourth field), and
 // the kinetic part of <H>_n comes from the KALPHA partials instead of Parseval.
 template <class G, int MODE, bool GEN>
-__device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, const int n, const int ncl) {
+__device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, const int n, const int ncl,
+                                            const unsigned iter = 0) {
   using C = typename G::C;
   using R = typename G::R;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -442,10 +477,25 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
   const C* twz = tws + G::NX + G::NY;
   const size_t sbase = size_t(n) * 2 * G::M;
   const C* in = a.phi + sbase;
+  const unsigned bar = static_cast<unsigned>(__cvta_generic_to_shared(red + G::RED_BAR));
   // load the slab of both components (asynchronous copies, all in flight)
-  for (int i = tid; i < 2 * G::NS; i += G::BT) {
-    const int comp = i / G::NS, s = i % G::NS;
-    cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
+  if constexpr (G::BULK) {
+    // one bulk copy per z row, issued by the first warp, completing on the barrier
+    if (tid < 32) {
+      if (tid == 0) mbar_arrive_expect_tx(bar, unsigned(2 * G::NS * sizeof(C)));
+      __syncwarp();
+      const unsigned b0 = static_cast<unsigned>(__cvta_generic_to_shared(buf));
+      for (int r = tid; r < 2 * G::P * G::NY; r += 32) {
+        const int comp = r / (G::P * G::NY), row = r % (G::P * G::NY);
+        bulk_g2s(b0 + unsigned((comp * G::SLAB + row * G::ZP) * sizeof(C)), in + comp * G::M + gs0 + row * G::NZ,
+                 unsigned(G::NZ * sizeof(C)), bar);
+      }
+    }
+  } else {
+    for (int i = tid; i < 2 * G::NS; i += G::BT) {
+      const int comp = i / G::NS, s = i % G::NS;
+      cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
+    }
   }
   // Prologue sweep over the slab: the potential part of <H>_n,
   // sum_r W (|u|^2 - |v|^2) + 2 Re(u^* D v), of the scaled input (the slab
@@ -466,8 +516,13 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
     }
   };
   if (need_e) load_wd(tid);
+  if constexpr (MODE == MODE_Y) {
+    // the corrector partial c (one state pass) starts moving into L2 with the slab
+    if (tid < 2) prefetch_l2(a.h3 + sbase + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
+  }
   const R sin_ = R(a.sc_in[n]);
-  cp_async_wait_all();
+  if constexpr (G::BULK) mbar_wait(bar, iter & 1u, a.err);
+  else cp_async_wait_all();
   __syncthreads();
   R ep = 0, ec = 0;  // compensated partial sum
   for (int s0 = tid; s0 < G::NS && need_e; s0 += G::BT * UP) {
@@ -542,7 +597,6 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       if constexpr (Scheme<MODE>::D >= 3) prefetch_l2(a.h3 + off, nb);
       if constexpr (Scheme<MODE>::D >= 4) prefetch_l2(a.h4 + off, nb);
     }
-    if constexpr (MODE == MODE_Y) prefetch_l2(a.h3 + off, nb);
   }
   double En = 0.0, Ev = 0.0;
   for (int r = 0; r < G::CS; ++r) { En += slot[r]; Ev += slot[G::CS + r]; }
@@ -619,7 +673,10 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
     // one pointwise sweep: H phi on the fly, f = -i (H - <H>_n) phi, integrator;
     // results go straight to global memory (normalisation deferred)
     constexpr int D = Scheme<MODE>::D;
-    constexpr int UE = (D >= 4 && U > 2) ? U / 2 : U;  // five history reads per site: smaller batches
+    // sites per batch: fewer with five history reads; the corrector and the
+    // other single-input modes keep 4 in flight even under a tight budget
+    // (their epilogue holds far fewer values per site)
+    constexpr int UE = XM ? ((D >= 4 && U > 2) ? U / 2 : U) : (sizeof(R) == 4 ? 4 : U);
     for (int s0 = tid; s0 < G::NS; s0 += G::BT * UE) {
       C u[UE], v[UE], x1[2][UE], x2[2][UE], x3[2][UE], x4[2][D >= 4 ? UE : 1];
       fx4<R> wd[UE];
@@ -872,12 +929,21 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_cons
     tws[i] = a.tw[i];
   }
   const int ncl = gridDim.x / G::CS;
+  if constexpr (G::BULK && MODE != MODE_GRAD && MODE != MODE_AGRAD) {
+    if (threadIdx.x == 0) {
+      double* red = reinterpret_cast<double*>(tws + NAX);
+      red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+      mbar_init(static_cast<unsigned>(__cvta_generic_to_shared(red + G::RED_BAR)), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   if constexpr (PERSIST) {
+    unsigned iter = 0;
 #pragma unroll 1
-    for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl) {
+    for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl, ++iter) {
       __syncthreads();
       if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, n, ncl);
-      else stage_state<G, MODE, GEN>(a, n, ncl);
+      else stage_state<G, MODE, GEN>(a, n, ncl, iter);
     }
   } else {
     __syncthreads();

@@ -214,3 +214,28 @@ def test_single_precision_warmup_reaches_the_double_fixed_point(converged_8):
     assert np.abs(np.sort(E) - np.sort(ref.last.E)).max() < 1e-6 * ref.last.E.max()
     assert np.abs(rho - ref.last.rho).max() < 1e-6 * ref.last.rho.max()
     assert np.abs(nu - ref.last.nu).max() < 1e-6 * np.abs(ref.last.nu).max()
+
+
+def test_trapped_slda_with_the_printed_C_matches_oracle_and_is_stationary():
+    """Reading K6: trapped SLDA (A = 1, B(0), C = -11.11) with a particle-number
+    target and Broyden mixing converges on the GPU to the oracle's fixed point
+    (same iterations, spectrum, densities, mu), and the static states stay put
+    under the time-dependent step."""
+    from paper_2602_08982_b300 import wslda as W
+    lat = o.Lattice(8, 8, 8)
+    v = inputs.harmonic_trap(lat.shape, 0.12)
+    sd = o.uniform_slda_seed(o.Lattice(16, 16, 16), 0.25, RHO_S)
+    fn = o.Functional("slda", B=o.B_SLDA, C=o.C_ASLDA, mu=sd.mu)
+    kw = dict(mixing=0.3, eps_energy=1e-7, max_iters=60, method="broyden", n_target=10.0, a_mu=0.5, eps_npart=1e-4)
+    ref = scf.static_solve(lat, fn, v, np.full(lat.M, sd.U), np.full(lat.M, sd.delta), **kw)
+    assert ref.converged
+    ctx, b = _ctx(W, W.FP64, lat, fn, v)
+    res, E = ctx.static_solve(b, np.full(lat.M, sd.U), np.full(lat.M, sd.delta), **kw)
+    rho, nu = ctx.get_densities(b)
+    _compare(res, E, rho, nu, ref, 1e-8, f_tol=1e-8)
+    assert abs(res["n_sigma"] - 10.0) < 1e-4 and np.abs(nu).max() > 1e-3
+    ctx.start(True, 0.01)
+    ctx.step(0.01, 10)
+    rho2, _ = ctx.get_densities(b)
+    ctx.close()
+    assert np.abs(rho2 - rho).max() < 1e-6 * rho.max()

@@ -133,3 +133,31 @@ def test_broyden_with_mu_update_reaches_the_slda_seed():
     assert r.converged and r.iters < 40
     assert abs(r.mu - sd.mu) < 1e-8
     assert np.abs(r.U - sd.U).max() < 1e-8 and np.abs(r.delta - sd.delta).max() < 1e-8
+
+
+def test_trapped_slda_converges_with_the_printed_C_and_not_with_the_seed_C():
+    """Reading K6. The uniform A = 1 seed backs out C = +5.3 on these lattices
+    (with the zone-corner cutoff of reading R5), which makes the density
+    derivative of the pairing energy, -|Delta|^2 / (3 C rho^(2/3)), attractive
+    and unbounded where rho -> 0: a trapped iteration with a particle-number
+    target then oscillates. With the printed ASLDA C = -11.11 that term is
+    repulsive, and the same iteration converges to a paired solution that is
+    a fixed point of K with the requested N."""
+    lat = o.Lattice(8, 8, 8)
+    vext = inputs.harmonic_trap(lat.shape, 0.12)
+    sd = o.uniform_slda_seed(o.Lattice(16, 16, 16), 0.25, RHO_S)
+    assert sd.C > 0
+    res = {}
+    for C in (o.C_ASLDA, sd.C):
+        fn = o.Functional("slda", B=o.B_SLDA, C=C, mu=sd.mu)
+        res[C] = scf.static_solve(lat, fn, vext, np.full(lat.M, sd.U), np.full(lat.M, sd.delta), mixing=0.3,
+                                  eps_energy=1e-6, max_iters=60, method="broyden", n_target=10.0, a_mu=0.5,
+                                  eps_npart=1e-3)
+    good, bad = res[o.C_ASLDA], res[sd.C]
+    assert good.converged and good.iters < 45
+    assert abs(lat.dV * good.last.rho.sum() - 10.0) < 1e-3
+    assert np.abs(good.delta).max() > 0.05  # paired
+    fn = o.Functional("slda", B=o.B_SLDA, C=o.C_ASLDA, mu=good.mu)
+    again = scf.map_K(lat, fn, vext, good.U, good.delta)
+    assert np.abs(again.U - good.U).max() < 1e-4 and np.abs(again.delta - good.delta).max() < 1e-4
+    assert not bad.converged
