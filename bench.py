@@ -141,14 +141,17 @@ def stage_source_hash() -> str:
     return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
 
 
-def profiled_traffic():
+def profiled_traffic(shape):
     """DRAM bytes per state-site of stage X from the committed ncu summary, if
-    that capture was taken on the current stage-kernel source; else None."""
+    that capture was taken on the current stage-kernel source and on this
+    lattice; else None."""
     path = os.path.join(ROOT, "profiles", "stage_x_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = dict(line.split("=", 1) for line in open(path).read().split() if "=" in line)
     if kv.get("stage_cuh_blob") != stage_source_hash():
+        return None
+    if kv.get("lattice") != "x".join(str(n) for n in shape):
         return None
     return float(kv["mixed_bytes_per_state_site"])
 
@@ -367,7 +370,7 @@ def run_arm(W, torch, prec, args, wl, rank, world, dev):
     hbm, which = measured_peaks()
     if prec == 1:
         achieved = bx * per_launch / (x_avg * 1e-3) / 1e9
-        tb = profiled_traffic() if args.integrator == "AB4AM5" and args.A == 1.0 else None  # captured on A = 1
+        tb = profiled_traffic(shape) if args.integrator == "AB4AM5" and args.A == 1.0 else None  # captured on A = 1
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None if tb is None else tb * per_launch,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation)",
