@@ -241,6 +241,46 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
+// The same copy with an L2 eviction policy for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(unsigned dst, const void* src, unsigned bytes, unsigned bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(pol) : "memory");
+}
+
+// L2 eviction priorities. The stages that apply H re-read their input state
+// in the epilogue, tens of microseconds after the slab copy brought it in;
+// meanwhile the history reads and the output writes stream several times
+// that volume through L2. The slab copy marks the input lines evict-last, the
+// epilogue's last read of them and every streaming access evict-first, so the
+// re-read hits L2 instead of DRAM.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* p, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float2* p, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol));
+}
+__device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol));
+}
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase) {
   unsigned ok;
   asm volatile(
@@ -485,10 +525,13 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
       if (tid == 0) mbar_arrive_expect_tx(bar, unsigned(2 * G::NS * sizeof(C)));
       __syncwarp();
       const unsigned b0 = static_cast<unsigned>(__cvta_generic_to_shared(buf));
+      const uint64_t keep = policy_evict_last();
       for (int r = tid; r < 2 * G::P * G::NY; r += 32) {
         const int comp = r / (G::P * G::NY), row = r % (G::P * G::NY);
-        bulk_g2s(b0 + unsigned((comp * G::SLAB + row * G::ZP) * sizeof(C)), in + comp * G::M + gs0 + row * G::NZ,
-                 unsigned(G::NZ * sizeof(C)), bar);
+        const unsigned d = b0 + unsigned((comp * G::SLAB + row * G::ZP) * sizeof(C));
+        const C* src = in + comp * G::M + gs0 + row * G::NZ;
+        if constexpr (applies_h(MODE)) bulk_g2s_hint(d, src, unsigned(G::NZ * sizeof(C)), bar, keep);
+        else bulk_g2s(d, src, unsigned(G::NZ * sizeof(C)), bar);
       }
     }
   } else {
@@ -677,6 +720,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
     // other single-input modes keep 4 in flight even under a tight budget
     // (their epilogue holds far fewer values per site)
     constexpr int UE = XM ? ((D >= 4 && U > 2) ? U / 2 : U) : (sizeof(R) == 4 ? 4 : U);
+    const uint64_t pf = policy_evict_first();
     for (int s0 = tid; s0 < G::NS; s0 += G::BT * UE) {
       C u[UE], v[UE], x1[2][UE], x2[2][UE], x3[2][UE], x4[2][D >= 4 ? UE : 1];
       fx4<R> wd[UE];
@@ -685,19 +729,19 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
         const int s = s0 + k * G::BT;
         if (s < G::NS) {
           const int g = gs0 + s;
-          u[k] = in[g];
-          v[k] = in[G::M + g];
+          u[k] = ld_hint(in + g, pf);
+          v[k] = ld_hint(in + G::M + g, pf);
           wd[k] = WD[g];
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t gg = sbase + c * G::M + g;
             if constexpr (XM) {
-              x1[c][k] = a.h1[gg];
-              x2[c][k] = a.h2[gg];
-              if constexpr (D >= 3) x3[c][k] = a.h3[gg];
-              if constexpr (D >= 4) x4[c][k] = a.h4[gg];
+              x1[c][k] = ld_hint(a.h1 + gg, pf);
+              x2[c][k] = ld_hint(a.h2 + gg, pf);
+              if constexpr (D >= 3) x3[c][k] = ld_hint(a.h3 + gg, pf);
+              if constexpr (D >= 4) x4[c][k] = ld_hint(a.h4 + gg, pf);
             }
-            if constexpr (MODE == MODE_Y) x3[c][k] = a.h3[gg];
+            if constexpr (MODE == MODE_Y) x3[c][k] = ld_hint(a.h3 + gg, pf);
             if constexpr (MODE == MODE_HORNER) x1[c][k] = a.h1[gg];
           }
         }
@@ -750,10 +794,10 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
               if constexpr (D >= 4) pb = add(pb, scl(x4[c][k], R(S::b[4])));
               res = add(ph[c], scl(pb, dt));
               const C corr = add(ph[c], scl(pa, dt));
-              a.h0[gg] = fv;
-              if constexpr (D == 2) const_cast<C*>(a.h2)[gg] = corr;  // over f_{k-3}, its last use
-              if constexpr (D == 3) a.h3[gg] = corr;                  // over f_{k-4}
-              if constexpr (D == 4) a.h4[gg] = corr;                  // over f_{k-5}
+              st_hint(a.h0 + gg, fv, pf);
+              if constexpr (D == 2) st_hint(const_cast<C*>(a.h2) + gg, corr, pf);  // over f_{k-3}, its last use
+              if constexpr (D == 3) st_hint(a.h3 + gg, corr, pf);                  // over f_{k-4}
+              if constexpr (D == 4) st_hint(a.h4 + gg, corr, pf);                  // over f_{k-5}
             } else if constexpr (MODE == MODE_Y) {
               res = add(x3[c][k], scl(mul_mi(hm[c]), R(a.ycoef * a.dt)));
             } else if constexpr (MODE == MODE_F) {
@@ -761,7 +805,7 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
             } else {  // HORNER: out = base + coef (H - E) in
               res = add(scl(x1[c][k], sbase_), mul(mk<C>(R(a.coef_re), R(a.coef_im)), hm[c]));
             }
-            dst[c * G::M + g] = res;
+            st_hint(dst + c * G::M + g, res, pf);
             if (norm_out) {
               const R t = (res.x * res.x + res.y * res.y) - nc;
               const R ns = np + t;
