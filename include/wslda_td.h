@@ -387,9 +387,13 @@ wslda_status wslda_densities_noalloc(int precision, const void* uv, const double
  * method of the paper): a network of four 3x3x3 convolutions with periodic
  * wrap-around, channels 2 -> hidden -> hidden -> hidden -> 2, tanh between
  * layers, mapping per-site (V_ext / eF, coupling) to (U / eF, Delta / eF).
- * Weights: float32 master copy, used rounded to bfloat16 (nearest even);
- * activations, accumulation, gradients and Adam (b1 0.9, b2 0.999, eps 1e-8)
- * are float32. Parameters are flattened per layer as W[co][ci][27] (offset
+ * Weights: float32 master copy, used rounded to bfloat16 (nearest even).
+ * The convolutions run on the tensor cores as implicit GEMMs with bfloat16
+ * operands and float32 accumulation: each layer's input (an activation, or
+ * in the backward pass the gradient that the input-gradient convolution
+ * consumes) is rounded to bfloat16 (nearest even) as it is staged; the
+ * weight gradient uses the same rounded layer inputs. Activations, stored
+ * gradients, the loss and Adam (b1 0.9, b2 0.999, eps 1e-8) are float32. Parameters are flattened per layer as W[co][ci][27] (offset
  * (dx, dy, dz) in {-1, 0, 1}^3 at (dx+1)*9 + (dy+1)*3 + (dz+1)) then bias[co];
  * a layer computes y[b][co][r] = bias[co] + sum_ci sum_d W[co][ci][d]
  * x[b][ci][r + d]. Activations are device float arrays [batch][2][M]; the
@@ -401,7 +405,12 @@ wslda_status wslda_densities_noalloc(int precision, const void* uv, const double
  *    the gradient stays in the network for adam() and is copied to grad_host
  *    when that pointer is not NULL.
  *  - symmetrize: average of each of nfields fields over the reflections
- *    i -> N - i (mod N) of the three axes (out must not alias y). */
+ *    i -> N - i (mod N) of the three axes (out must not alias y).
+ *  - get_activation: the output of layer 0, 1 or 2 (after tanh, [batch][hidden]
+ *    [M] floats) of the last forward or loss_grad call, copied to `out` (host
+ *    or device memory); the call synchronises `stream`.
+ *  - A tensor-core completion wait that gives up (bounded, about 2 s) makes
+ *    loss_grad return WSLDA_ETIMEOUT. */
 typedef struct wslda_net wslda_net;
 wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch, wslda_net** out);
 void wslda_net_destroy(wslda_net* net);
@@ -414,6 +423,7 @@ wslda_status wslda_net_loss_grad(wslda_net* net, const float* x, const float* ta
                                  float* grad_host, void* stream);
 wslda_status wslda_net_adam(wslda_net* net, double lr, void* stream);
 wslda_status wslda_net_symmetrize(const float* y, int64_t nfields, int nx, int ny, int nz, float* out, void* stream);
+wslda_status wslda_net_get_activation(wslda_net* net, int layer, int batch, float* out, void* stream);
 
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events on
  * the context's stream and its duration is added to the kernel's total.

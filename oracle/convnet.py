@@ -10,8 +10,12 @@ start the static self-consistent iteration of Alg. 1 (Sec. 3.2). It is a stack
 of 3x3x3 convolutions with periodic wrap-around (the lattice is periodic,
 Sec. 3.1), tanh between layers and a linear last layer, trained on the mean
 squared error with Adam (Kingma and Ba, arXiv:1412.6980). Weights are used in
-bfloat16 (rounded to nearest even from the float32 master copy); everything
-else is float64 here.
+bfloat16 (rounded to nearest even from the float32 master copy), and so is
+every convolution operand: a layer's input enters its convolution rounded to
+bfloat16, the weight gradient uses those rounded inputs, and the gradient
+that the input-gradient convolution consumes is rounded too (the operands of
+a bfloat16 tensor-core GEMM with float32 accumulation). Everything else is
+float64 here. With bf16=False nothing is rounded (the plain network).
 
 Conventions: activations x[b, c, ix, iy, iz]; weights W[co, ci, dx, dy, dz]
 with offsets d - 1 in {-1, 0, 1}; a layer computes
@@ -83,7 +87,7 @@ def forward(theta, shapes, x, bf16: bool = True):
     h = x
     for i, (W, b) in enumerate(params):
         Wq = to_bf16(W) if bf16 else W
-        h = conv(h, Wq, b)
+        h = conv(to_bf16(h) if bf16 else h, Wq, b)
         if i < len(params) - 1:
             h = np.tanh(h)
         acts.append(h)
@@ -108,17 +112,18 @@ def gradient(theta, shapes, x, t, bf16: bool = True):
         Wq = to_bf16(W) if bf16 else W
         if i < len(params) - 1:
             g = g * (1.0 - acts[i + 1] ** 2)  # through tanh
-        xin = acts[i]
+        xin = to_bf16(acts[i]) if bf16 else acts[i]
         gW = np.zeros_like(W)
         for d in OFFSETS:
             gW[:, :, d[0] + 1, d[1] + 1, d[2] + 1] = np.einsum("boxyz,bcxyz->oc", g, shift(xin, d))
         gb = g.sum(axis=(0, 2, 3, 4))
         grads.append((gW, gb))
         # dL/dx[r] = sum_d W[:, :, d]^T g[r - d]
+        gq = to_bf16(g) if bf16 else g
         gx = np.zeros_like(xin)
         for d in OFFSETS:
             gx += np.einsum("oc,boxyz->bcxyz", Wq[:, :, d[0] + 1, d[1] + 1, d[2] + 1],
-                            shift(g, (-d[0], -d[1], -d[2])))
+                            shift(gq, (-d[0], -d[1], -d[2])))
         g = gx
     flat = []
     for gW, gb in reversed(grads):

@@ -13,12 +13,15 @@
 // (dz+1)) followed by bias[co]. A layer computes
 //   y[b][co][r] = bias[co] + sum_ci sum_d W[co][ci][d] x[b][ci][r + d].
 //
-// Kernels: quantize (bfloat16 weight copy), conv_fwd (thread per site, all
-// output channels in registers, the layer's weights in shared memory),
-// conv_bwd_data (transposed and mirrored weights, times 1 - a^2 through tanh),
-// conv_bwd_weight (CTA per (co, ci) pair, fixed-order reduction over batch and
-// sites), bias_grad, mse (gradient of the loss and per-block partial sums),
-// adam, mirror_avg (projection onto reflection-symmetric fields).
+// Kernels: quantize (bfloat16 weight copy); the convolutions themselves run on
+// the tensor cores (conv_tc.cu: implicit GEMM with bfloat16 operands and
+// float32 accumulation; layer inputs are rounded to bfloat16 as they are
+// staged), forward with bias and tanh fused, and the input gradient as the
+// same convolution with transposed, mirrored weights times 1 - a^2 through
+// tanh; conv_bwd_weight (CTA per (co, ci), fixed-order reduction over batch
+// and sites, layer input rounded as in the forward pass), bias_grad, mse
+// (gradient of the loss and per-block partial sums), adam, mirror_avg
+// (projection onto reflection-symmetric fields).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,6 +32,7 @@
 #include <vector>
 
 #include "../../include/wslda_td.h"
+#include "conv_tc.cuh"
 
 namespace {
 
@@ -57,81 +61,9 @@ __global__ void quantize(const float* __restrict__ theta, float* __restrict__ wq
   wq[i] = w ? __bfloat162float(__float2bfloat16_rn(theta[i])) : theta[i];
 }
 
-// Forward layer: COUT accumulators per thread; grid (ceil(M/128), B).
-template <int COUT>
-__global__ void __launch_bounds__(128) conv_fwd(Lat L, int cin, const float* __restrict__ W,
-                                                const float* __restrict__ bias, const float* __restrict__ x,
-                                                float* __restrict__ y, int act) {
-  extern __shared__ float w_s[];  // [COUT][cin][27] then bias[COUT]
-  const int M = L.nx * L.ny * L.nz;
-  const int nw = COUT * cin * 27;
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) w_s[i] = W[i];
-  for (int i = threadIdx.x; i < COUT; i += blockDim.x) w_s[nw + i] = bias[i];
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= M) return;
-  const int b = blockIdx.y;
-  const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
-  const float* xb = x + int64_t(b) * cin * M;
-  float acc[COUT];
-#pragma unroll
-  for (int co = 0; co < COUT; ++co) acc[co] = w_s[nw + co];
-  for (int d = 0; d < 27; ++d) {
-    const int q = neighbour(L, ix, iy, iz, d);
-    for (int ci = 0; ci < cin; ++ci) {
-      const float v = xb[int64_t(ci) * M + q];
-#pragma unroll
-      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(w_s[(co * cin + ci) * 27 + d], v, acc[co]);
-    }
-  }
-  float* yb = y + int64_t(b) * COUT * M;
-#pragma unroll
-  for (int co = 0; co < COUT; ++co) yb[int64_t(co) * M + s] = act ? tanhf(acc[co]) : acc[co];
-}
-
-// Gradient with respect to the layer input: CIN accumulators per thread,
-// gx[ci][r] = sum_co sum_d W[co][ci][d] g[co][r - d]; when `through_tanh`
-// the result is multiplied by 1 - x^2 (x the layer input, a tanh output).
-template <int CIN>
-__global__ void __launch_bounds__(128) conv_bwd_data(Lat L, int cout, const float* __restrict__ W,
-                                                     const float* __restrict__ g, const float* __restrict__ x,
-                                                     float* __restrict__ gx, int through_tanh) {
-  extern __shared__ float w_s[];  // [cout][CIN][27]
-  const int M = L.nx * L.ny * L.nz;
-  const int nw = cout * CIN * 27;
-  for (int i = threadIdx.x; i < nw; i += blockDim.x) w_s[i] = W[i];
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= M) return;
-  const int b = blockIdx.y;
-  const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
-  const float* gb = g + int64_t(b) * cout * M;
-  float acc[CIN];
-#pragma unroll
-  for (int ci = 0; ci < CIN; ++ci) acc[ci] = 0.f;
-  for (int d = 0; d < 27; ++d) {
-    const int q = neighbour(L, ix, iy, iz, 26 - d);  // r - d
-    for (int co = 0; co < cout; ++co) {
-      const float v = gb[int64_t(co) * M + q];
-#pragma unroll
-      for (int ci = 0; ci < CIN; ++ci) acc[ci] = fmaf(w_s[(co * CIN + ci) * 27 + d], v, acc[ci]);
-    }
-  }
-  const float* xb = x + int64_t(b) * CIN * M;
-  float* ob = gx + int64_t(b) * CIN * M;
-#pragma unroll
-  for (int ci = 0; ci < CIN; ++ci) {
-    float v = acc[ci];
-    if (through_tanh) {
-      const float a = xb[int64_t(ci) * M + s];
-      v *= 1.f - a * a;
-    }
-    ob[int64_t(ci) * M + s] = v;
-  }
-}
-
 // Weight gradient: CTA per (co, ci); 27 partial sums per thread over the
-// batch and sites, then a fixed-order reduction across the CTA.
+// batch and sites, then a fixed-order reduction across the CTA. The layer
+// input enters rounded to bfloat16, as the forward convolution used it.
 __global__ void __launch_bounds__(256) conv_bwd_weight(Lat L, int cin, int cout, int batch,
                                                        const float* __restrict__ g, const float* __restrict__ x,
                                                        float* __restrict__ gW) {
@@ -148,7 +80,8 @@ __global__ void __launch_bounds__(256) conv_bwd_weight(Lat L, int cin, int cout,
     const float gv = g[(int64_t(b) * cout + co) * M + s];
     const float* xb = x + (int64_t(b) * cin + ci) * M;
 #pragma unroll
-    for (int d = 0; d < 27; ++d) acc[d] = fmaf(gv, xb[neighbour(L, ix, iy, iz, d)], acc[d]);
+    for (int d = 0; d < 27; ++d)
+      acc[d] = fmaf(gv, __bfloat162float(__float2bfloat16_rn(xb[neighbour(L, ix, iy, iz, d)])), acc[d]);
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -257,6 +190,7 @@ struct wslda_net {
   float* act[kLayers + 1] = {};  // act[0] is the caller's input (not owned)
   float *g0 = nullptr, *g1 = nullptr;
   double* part = nullptr;
+  int* err_d = nullptr;  // device error word (bit 3: a tensor-core completion wait timed out)
   int64_t *wb = nullptr, *we = nullptr;
   int64_t step = 0;
   std::vector<void*> owned;
@@ -271,25 +205,25 @@ wslda_status net_fail(wslda_net* n, wslda_status s, const std::string& msg) {
   return s;
 }
 
-template <int COUT>
+// Layer l forward on the tensor cores: bias, tanh except after the last layer.
 cudaError_t launch_fwd(const wslda_net* n, int l, const float* x, float* y, int batch, cudaStream_t s) {
-  const size_t smem = (size_t(COUT) * n->cin[l] * 27 + COUT) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(conv_fwd<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  dim3 grid(unsigned((n->M + 127) / 128), unsigned(batch));
-  conv_fwd<COUT><<<grid, 128, smem, s>>>(n->L, n->cin[l], n->wq + n->woff[l], n->wq + n->boff[l], x, y,
-                                         l < kLayers - 1);
-  return cudaGetLastError();
+  wslda::ConvTcArgs a{};
+  a.nx = n->L.nx; a.ny = n->L.ny; a.nz = n->L.nz;
+  a.cin = n->cin[l]; a.cout = n->cout[l];
+  a.x = x; a.w = n->wq + n->woff[l]; a.transposed = 0; a.bias = n->wq + n->boff[l];
+  a.epi = l < kLayers - 1 ? 1 : 0; a.aux = nullptr; a.y = y; a.err = n->err_d;
+  return wslda::launch_conv_tc(a, batch, s);
 }
 
-template <int CIN>
+// Gradient with respect to the input of layer l > 0 (a tanh output): the
+// convolution of g with the transposed, mirrored weights, times 1 - a^2.
 cudaError_t launch_bwd_data(const wslda_net* n, int l, const float* g, float* gx, int batch, cudaStream_t s) {
-  const size_t smem = size_t(n->cout[l]) * CIN * 27 * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(conv_bwd_data<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  dim3 grid(unsigned((n->M + 127) / 128), unsigned(batch));
-  conv_bwd_data<CIN><<<grid, 128, smem, s>>>(n->L, n->cout[l], n->wq + n->woff[l], g, n->act[l], gx, l > 0);
-  return cudaGetLastError();
+  wslda::ConvTcArgs a{};
+  a.nx = n->L.nx; a.ny = n->L.ny; a.nz = n->L.nz;
+  a.cin = n->cout[l]; a.cout = n->cin[l];
+  a.x = g; a.w = n->wq + n->woff[l]; a.transposed = 1; a.bias = nullptr;
+  a.epi = 2; a.aux = n->act[l]; a.y = gx; a.err = n->err_d;
+  return wslda::launch_conv_tc(a, batch, s);
 }
 
 cudaError_t forward(wslda_net* n, const float* x, int batch, float* y, cudaStream_t s) {
@@ -300,11 +234,7 @@ cudaError_t forward(wslda_net* n, const float* x, int batch, float* y, cudaStrea
   n->act[0] = const_cast<float*>(x);
   for (int l = 0; l < kLayers; ++l) {
     float* out = (l == kLayers - 1 && y) ? y : n->act[l + 1];
-    const int co = n->cout[l];
-    if (co == 2) e = launch_fwd<2>(n, l, n->act[l], out, batch, s);
-    else if (co == 8) e = launch_fwd<8>(n, l, n->act[l], out, batch, s);
-    else e = launch_fwd<32>(n, l, n->act[l], out, batch, s);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_fwd(n, l, n->act[l], out, batch, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -340,7 +270,8 @@ wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch,
   bool ok = alloc((void**)&n->theta, n->P * 4) && alloc((void**)&n->wq, n->P * 4) &&
             alloc((void**)&n->grad, n->P * 4) && alloc((void**)&n->m, n->P * 4) && alloc((void**)&n->v, n->P * 4) &&
             alloc((void**)&n->g0, amax) && alloc((void**)&n->g1, amax) &&
-            alloc((void**)&n->part, kMseBlocks * sizeof(double)) && alloc((void**)&n->wb, kLayers * 8) &&
+            alloc((void**)&n->part, kMseBlocks * sizeof(double)) && alloc((void**)&n->err_d, sizeof(int)) &&
+            alloc((void**)&n->wb, kLayers * 8) &&
             alloc((void**)&n->we, kLayers * 8);
   for (int l = 1; l <= kLayers && ok; ++l)
     ok = alloc((void**)&n->act[l], size_t(max_batch) * ch[l] * n->M * sizeof(float));
@@ -353,6 +284,7 @@ wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch,
     ok = cudaMemcpy(n->wb, wb, sizeof(wb), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(n->we, we, sizeof(we), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(n->theta, 0, n->P * 4) == cudaSuccess && cudaMemset(n->m, 0, n->P * 4) == cudaSuccess &&
+         cudaMemset(n->err_d, 0, sizeof(int)) == cudaSuccess &&
          cudaMemset(n->v, 0, n->P * 4) == cudaSuccess;
   }
   if (!ok) {
@@ -418,15 +350,18 @@ wslda_status wslda_net_loss_grad(wslda_net* n, const float* x, const float* t, i
     bias_grad<<<unsigned(n->cout[l]), 256, 0, s>>>(n->M, n->cout[l], batch, g, n->grad + n->boff[l]);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if (l > 0) {
-      e = n->cin[l] == 8 ? launch_bwd_data<8>(n, l, g, gnext, batch, s) : launch_bwd_data<32>(n, l, g, gnext, batch, s);
+      e = launch_bwd_data(n, l, g, gnext, batch, s);
       std::swap(g, gnext);
     }
   }
   std::vector<double> part(kMseBlocks);
+  int errw = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), n->part, kMseBlocks * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&errw, n->err_d, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && grad_host) e = cudaMemcpyAsync(grad_host, n->grad, n->P * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return net_fail(n, WSLDA_ECUDA, std::string("loss_grad: ") + cudaGetErrorString(e));
+  if (errw) return net_fail(n, WSLDA_ETIMEOUT, "a tensor-core completion wait timed out");
   double acc = 0.0;
   for (double p : part) acc += p;
   *loss = acc / double(nout);
@@ -442,6 +377,16 @@ wslda_status wslda_net_adam(wslda_net* n, double lr, void* stream) {
       n->theta, n->grad, n->m, n->v, n->P, float(lr), float(b1), float(b2), float(c1), float(c2), 1e-8f);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? WSLDA_OK : net_fail(n, WSLDA_ECUDA, std::string("adam: ") + cudaGetErrorString(e));
+}
+
+wslda_status wslda_net_get_activation(wslda_net* n, int layer, int batch, float* out, void* stream) {
+  if (!n || !out || layer < 0 || layer > kLayers - 2 || batch < 1 || batch > n->max_batch) return WSLDA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = size_t(batch) * n->cout[layer] * n->M * sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(out, n->act[layer + 1], bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return net_fail(n, WSLDA_ECUDA, std::string("get_activation: ") + cudaGetErrorString(e));
+  return WSLDA_OK;
 }
 
 wslda_status wslda_net_symmetrize(const float* y, int64_t nfields, int nx, int ny, int nz, float* out,

@@ -119,6 +119,7 @@ def _load():
         "wslda_net_loss_grad": (I, [P, P, P, I, DP, P, P]),
         "wslda_net_adam": (I, [P, D, P]),
         "wslda_net_symmetrize": (I, [P, I64, I, I, I, P, P]),
+        "wslda_net_get_activation": (I, [P, I, I, P, P]),
         "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
         "wslda_imprint_phase": (I, [P, I, I, P, I]),
         "wslda_measure_fp64_rate": (I, [I, DP]),
@@ -525,6 +526,14 @@ class Net:
 
     def adam(self, lr: float, stream=None):
         self._check(lib.wslda_net_adam(self._h, float(lr), self._stream(stream)))
+
+    def get_activation(self, layer: int, batch: int, stream=None):
+        """Output of hidden layer `layer` (0..2) of the last forward pass, as a
+        host array [batch][hidden][M]."""
+        out = np.empty((batch, self.hidden, int(np.prod(self.shape))), dtype=np.float32)
+        self._check(lib.wslda_net_get_activation(self._h, int(layer), int(batch), out.ctypes.data_as(ct.c_void_p),
+                                                 self._stream(stream)))
+        return out
 
     def symmetrize(self, y, out, nfields: int, stream=None):
         st = lib.wslda_net_symmetrize(self._dev(y), int(nfields), *self.shape, self._dev(out), self._stream(stream))

@@ -24,22 +24,51 @@ def _setup(shape, hidden, batch, seed):
     return net, shapes, theta, x, t, xd, td
 
 
+@pytest.mark.parametrize("shape,hidden,batch", [((6, 6, 8), 8, 2), ((12, 12, 12), 32, 3), ((5, 7, 9), 32, 2)])
+def test_each_tensor_core_layer_matches_oracle(shape, hidden, batch):
+    """Every layer of the forward pass (tensor-core implicit GEMM, bfloat16
+    operands, float32 accumulation) against the oracle's layer fed the GPU's
+    own layer input, so both sides round the same float32 values to
+    bfloat16 and differ only in the accumulation: within 1e-5 of the largest
+    output. The 5x7x9 lattice leaves a ragged last tile of 128 sites."""
+    import torch
+    net, shapes, theta, x, t, xd, td = _setup(shape, hidden, batch, 303)
+    y = torch.empty_like(xd)
+    net.forward(xd, y, batch)
+    params = cn.unflatten(theta.astype(np.float64), shapes)
+    ins = [x] + [net.get_activation(l, batch) for l in range(3)]
+    outs = ins[1:] + [y.cpu().numpy()]
+    for l, (W, b) in enumerate(params):
+        xin = ins[l].astype(np.float64).reshape((batch, -1) + shape)
+        ref = cn.conv(cn.to_bf16(xin), cn.to_bf16(W), b)
+        if l < 3:
+            ref = np.tanh(ref)
+        got = outs[l].reshape(ref.shape)
+        assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max(), l
+    net.close()
+
+
 @pytest.mark.parametrize("shape,hidden,batch", [((6, 6, 8), 8, 2), ((12, 12, 12), 32, 3)])
 def test_forward_and_gradient_match_oracle(shape, hidden, batch):
+    """The whole network and its gradient against the oracle run from the
+    same parameters and inputs. Both round every convolution operand to
+    bfloat16; an activation that lies within float32 rounding of a bfloat16
+    rounding boundary can round differently on the two sides (the oracle
+    carries it in double), which moves single outputs by up to ~1e-3 of the
+    largest (6e-4 in a float32 emulation on the CPU), hence the tolerance."""
     import torch
     net, shapes, theta, x, t, xd, td = _setup(shape, hidden, batch, 101)
-    M = int(np.prod(shape))
     y = torch.empty_like(xd)
     net.forward(xd, y, batch)
     th = theta.astype(np.float64)
     xo = x.astype(np.float64).reshape((batch, 2) + shape)
     to = t.astype(np.float64).reshape((batch, 2) + shape)
     yo, _ = cn.forward(th, shapes, xo)
-    assert np.abs(y.cpu().numpy().reshape(yo.shape) - yo).max() < 2e-5 * np.abs(yo).max()
+    assert np.abs(y.cpu().numpy().reshape(yo.shape) - yo).max() < 3e-3 * np.abs(yo).max()
     loss, g = net.loss_grad(xd, td, batch, want_grad=True)
     Lo, go = cn.gradient(th, shapes, xo, to)
-    assert abs(loss - Lo) < 1e-5 * Lo
-    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+    assert abs(loss - Lo) < 1e-4 * Lo
+    assert np.abs(g - go).max() < 3e-3 * np.abs(go).max()
     net.close()
 
 
