@@ -97,8 +97,10 @@ def parse():
     p.add_argument("--init", default="quench", choices=["quench", "scf"],
                    help="quench: uniform plane-wave states in the trap (default); scf: states of a static "
                         "self-consistent solve with nstates = M (slow: minutes at 32^3)")
-    p.add_argument("--scf-n", type=float, default=200.0, help="particle-number target per spin for --init scf")
-    p.add_argument("--scf-iters", type=int, default=40)
+    p.add_argument("--scf-n", type=float, default=30.0,
+                   help="particle-number target per spin for --init scf (30: a Thomas-Fermi radius of about 11 "
+                        "sites in the w = 0.05 trap, central kF near 1)")
+    p.add_argument("--scf-iters", type=int, default=60)
     p.add_argument("--scf-fp32-iters", type=int, default=30)
     p.add_argument("--friction", default=None,
                    help="alpha,beta,gamma of the quantum-friction terms (Sec. 5.2.4), e.g. 5,5,0")
@@ -219,10 +221,11 @@ def resolve(args, name):
 ASLDA_DMU = (0.02, -0.02)  # mu_a - mu, mu_b - mu of the spin-imbalanced workload
 
 
-def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0, aslda=False):
+def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0, aslda=False, C=None):
     """A context with one box of the workload (SLDA with the uniform seed's
-    B, C, mu; A != 1 adds the current terms; aslda: the spin-imbalanced
-    functional with C = -11.11 and mu_a, mu_b around the seed's mu)."""
+    B, C, mu unless C or mu are given; A != 1 adds the current terms; aslda:
+    the spin-imbalanced functional with C = -11.11 and mu_a, mu_b around the
+    seed's mu)."""
     from paper_2602_08982_b300 import inputs
     shape = wl["shape"]
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
@@ -233,8 +236,8 @@ def make_box(W, prec, wl, stream, scheme="AB4AM5", mu=None, A=1.0, aslda=False):
         box = ctx.add_box(shape, kind=W.ASLDA, C=-11.11, mu=m + ASLDA_DMU[0], mu_b=m + ASLDA_DMU[1],
                           nstates=wl["nstates"])
     else:
-        box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=m, A=A,
-                          nstates=wl["nstates"])
+        box = ctx.add_box(shape, kind=W.SLDA if A != 1.0 else W.SLDA_A1, B=W.B_SLDA, C=u["C"] if C is None else C,
+                          mu=m, A=A, nstates=wl["nstates"])
     ctx.set_vext(box, inputs.harmonic_trap(shape, wl["omega"]))
     return ctx, box, u
 
@@ -290,9 +293,10 @@ SCF_START = {}
 
 def scf_start(W, args, wl):
     """Trapped start from a static self-consistent solve (Alg. 1) of the
-    workload's SLDA system with a particle-number target (Eq. update-mu),
-    modified Broyden mixing and single-precision leading iterations; the
-    states are kept in host memory for every arm."""
+    workload's SLDA system with the printed C (a trapped solve needs C < 0,
+    the seed's backed-out C is positive), a particle-number target (Eq.
+    update-mu), modified Broyden mixing and single-precision leading
+    iterations; the states are kept in host memory for every arm."""
     if "phi" in SCF_START:
         return SCF_START
     from paper_2602_08982_b300 import inputs
@@ -300,10 +304,10 @@ def scf_start(W, args, wl):
     M = shape[0] * shape[1] * shape[2]
     u = W.uniform_solve(shape, kind=W.SLDA_A1, B=W.B_SLDA, rho_sigma=RHO_SIGMA, delta0=0.25)
     ctx = W.Context(W.FP64)
-    b = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=u["C"], mu=u["mu"], nstates=M)
+    b = ctx.add_box(shape, kind=W.SLDA_A1, B=W.B_SLDA, C=W.C_ASLDA, mu=u["mu"], nstates=M)
     ctx.set_vext(b, inputs.harmonic_trap(shape, wl["omega"]))
     t0 = time.perf_counter()
-    res, _ = ctx.static_solve(b, np.full(M, u["U"]), np.full(M, u["delta"]), method="broyden", mixing=0.5,
+    res, _ = ctx.static_solve(b, np.full(M, u["U"]), np.full(M, u["delta"]), method="broyden", mixing=0.3,
                               eps_energy=1e-6, max_iters=args.scf_iters, n_target=args.scf_n, a_mu=0.5,
                               eps_npart=1e-3, fp32_iters=args.scf_fp32_iters)
     sec = time.perf_counter() - t0
@@ -320,7 +324,8 @@ def run_arm(W, torch, prec, args, wl, rank, world, dev):
     shape, nstates = wl["shape"], wl["nstates"]
     if args.init == "scf":
         start = scf_start(W, args, wl)
-        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, mu=start["info"]["mu"], A=args.A)
+        ctx, box, u = make_box(W, prec, wl, stream.cuda_stream, args.integrator, mu=start["info"]["mu"], A=args.A,
+                               C=W.C_ASLDA)
         ctx.load_states(box, start["phi"])
         ctx.start(True, args.dt)               # a static solution: stationary start
     else:
@@ -713,7 +718,7 @@ def workload_config(args, wl, precision):
             "dt": args.dt,
             "functional": (f"SLDA with current terms (A={args.A}), " if args.A != 1.0 else "SLDA (A=1), ")
                           + "B=B_ASLDA(0), C from the uniform 16^3-style seed on this lattice",
-            "init": ("states of a static self-consistent solve (fixed N, Broyden), stationary start"
+            "init": ("states of a static self-consistent solve with C = -11.11 (fixed N, Broyden), stationary start"
                      if args.init == "scf" else
                      "uniform plane-wave BCS states (Delta0 = 0.5 eF) quenched into the trap, Taylor start"),
             "friction": args.friction, "precision": precision,

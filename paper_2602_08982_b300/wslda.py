@@ -23,6 +23,7 @@ A_ASLDA = 1.094  # A_a(0) of the ASLDA functional (Sec. 2.4)
 SCHEMES = {"AB4AM5": 0, "AB3AM4": 1, "AB5AM5": 2}
 # B of the spin-symmetric ASLDA functional (Sec. 2.4): 2^(2/3) [0.357 - 2 A(0) 2^(-5/3)], A(0) = 1.094
 B_SLDA = 2.0 ** (2.0 / 3.0) * (0.357 - 2.0 * 1.094 * 2.0 ** (-5.0 / 3.0))
+C_ASLDA = -11.11  # C of the ASLDA functional as printed (Sec. 2.4)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN", 5: "EDRIFT", 6: "ETIMEOUT", 7: "ESTATE",
           8: "EUNSUPPORTED"}
 KERNEL_KINDS = {"stage_x": 0, "stage_y": 1, "density": 2, "potentials": 3, "aux": 4}
