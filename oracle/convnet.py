@@ -12,9 +12,10 @@ Sec. 3.1), tanh between layers and a linear last layer, trained on the mean
 squared error with Adam (Kingma and Ba, arXiv:1412.6980). Weights are used in
 bfloat16 (rounded to nearest even from the float32 master copy), and so is
 every convolution operand: a layer's input enters its convolution rounded to
-bfloat16, the weight gradient uses those rounded inputs, and the gradient
-that the input-gradient convolution consumes is rounded too (the operands of
-a bfloat16 tensor-core GEMM with float32 accumulation). Everything else is
+bfloat16, and the gradient of a layer's output enters both gradient
+convolutions (with respect to the weights and to the input) rounded too,
+the weight gradient pairing it with the rounded inputs (the operands of
+bfloat16 tensor-core GEMMs with float32 accumulation). Everything else is
 float64 here. With bf16=False nothing is rounded (the plain network).
 
 Conventions: activations x[b, c, ix, iy, iz]; weights W[co, ci, dx, dy, dz]
@@ -113,13 +114,13 @@ def gradient(theta, shapes, x, t, bf16: bool = True):
         if i < len(params) - 1:
             g = g * (1.0 - acts[i + 1] ** 2)  # through tanh
         xin = to_bf16(acts[i]) if bf16 else acts[i]
+        gq = to_bf16(g) if bf16 else g
         gW = np.zeros_like(W)
         for d in OFFSETS:
-            gW[:, :, d[0] + 1, d[1] + 1, d[2] + 1] = np.einsum("boxyz,bcxyz->oc", g, shift(xin, d))
+            gW[:, :, d[0] + 1, d[1] + 1, d[2] + 1] = np.einsum("boxyz,bcxyz->oc", gq, shift(xin, d))
         gb = g.sum(axis=(0, 2, 3, 4))
         grads.append((gW, gb))
         # dL/dx[r] = sum_d W[:, :, d]^T g[r - d]
-        gq = to_bf16(g) if bf16 else g
         gx = np.zeros_like(xin)
         for d in OFFSETS:
             gx += np.einsum("oc,boxyz->bcxyz", Wq[:, :, d[0] + 1, d[1] + 1, d[2] + 1],

@@ -280,6 +280,175 @@ cudaError_t launch_tc(const ConvTcArgs& a, int batch, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+constexpr int kKc = 64;  // reduction (site) chunk of the weight-gradient GEMM
+
+// Weight gradient as a split-K implicit GEMM on the tensor cores:
+//   D[(d, ci)][co] = sum over sites k of bf16(x[ci][k + off(d)]) bf16(g[co][k]),
+// rows (d, ci) in 128-row tiles (blockIdx.x), the batch's sites split into
+// `nsplit` ranges (blockIdx.y), 64 sites per MMA round. Each CTA writes its
+// float32 partial tile to part[split][row][co]; wgrad_reduce sums the splits
+// in a fixed order.
+template <int CINP, int NP>
+__global__ void __launch_bounds__(kRows) wgrad_tc_kernel(const WgradTcArgs a) {
+  constexpr unsigned A_KG = unsigned(kRows / 8) * kCore;   // K-direction core stride in A (2048)
+  constexpr unsigned B_KG = unsigned(NP / 8) * kCore;      // K-direction core stride in B
+  constexpr unsigned A_BYTES = (kKc / 8) * A_KG, B_BYTES = (kKc / 8) * B_KG;
+  constexpr uint32_t IDESC = instr_desc(NP, kRows);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + A_BYTES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(Bs + B_BYTES);
+  const unsigned bar = smem_u32(Bs + B_BYTES + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int M = a.nx * a.ny * a.nz;
+  const int64_t K = int64_t(a.batch) * M;
+  const int64_t k_lo = int64_t(blockIdx.y) * a.ksplit;
+  const int64_t k_hi = k_lo + a.ksplit < K ? k_lo + a.ksplit : K;
+  if (tid == 0) {
+    mbar_init1(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const unsigned tmem = *tslot;
+  // thread -> (site of the chunk, half of the rows)
+  const int kk = tid & (kKc - 1), half = tid / kKc;
+  bool ok = true;
+  int round = 0;
+  for (int64_t k0 = k_lo; k0 < k_hi; k0 += kKc, ++round) {
+    if (round > 0) {
+      ok = mma_wait(bar, unsigned(round - 1) & 1u) && ok;
+      fence_after_sync();
+    }
+    const int64_t k = k0 + kk;
+    const bool live = k < k_hi;
+    int b = 0, r = 0, ix = 0, iy = 0, iz = 0;
+    if (live) {
+      b = int(k / M);
+      r = int(k % M);
+      iz = r % a.nz;
+      iy = (r / a.nz) % a.ny;
+      ix = r / (a.ny * a.nz);
+    }
+    const unsigned koff = unsigned(kk & 7) * 2;  // byte of this site within its 16-byte core row
+    // A: rows (d, ci) of this tile, this thread's site, 64 of the 128 rows
+    for (int m = half * 64; m < half * 64 + 64; ++m) {
+      const int row = blockIdx.x * kRows + m, d = row / CINP, ci = row % CINP;
+      float v = 0.f;
+      if (live && d < 27 && ci < a.cin) {
+        const int q = (wrapi(ix + d / 9 - 1, a.nx) * a.ny + wrapi(iy + (d / 3) % 3 - 1, a.ny)) * a.nz +
+                      wrapi(iz + d % 3 - 1, a.nz);
+        v = a.x[(size_t(b) * a.cin + ci) * M + q];
+      }
+      *reinterpret_cast<__nv_bfloat16*>(As + (kk >> 3) * A_KG + (m >> 3) * kCore + (m & 7) * 16 + koff) =
+          __float2bfloat16_rn(v);
+    }
+    // B: the output-gradient rows co, this thread's site
+    for (int n = half; n < NP; n += 2) {
+      float v = 0.f;
+      if (live && n < a.cout) v = a.g[(size_t(b) * a.cout + n) * M + r];
+      *reinterpret_cast<__nv_bfloat16*>(Bs + (kk >> 3) * B_KG + (n >> 3) * kCore + (n & 7) * 16 + koff) =
+          __float2bfloat16_rn(v);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      const unsigned a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+      for (int kb = 0; kb < kKc / 16; ++kb)
+        mma_bf16(tmem, smem_desc(a0 + 2 * kb * A_KG, A_KG, kCore), smem_desc(b0 + 2 * kb * B_KG, B_KG, kCore), IDESC,
+                 (round | kb) != 0);
+      mma_commit(bar);
+    }
+  }
+  if (round > 0) {
+    ok = mma_wait(bar, unsigned(round - 1) & 1u) && ok;
+    if (!ok) {
+      if (a.err && tid == 0) atomicOr(a.err, 8);
+      mma_wait(bar, unsigned(round - 1) & 1u);
+    }
+  }
+  fence_after_sync();
+  float v[NP];
+  const unsigned taddr = tmem + (unsigned(32 * warp) << 16);
+  tmem_ld16(taddr, v);
+  if constexpr (NP == 32) tmem_ld16(taddr + 16, v + 16);
+  const int row = blockIdx.x * kRows + tid;
+  float* dst = a.part + (size_t(blockIdx.y) * a.rows + row) * NP;
+#pragma unroll
+  for (int n = 0; n < NP; ++n) dst[n] = round > 0 ? v[n] : 0.f;
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// gW[co][ci][d] = sum over splits (ascending) of part[split][d * CINP + ci][co]
+__global__ void wgrad_reduce(const float* __restrict__ part, int nsplit, int rows, int np, int cinp, int cin, int cout,
+                             float* __restrict__ gW) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cout * cin * 27) return;
+  const int co = i / (cin * 27), ci = (i / 27) % cin, d = i % 27;
+  const int row = d * cinp + ci;
+  float acc = 0.f;
+  for (int sp = 0; sp < nsplit; ++sp) acc += part[(size_t(sp) * rows + row) * np + co];
+  gW[i] = acc;
+}
+
+template <int CINP, int NP>
+cudaError_t launch_wgrad(WgradTcArgs a, cudaStream_t s) {
+  constexpr size_t bytes = (kKc / 8) * size_t(kRows / 8) * kCore + (kKc / 8) * size_t(NP / 8) * kCore + 16 + 1024 +
+                           32768;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<CINP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(bytes));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int tiles = (27 * CINP + kRows - 1) / kRows;
+  a.rows = tiles * kRows;
+  const int64_t K = int64_t(a.batch) * a.nx * a.ny * a.nz;
+  // splits so that the grid covers about two waves of CTAs, each a whole number of 64-site chunks
+  int nsplit = (296 + tiles - 1) / tiles;
+  if (nsplit > a.max_split) nsplit = a.max_split;
+  int64_t ks = (K + nsplit - 1) / nsplit;
+  ks = (ks + kKc - 1) / kKc * kKc;
+  nsplit = int((K + ks - 1) / ks);
+  a.ksplit = ks;
+  wgrad_tc_kernel<CINP, NP><<<dim3(unsigned(tiles), unsigned(nsplit)), kRows, bytes, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = a.cout * a.cin * 27;
+  wgrad_reduce<<<unsigned((n + 255) / 256), 256, 0, s>>>(a.part, nsplit, a.rows, NP, CINP, a.cin, a.cout, a.gW);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv_wgrad_tc(const WgradTcArgs& a, cudaStream_t s) {
+  if (a.cin < 1 || a.cin > 32 || a.cout < 1 || a.cout > 32 || a.batch < 1 || a.max_split < 1)
+    return cudaErrorInvalidValue;
+  const bool k32 = a.cin > 16, n32 = a.cout > 16;
+  if (k32 && n32) return launch_wgrad<32, 32>(a, s);
+  if (k32) return launch_wgrad<32, 16>(a, s);
+  if (n32) return launch_wgrad<16, 32>(a, s);
+  return launch_wgrad<16, 16>(a, s);
+}
+
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int batch, cudaStream_t s) {
   if (a.cin < 1 || a.cin > 32 || a.cout < 1 || a.cout > 32 || batch < 1) return cudaErrorInvalidValue;
   const bool k32 = a.cin > 16, n32 = a.cout > 16;

@@ -22,4 +22,21 @@ struct ConvTcArgs {
 // off(d) = (d / 9 - 1, (d / 3) % 3 - 1, d % 3 - 1), float32 accumulation.
 cudaError_t launch_conv_tc(const ConvTcArgs& a, int batch, cudaStream_t s);
 
+struct WgradTcArgs {
+  int nx, ny, nz;
+  int cin, cout, batch;  // layer channels (1..32 each) and samples
+  const float* x;        // [batch][cin][M] layer input, rounded to bfloat16 as it is staged
+  const float* g;        // [batch][cout][M] gradient of the layer output (pre-activation), rounded likewise
+  float* part;           // scratch: max_split x 896 x 32 floats
+  int max_split;         // largest number of site ranges (split-K) the scratch holds
+  int rows, ksplit;      // set by the launcher
+  float* gW;             // [cout][cin][27] result
+  int* err;              // bit 3 set if an MMA completion wait timed out (may be NULL)
+};
+
+// gW[co][ci][d] = sum_b sum_r bf16(g[b][co][r]) bf16(x[b][ci][r + off(d)]),
+// float32 accumulation: split-K tensor-core GEMM, then a fixed-order sum of
+// the splits.
+cudaError_t launch_conv_wgrad_tc(const WgradTcArgs& a, cudaStream_t s);
+
 }  // namespace wslda

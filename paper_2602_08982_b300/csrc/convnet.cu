@@ -18,8 +18,9 @@
 // float32 accumulation; layer inputs are rounded to bfloat16 as they are
 // staged), forward with bias and tanh fused, and the input gradient as the
 // same convolution with transposed, mirrored weights times 1 - a^2 through
-// tanh; conv_bwd_weight (CTA per (co, ci), fixed-order reduction over batch
-// and sites, layer input rounded as in the forward pass), bias_grad, mse
+// tanh, and the weight gradient as a split-K GEMM over the sites with a
+// fixed-order sum of the splits (layer input and output gradient rounded to
+// bfloat16 likewise); bias_grad, mse
 // (gradient of the loss and per-block partial sums), adam, mirror_avg
 // (projection onto reflection-symmetric fields).
 #include <cuda_bf16.h>
@@ -43,14 +44,6 @@ struct Lat {
   int nx, ny, nz;
 };
 
-__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// site index of (ix, iy, iz) + d, periodic; d = offset index 0..26
-__device__ __forceinline__ int neighbour(const Lat& L, int ix, int iy, int iz, int d) {
-  const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-  return (wrap(ix + dx, L.nx) * L.ny + wrap(iy + dy, L.ny)) * L.nz + wrap(iz + dz, L.nz);
-}
-
 __global__ void quantize(const float* __restrict__ theta, float* __restrict__ wq, int64_t n, const int64_t* wb,
                          const int64_t* we) {
   // weight entries [wb[l], we[l]) of each layer are rounded; biases are copied
@@ -59,43 +52,6 @@ __global__ void quantize(const float* __restrict__ theta, float* __restrict__ wq
   bool w = false;
   for (int l = 0; l < kLayers; ++l) w = w || (i >= wb[l] && i < we[l]);
   wq[i] = w ? __bfloat162float(__float2bfloat16_rn(theta[i])) : theta[i];
-}
-
-// Weight gradient: CTA per (co, ci); 27 partial sums per thread over the
-// batch and sites, then a fixed-order reduction across the CTA. The layer
-// input enters rounded to bfloat16, as the forward convolution used it.
-__global__ void __launch_bounds__(256) conv_bwd_weight(Lat L, int cin, int cout, int batch,
-                                                       const float* __restrict__ g, const float* __restrict__ x,
-                                                       float* __restrict__ gW) {
-  __shared__ float red[8][27];
-  const int co = blockIdx.x / cin, ci = blockIdx.x % cin;
-  const int M = L.nx * L.ny * L.nz;
-  float acc[27];
-#pragma unroll
-  for (int d = 0; d < 27; ++d) acc[d] = 0.f;
-  const int64_t total = int64_t(batch) * M;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = int(t / M), s = int(t % M);
-    const int iz = s % L.nz, iy = (s / L.nz) % L.ny, ix = s / (L.ny * L.nz);
-    const float gv = g[(int64_t(b) * cout + co) * M + s];
-    const float* xb = x + (int64_t(b) * cin + ci) * M;
-#pragma unroll
-    for (int d = 0; d < 27; ++d)
-      acc[d] = fmaf(gv, __bfloat162float(__float2bfloat16_rn(xb[neighbour(L, ix, iy, iz, d)])), acc[d]);
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    float v = acc[d];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[w][d] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 27) {
-    float v = 0.f;
-    for (int i = 0; i < int(blockDim.x >> 5); ++i) v += red[i][threadIdx.x];
-    gW[(co * cin + ci) * 27 + threadIdx.x] = v;
-  }
 }
 
 // Bias gradient: CTA per output channel.
@@ -191,6 +147,7 @@ struct wslda_net {
   float *g0 = nullptr, *g1 = nullptr;
   double* part = nullptr;
   int* err_d = nullptr;  // device error word (bit 3: a tensor-core completion wait timed out)
+  float* wpart = nullptr;  // split-K partial sums of the weight gradient
   int64_t *wb = nullptr, *we = nullptr;
   int64_t step = 0;
   std::vector<void*> owned;
@@ -199,6 +156,7 @@ struct wslda_net {
 
 namespace {
 constexpr int kMseBlocks = 148;
+constexpr int kMaxSplit = 64;  // site ranges of the weight-gradient GEMM
 
 wslda_status net_fail(wslda_net* n, wslda_status s, const std::string& msg) {
   if (n) n->err = msg;
@@ -271,6 +229,7 @@ wslda_status wslda_net_create(int nx, int ny, int nz, int hidden, int max_batch,
             alloc((void**)&n->grad, n->P * 4) && alloc((void**)&n->m, n->P * 4) && alloc((void**)&n->v, n->P * 4) &&
             alloc((void**)&n->g0, amax) && alloc((void**)&n->g1, amax) &&
             alloc((void**)&n->part, kMseBlocks * sizeof(double)) && alloc((void**)&n->err_d, sizeof(int)) &&
+            alloc((void**)&n->wpart, size_t(kMaxSplit) * 896 * 32 * sizeof(float)) &&
             alloc((void**)&n->wb, kLayers * 8) &&
             alloc((void**)&n->we, kLayers * 8);
   for (int l = 1; l <= kLayers && ok; ++l)
@@ -344,9 +303,14 @@ wslda_status wslda_net_loss_grad(wslda_net* n, const float* x, const float* t, i
     e = cudaGetLastError();
   }
   for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
-    conv_bwd_weight<<<unsigned(n->cout[l] * n->cin[l]), 256, 0, s>>>(n->L, n->cin[l], n->cout[l], batch, g,
-                                                                     n->act[l], n->grad + n->woff[l]);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    {
+      wslda::WgradTcArgs w{};
+      w.nx = n->L.nx; w.ny = n->L.ny; w.nz = n->L.nz;
+      w.cin = n->cin[l]; w.cout = n->cout[l]; w.batch = batch;
+      w.x = n->act[l]; w.g = g; w.part = n->wpart; w.max_split = kMaxSplit;
+      w.gW = n->grad + n->woff[l]; w.err = n->err_d;
+      if ((e = wslda::launch_conv_wgrad_tc(w, s)) != cudaSuccess) break;
+    }
     bias_grad<<<unsigned(n->cout[l]), 256, 0, s>>>(n->M, n->cout[l], batch, g, n->grad + n->boff[l]);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if (l > 0) {
