@@ -19,7 +19,8 @@ Default run (N = 1):
     steps per CUDA graph, boxes on forked streams.
   * mixed_vs_oracle: the mixed path against the CPU oracle on a bounded
     sample of the main workload (same lattice, trap and vortex, a subset of
-    the states as the whole system), after 100 steps, with the energy drift.
+    the states as the whole system), after 200 steps (the elongated-trap
+    configuration's horizon), with the energy drift.
   * energy_drift: drift of E_tot - mu N over the timed run.
   * cufft: the kinetic-term transforms of one stage (forward 3D FFT of u and
     v, multiply by k^2/2, inverse) done with cuFFT (through torch.fft) on the
@@ -90,7 +91,7 @@ def parse():
                    help="skip the batched workload (64 cubic boxes 12^3..24^3, BdG, one graph per 4 steps)")
     p.add_argument("--no-oracle-check", action="store_true", help="skip the mixed-vs-oracle sample")
     p.add_argument("--oracle-states", type=int, default=32)
-    p.add_argument("--oracle-steps", type=int, default=100)
+    p.add_argument("--oracle-steps", type=int, default=200)
     p.add_argument("--no-cufft", action="store_true")
     p.add_argument("--integrator", default="AB4AM5", choices=["AB4AM5", "AB3AM4", "AB5AM5"],
                    help="predictor-corrector scheme of Sec. 3.3 (AB4AM5 is Alg. 2)")

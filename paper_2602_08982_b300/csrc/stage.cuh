@@ -838,7 +838,8 @@ __device__ __forceinline__ void stage_state(const StageArgs<typename G::R>& a, c
 // MODE_GRAD / MODE_AGRAD for one state: derivatives along z, y, x in turn,
 // each from a fresh load of the input slab, each followed by its sweep.
 template <class G, int MODE>
-__device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, const int n, const int ncl) {
+__device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, const int n, const int ncl,
+                                            const unsigned iter = 0) {
   using C = typename G::C;
   using R = typename G::R;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -864,14 +865,30 @@ __device__ __forceinline__ void deriv_state(const StageArgs<typename G::R>& a, c
   if (tid < 2 && n + ncl < a.nstates)
     prefetch_l2(a.phi + size_t(n + ncl) * 2 * G::M + size_t(tid) * G::M + gs0, unsigned(G::NS * sizeof(C)));
   R ep = 0, ec = 0;  // AGRAD: compensated partial of sum Re(phi^* G)
+  const unsigned bar = static_cast<unsigned>(__cvta_generic_to_shared(red + G::RED_BAR));
 #pragma unroll 1
   for (int d = 2; d >= 0; --d) {
     if (d != 2) __syncthreads();  // the previous sweep has read the slab
-    for (int i = tid; i < 2 * G::NS; i += G::BT) {
-      const int comp = i / G::NS, s = i % G::NS;
-      cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
+    if constexpr (G::BULK) {
+      // one bulk copy per z row on the slab barrier: completion 3 iter + (2 - d)
+      if (tid < 32) {
+        if (tid == 0) mbar_arrive_expect_tx(bar, unsigned(2 * G::NS * sizeof(C)));
+        __syncwarp();
+        const unsigned b0 = static_cast<unsigned>(__cvta_generic_to_shared(buf));
+        for (int r = tid; r < 2 * G::P * G::NY; r += 32) {
+          const int comp = r / (G::P * G::NY), row = r % (G::P * G::NY);
+          bulk_g2s(b0 + unsigned((comp * G::SLAB + row * G::ZP) * sizeof(C)), in + comp * G::M + gs0 + row * G::NZ,
+                   unsigned(G::NZ * sizeof(C)), bar);
+        }
+      }
+      mbar_wait(bar, (3u * iter + unsigned(2 - d)) & 1u, a.err);
+    } else {
+      for (int i = tid; i < 2 * G::NS; i += G::BT) {
+        const int comp = i / G::NS, s = i % G::NS;
+        cp_async<sizeof(C)>(buf + comp * G::SLAB + sidx(s), in + comp * G::M + gs0 + s);
+      }
+      cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     if (d == 2) {
       local_deriv<G, 2>(buf, ktab, tws + G::NX + G::NY);
@@ -973,7 +990,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_cons
     tws[i] = a.tw[i];
   }
   const int ncl = gridDim.x / G::CS;
-  if constexpr (G::BULK && MODE != MODE_GRAD && MODE != MODE_AGRAD) {
+  if constexpr (G::BULK) {
     if (threadIdx.x == 0) {
       double* red = reinterpret_cast<double*>(tws + NAX);
       red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
@@ -986,7 +1003,7 @@ __global__ void __launch_bounds__(G::BT, G::MINB) stage_kernel(const __grid_cons
 #pragma unroll 1
     for (int n = blockIdx.x / G::CS; n < a.nstates; n += ncl, ++iter) {
       __syncthreads();
-      if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, n, ncl);
+      if constexpr (MODE == MODE_GRAD || MODE == MODE_AGRAD) deriv_state<G, MODE>(a, n, ncl, iter);
       else stage_state<G, MODE, GEN>(a, n, ncl, iter);
     }
   } else {
