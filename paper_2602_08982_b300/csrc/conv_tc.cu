@@ -19,8 +19,8 @@
 // W'[ci][co][d] = W[co][ci][26 - d] (offsets mirrored, channels transposed)
 // gx[ci][r] = sum_d sum_co W'[ci][co][d] g[co][r + off(d)].
 //
-// Flow per CTA: weights of all 27 offsets into shared memory once; then three
-// chunks of nine offsets (one x offset each): the 128 threads gather and round
+// Flow per CTA: weights of all 27 offsets into shared memory once; then nine
+// chunks of three offsets (one (dx, dy) pair each): the 128 threads gather and round
 // their row of each A tile, one thread issues the chunk's MMAs and commits
 // them to an mbarrier, and the next chunk waits on it before reusing the A
 // buffer. Every wait is bounded; on a timeout bit 3 of the error word is set
@@ -36,7 +36,7 @@ namespace wslda {
 namespace {
 
 constexpr int kRows = 128;          // GEMM rows (sites) per CTA
-constexpr int kChunk = 9;           // offsets per A buffer fill
+constexpr int kChunk = 3;           // offsets per A buffer fill (one dx, dy pair: dz = -1, 0, 1)
 constexpr unsigned kCore = 128;     // bytes per 8 x 16-byte core matrix
 constexpr unsigned kTmemCols = 32;  // accumulator columns (N <= 32)
 
@@ -182,15 +182,16 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
   fence_after_sync();
   const unsigned tmem = *tslot;
   bool ok = true;
-  for (int c = 0; c < 3; ++c) {
+  constexpr int NCH = 27 / kChunk;
+  for (int c = 0; c < NCH; ++c) {
     if (c > 0) {  // the previous chunk's MMAs have read the A buffer
       ok = mma_wait(bar, unsigned(c - 1) & 1u) && ok;
       fence_after_sync();
     }
-    // this thread's row of the nine A tiles of offsets dx = c - 1
+    // this thread's row of the A tiles of offsets d = 3c + dl: dx = c / 3 - 1, dy = c % 3 - 1, dz = dl - 1
     for (int dl = 0; dl < kChunk; ++dl) {
-      const int q = s < M ? (wrapi(ix + c - 1, a.nx) * a.ny + wrapi(iy + dl / 3 - 1, a.ny)) * a.nz +
-                                wrapi(iz + dl % 3 - 1, a.nz)
+      const int q = s < M ? (wrapi(ix + c / 3 - 1, a.nx) * a.ny + wrapi(iy + c % 3 - 1, a.ny)) * a.nz +
+                                wrapi(iz + dl - 1, a.nz)
                           : 0;
 #pragma unroll
       for (int g = 0; g < KG; ++g) {
@@ -223,10 +224,10 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
       mma_commit(bar);
     }
   }
-  ok = mma_wait(bar, 0u) && ok;  // third completion: parity 0 again
+  ok = mma_wait(bar, unsigned(NCH - 1) & 1u) && ok;  // the last chunk's completion
   if (!ok) {
     if (a.err) atomicOr(a.err, 8);
-    mma_wait(bar, 0u);
+    mma_wait(bar, unsigned(NCH - 1) & 1u);
   }
   fence_after_sync();
   // epilogue: lane = row of this warp's quarter of the accumulator
@@ -261,10 +262,9 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
 
 template <int CINP, int NP>
 cudaError_t launch_tc(const ConvTcArgs& a, int batch, cudaStream_t s) {
-  // operands, tensor-memory slot and barrier, alignment slack, and 32 KB past
-  // the end so that no descriptor can address memory outside the allocation
+  // operands, tensor-memory slot and barrier, alignment slack
   constexpr size_t bytes = 27 * size_t(CINP / 8) * (NP / 8) * kCore + kChunk * size_t(CINP / 8) * (kRows / 8) * kCore +
-                           16 + 1024 + 32768;
+                           16 + 1024;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CINP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -410,8 +410,7 @@ __global__ void wgrad_reduce(const float* __restrict__ part, int nsplit, int row
 
 template <int CINP, int NP>
 cudaError_t launch_wgrad(WgradTcArgs a, cudaStream_t s) {
-  constexpr size_t bytes = (kKc / 8) * size_t(kRows / 8) * kCore + (kKc / 8) * size_t(NP / 8) * kCore + 16 + 1024 +
-                           32768;
+  constexpr size_t bytes = (kKc / 8) * size_t(kRows / 8) * kCore + (kKc / 8) * size_t(NP / 8) * kCore + 16 + 1024;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<CINP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,

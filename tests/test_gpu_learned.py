@@ -24,13 +24,19 @@ def _setup(shape, hidden, batch, seed):
     return net, shapes, theta, x, t, xd, td
 
 
-@pytest.mark.parametrize("shape,hidden,batch", [((6, 6, 8), 8, 2), ((12, 12, 12), 32, 3), ((5, 7, 9), 32, 2)])
+@pytest.mark.parametrize("shape,hidden,batch", [((6, 6, 8), 8, 2), ((12, 12, 12), 32, 3), ((5, 7, 9), 32, 2),
+                                                ((32, 32, 32), 32, 2)],
+                         ids=["6x6x8", "12cubed", "5x7x9", "32cubed"])
 def test_each_tensor_core_layer_matches_oracle(shape, hidden, batch):
     """Every layer of the forward pass (tensor-core implicit GEMM, bfloat16
     operands, float32 accumulation) against the oracle's layer fed the GPU's
     own layer input, so both sides round the same float32 values to
-    bfloat16 and differ only in the accumulation: within 1e-5 of the largest
-    output. The 5x7x9 lattice leaves a ragged last tile of 128 sites."""
+    bfloat16 and differ only in the accumulation. The bound is elementwise
+    and follows from the arithmetic: the bfloat16 products are exact in
+    float32, and any order of n float32 additions, each with a relative error
+    of at most 2^-23 (round to nearest or toward zero), is within
+    n 2^-23 sum |terms| of the exact sum; tanh does not enlarge it. The 5x7x9
+    lattice leaves a ragged last tile of 128 sites."""
     import torch
     net, shapes, theta, x, t, xd, td = _setup(shape, hidden, batch, 303)
     y = torch.empty_like(xd)
@@ -40,11 +46,15 @@ def test_each_tensor_core_layer_matches_oracle(shape, hidden, batch):
     outs = ins[1:] + [y.cpu().numpy()]
     for l, (W, b) in enumerate(params):
         xin = ins[l].astype(np.float64).reshape((batch, -1) + shape)
-        ref = cn.conv(cn.to_bf16(xin), cn.to_bf16(W), b)
+        xq, Wq = cn.to_bf16(xin), cn.to_bf16(W)
+        ref = cn.conv(xq, Wq, b)
+        bound = (27 * xin.shape[1] + 1) * 2.0 ** -23 * cn.conv(np.abs(xq), np.abs(Wq), np.abs(b)) + 1e-6
         if l < 3:
             ref = np.tanh(ref)
         got = outs[l].reshape(ref.shape)
-        assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max(), l
+        err = np.abs(got - ref)
+        assert (err <= bound).all(), (l, float(err.max()), float((err / bound).max()))
+        assert err.max() < 1e-4 * max(np.abs(ref).max(), 1.0), l
     net.close()
 
 
