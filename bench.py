@@ -394,6 +394,14 @@ def run_arm(W, torch, prec, args, wl, rank, world, dev):
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "stage_x (f + AB4 predictor + AM5 partial + normalisation), FP64",
                 "peak_source": src, "algorithmic_flops_per_state_site": fx}
+        try:
+            # the count takes additions and multiplications as one operation each and the
+            # butterflies are mostly unfused, so the FP64 addition issue rate also bounds them
+            add = W.measure_fp64_add_rate(5)
+            roof["unfused"] = {"peak": add, "unit": "Tops/s", "frac": achieved / add,
+                               "peak_source": "of measured (FP64 addition microbenchmark on this GPU, this run)"}
+        except W.WsldaError:
+            pass
     sb = step_algorithmic_bytes(prec, args.integrator)
     step_gbs = sb * per_launch / (ms / args.steps * 1e-3) / 1e9
     share = {k: kt[k][0] / ms for k in kt}

@@ -308,6 +308,11 @@ wslda_status wslda_imprint_phase(wslda_ctx* ctx, int box, int comp, const double
  * the method: it is the measured peak against which the FP64 step's
  * ALU-bound stage kernels are reported. Changes no device setting. */
 wslda_status wslda_measure_fp64_rate(int reps, double* tflops);
+/* FP64 addition throughput of the current device in tera-operations per
+ * second (one addition per instruction), measured the same way: the ceiling
+ * of FP64 work made of unfused additions and multiplications, such as the
+ * butterflies of the transforms. A microbenchmark, not a step of the method. */
+wslda_status wslda_measure_fp64_add_rate(int reps, double* tops);
 
 /* Static self-consistent solve (Alg. 1, Sec. 3.2) of a trapped, spin-symmetric
  * T = 0 system, whose positive-energy eigenstates then become the box's states

@@ -33,7 +33,71 @@ __global__ void __launch_bounds__(256) fp64_fma_chains(double* sink, int iters, 
   if (t == -1.0) sink[blockIdx.x] = t;  // never true for a in (0, 1), b > 0
 }
 
+// The same with additions: the FP64 butterflies of the transforms are mostly
+// unfused additions and multiplications, each one operation per instruction.
+__global__ void __launch_bounds__(256) fp64_add_chains(double* sink, int iters, double b) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * double(threadIdx.x + c);
+#pragma unroll 1
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = x[c] + b;
+    }
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) t += x[c];
+  if (t == -1.0) sink[blockIdx.x] = t;  // never true for b > 0
+}
+
+// Best time over `reps` launches (after one warm-up) of the chain kernel.
+template <class K>
+wslda_status time_chains(int reps, K launch, float* best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  wslda_status st = WSLDA_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = WSLDA_ECUDA;
+  float best = 1e30f;
+  for (int r = 0; r <= reps && st == WSLDA_OK; ++r) {
+    cudaEventRecord(e0, 0);
+    launch();
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = WSLDA_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms < best) best = ms;
+  }
+  if (cudaGetLastError() != cudaSuccess) st = WSLDA_ECUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  *best_ms = best;
+  return st;
+}
+
 }  // namespace
+
+extern "C" wslda_status wslda_measure_fp64_add_rate(int reps, double* tops) {
+  if (!tops || reps < 1) return WSLDA_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return WSLDA_ECUDA;
+  const int blocks = sms * 8, threads = 256, iters = 1024;
+  double* sink = nullptr;
+  if (cudaMalloc(&sink, size_t(blocks) * sizeof(double)) != cudaSuccess) return WSLDA_ENOMEM;
+  float best = 0.f;
+  const wslda_status st =
+      time_chains(reps, [&] { fp64_add_chains<<<blocks, threads>>>(sink, iters, 1e-7); }, &best);
+  cudaFree(sink);
+  if (st != WSLDA_OK) return st;
+  const double adds = double(blocks) * threads * double(iters) * 16.0 * kChains;
+  *tops = adds / (double(best) * 1e-3) / 1e12;
+  return WSLDA_OK;
+}
 
 extern "C" wslda_status wslda_measure_fp64_rate(int reps, double* tflops) {
   if (!tflops || reps < 1) return WSLDA_EINVAL;

@@ -124,6 +124,7 @@ def _load():
         "wslda_static_solve": (I, [P, I, P, P, ct.POINTER(ScfParams), P, ct.POINTER(ScfResult)]),
         "wslda_imprint_phase": (I, [P, I, I, P, I]),
         "wslda_measure_fp64_rate": (I, [I, DP]),
+        "wslda_measure_fp64_add_rate": (I, [I, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -161,6 +162,16 @@ def measure_fp64_rate(reps: int = 5) -> float:
     st = lib.wslda_measure_fp64_rate(int(reps), ct.byref(out))
     if st:
         raise WsldaError(st, "wslda_measure_fp64_rate failed")
+    return out.value
+
+
+def measure_fp64_add_rate(reps: int = 5) -> float:
+    """FP64 addition throughput of the current device in tera-operations per
+    second (wslda_measure_fp64_add_rate)."""
+    out = ct.c_double()
+    st = lib.wslda_measure_fp64_add_rate(int(reps), ct.byref(out))
+    if st:
+        raise WsldaError(st, "wslda_measure_fp64_add_rate failed")
     return out.value
 
 

@@ -261,3 +261,14 @@ def test_complex_float_state_io(prec):
     back = b.get_states(bx)
     b.close()
     assert np.array_equal(back, c.phi.astype(np.complex64).astype(np.complex128))
+
+
+def test_fp64_rate_probes_measure_the_device():
+    """The FP64 microbenchmarks behind the FP64 step's roofline: finite and
+    positive, and an addition (one operation per instruction) issues no
+    faster than an FMA delivers its two."""
+    from paper_2602_08982_b300 import wslda as W
+    fma = W.measure_fp64_rate(2)
+    add = W.measure_fp64_add_rate(2)
+    assert np.isfinite(fma) and np.isfinite(add) and fma > 0.1 and add > 0.05
+    assert add < fma
