@@ -9,7 +9,10 @@ Workflow around the wslda_net_* kernels and wslda_static_solve:
   * predict(): the network's fields, averaged over the lattice reflections so
     that they have the symmetry the solver requires;
   * iterations(): self-consistent iterations from a given start, with the
-    plain linear mixing that serves as the fallback and judge.
+    plain linear mixing that serves as the fallback and judge;
+  * converged_td(): a static solve from a given start, then the
+    mixed-precision time evolution of its states (the use the method makes
+    of a converged state).
 Device memory comes from torch; every arithmetic step runs in the library.
 """
 from __future__ import annotations
@@ -137,3 +140,24 @@ def iterations(shape, om, inv_kfa, U0=None, D0=None, mixing=0.5, eps=1e-6, max_i
     uniform system's fields)."""
     res, _, _ = solve(shape, om, inv_kfa, U0, D0, method="linear", mixing=mixing, eps=eps, max_iters=max_iters)
     return res["iters"], res["converged"]
+
+
+def converged_td(shape, om, inv_kfa, U0, D0, steps: int = 100, dt: float = 0.007, eps: float = 1e-7,
+                 max_iters: int = 400):
+    """Static solve of one trap from (U0, D0) (Broyden mixing), then `steps`
+    steps of the mixed-precision TD evolution (AB4AM5, stationary start) of its
+    states. Returns (solve result, largest relative change of rho over the
+    evolution, relative drift of E_tot - mu N)."""
+    ctx, b, _ = _box(shape, om, inv_kfa)
+    res, _ = ctx.static_solve(b, U0, D0, method="broyden", mixing=0.5, eps_energy=eps, max_iters=max_iters)
+    rho0, _ = ctx.get_densities(b)
+    phi = ctx.get_states(b)
+    ctx.close()
+    ctx, b, _ = _box(shape, om, inv_kfa, precision=W.MIXED)
+    ctx.load_states(b, phi)
+    ctx.start(True, dt)
+    ctx.step(dt, steps)
+    rho1, _ = ctx.get_densities(b)
+    de, _ = ctx.check_conservation(b, float("inf"), float("inf"))
+    ctx.close()
+    return res, float(np.abs(rho1 - rho0).max() / np.abs(rho0).max()), float(de)

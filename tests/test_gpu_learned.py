@@ -166,8 +166,19 @@ def test_trained_network_cuts_static_iterations():
         # the BdG functional has no mean field: only Delta is taken from the network
         n1, ok1 = L.iterations(shape, om, a, U0=np.zeros_like(U), D0=D, eps=1e-5, max_iters=cap)
         rows.append((seed, n0 if ok0 else cap, ok0, n1 if ok1 else cap, ok1))
+    # the pipeline the learned start feeds: a converged static solve from the
+    # network's fields, then 100 mixed-precision TD steps of its states
+    om, a = L.draw_trap(HELD_OUT[0], 0.1, 0.2)
+    U, D = L.predict(net, L.net_input(shape, om, a))
+    res, drho, de = L.converged_td(shape, om, a, np.zeros_like(U), D, steps=100)
     net.close()
     print("held-out traps (seed, uniform iters, converged, network iters, converged):", rows)
+    for k, name in ((1, "uniform start"), (3, "network start")):
+        it = [r[k] for r in rows]
+        print(f"{name}: mean {np.mean(it):.1f}, median {np.median(it):.1f} iterations (cap {cap} counted)")
+    print(f"100 mixed TD steps from the network-started solve ({res['iters']} Broyden iterations): "
+          f"rho changes by {drho:.2e}, E - mu N drifts by {de:.2e}")
+    assert res["converged"] and drho < 1e-3 and de < 1e-5
     assert sum(r[4] for r in rows) >= sum(r[2] for r in rows), rows
     assert np.mean([r[3] for r in rows]) < np.mean([r[1] for r in rows]), rows
     both = [r for r in rows if r[2] and r[4]]
