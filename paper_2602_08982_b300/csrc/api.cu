@@ -49,6 +49,7 @@ struct Box {
   int ncl = 0;           // persistent stage launches: clusters (0 = one cluster per state)
   const KernelSet* ks_y = nullptr;  // launch variant of the corrector stage (NULL: ks)
   int ncl_y = 0;
+  int kt[3] = {1, 1, 1};  // lanes per x / y / z pencil the kinetic tables are ordered for
   size_t csize = 0;      // bytes per complex element (8 or 16)
   int D = 3;             // history values the predictor reads (AB3AM4 2, AB4AM5 3, AB5AM5 4)
   void* slot[6] = {};    // D + 2 state buffers [n][2][M]
@@ -310,6 +311,9 @@ double box_dV(const Box& b) { return b.lat.dx * b.lat.dy * b.lat.dz; }
 // predictor-stage kernel mode of the box's scheme
 int x_mode(const Box& b) { return b.D == 2 ? MODE_X3 : (b.D == 4 ? MODE_X5 : MODE_X); }
 
+// whether a launch variant reads the box's kinetic tables in their order
+bool same_layout(const KernelSet* k, const Box& b) { return k->tx == b.kt[0] && k->ty == b.kt[1] && k->tz == b.kt[2]; }
+
 // A stage launch; normalising modes are followed by the kernel that turns the
 // per-CTA norm partials into the per-state factor (same profiling scope).
 template <typename R>
@@ -318,6 +322,7 @@ wslda_status launch_mode(wslda_ctx* c, Box& b, int mode, StageArgs<R>& a, int ki
   if (b.n == 0) return WSLDA_OK;
   const bool ym = mode == MODE_Y && b.ks_y;
   const KernelSet* ks = ym ? b.ks_y : b.ks;
+  if (!same_layout(ks, b)) return fail(c, WSLDA_EUNSUPPORTED, "launch variant does not match the kinetic tables");
   const bool gen = b.cur && applies_h(mode);
   if (gen) {
     // current term -(i/2){A, grad} phi of this launch's input states and its
@@ -570,7 +575,11 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
   const char* pers = getenv("WSLDA_PERSIST");
   // boxes with the current terms run their H stages one cluster per state
   const int pmode = b.cur ? 0 : (pers ? (atoi(pers) ? 1 : 0) : -1);
-  std::vector<const KernelSet*> v = find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
+  std::vector<const KernelSet*> v;
+  // only variants whose pencils split over the same lanes as the box's kinetic
+  // tables (the frequency order of a transformed pencil depends on it)
+  for (const KernelSet* k : find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz))
+    if (same_layout(k, b)) v.push_back(k);
   if (forced) v.assign(1, b.ks);
   if (v.size() == 1 && pmode >= 0) {
     b.ncl = pmode ? resident_clusters(b.ks) : 0;
@@ -581,7 +590,7 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
       const std::vector<const KernelSet*> all =
           find_variants(c->prec == WSLDA_MIXED, b.lat.nx, b.lat.ny, b.lat.nz);
       const int i = atoi(fy);
-      if (i >= 0 && i < int(all.size())) b.ks_y = all[i];
+      if (i >= 0 && i < int(all.size()) && same_layout(all[i], b)) b.ks_y = all[i];
     }
     b.ncl_y = pmode ? resident_clusters(b.ks_y) : 0;
     return WSLDA_OK;
@@ -983,6 +992,9 @@ int wslda_add_box(wslda_ctx* c, const wslda_lattice* lat, const wslda_functional
   b.n = nstates;
   b.M = int(M);
   b.ks = ks;
+  b.kt[0] = ks->tx;
+  b.kt[1] = ks->ty;
+  b.kt[2] = ks->tz;
   b.csize = prec ? 8 : 16;
   const size_t rsize = prec ? 4 : 8;
   b.fdev.kind = fn->kind == WSLDA_FUNC_BDG ? 1 : 0;

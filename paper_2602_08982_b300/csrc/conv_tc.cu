@@ -421,8 +421,10 @@ cudaError_t launch_wgrad(WgradTcArgs a, cudaStream_t s) {
   const int tiles = (27 * CINP + kRows - 1) / kRows;
   a.rows = tiles * kRows;
   const int64_t K = int64_t(a.batch) * a.nx * a.ny * a.nz;
-  // splits so that the grid covers about two waves of CTAs, each a whole number of 64-site chunks
-  int nsplit = (296 + tiles - 1) / tiles;
+  // splits so that the grid covers about two CTAs per SM, each a whole number of 64-site chunks
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int nsplit = (2 * sms + tiles - 1) / tiles;
   if (nsplit > a.max_split) nsplit = a.max_split;
   int64_t ks = (K + nsplit - 1) / nsplit;
   ks = (ks + kKc - 1) / kKc * kKc;

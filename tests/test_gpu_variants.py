@@ -99,3 +99,29 @@ def test_scheme_variant_matches_oracle(prec, shape, variant, scheme, persist, mo
     rho, nu = ctx.get_densities(box)
     ctx.close()
     assert rel(rho, r) < tol and rel(nu, n) < tol, desc
+
+
+def test_corrector_variant_keeps_the_kinetic_table_layout(monkeypatch):
+    """The kinetic tables of a box are ordered for the lanes per pencil of its
+    launch variant (a pencil split over T lanes leaves its frequencies in a
+    T-dependent order). A corrector variant with another split (here FP64
+    32^3 with pencils over 2 lanes for the predictor, 4 for the requested
+    corrector) must not be taken: the corrector stays on the predictor's
+    layout and the step still matches the oracle."""
+    from paper_2602_08982_b300 import wslda as W
+    variants = W.lattice_variants(W.FP64, 32, 32, 32)
+    assert variants >= 3
+    c, (r, n) = _reference64((32, 32, 32))
+    monkeypatch.setenv("WSLDA_VARIANT", "0")
+    monkeypatch.setenv("WSLDA_VARIANT_Y", "2")
+    monkeypatch.setenv("WSLDA_PERSIST", "0")
+    ctx, box = gpu_context(c, W.FP64)
+    ctx.start(False, 0.01)
+    ctx.step(0.01, 2)
+    desc = ctx.get_variant(box)
+    rho, nu = ctx.get_densities(box)
+    ctx.close()
+    x_part, y_part = desc.split("; stage Y:")
+    lanes = lambda d: d.split("lanes_per_pencil=")[1].split()[0]
+    assert lanes(x_part) == lanes(y_part) == "2,2,2", desc
+    assert rel(rho, r) < 1e-12 and rel(nu, n) < 1e-12, desc
