@@ -562,7 +562,9 @@ wslda_status taylor_step(wslda_ctx* c, Box& b, double dt) {
 // Autotuner: time the predictor and the corrector stage of every compiled
 // launch variant of the box's shape, in both launch forms, on (a copy of) up
 // to 2048 of the box's states in the free history slots, and keep the fastest
-// for each stage. The choice is cached per shape, precision and state count
+// for each stage (for boxes with current terms, each stage together with the
+// current-term pass it needs and, for the predictor, the derivative launches
+// of the field refreshes, which run on its variant). The choice is cached per shape, precision and state count
 // for the process.
 template <typename R>
 wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
@@ -634,12 +636,36 @@ wslda_status autotune_box(wslda_ctx* c, Box& b, double dt) {
       a.sc_out = b.sc[b.ih[1]];
       a.dt = dt;
       a.err = c->err_d;
+      // boxes with current terms: each stage comes with its current-term pass
+      // (and the alpha-phi pass of ASLDA) on the same variant, and the
+      // derivative launches of the field refreshes run on the predictor's
+      // variant, so those are timed with the stages they go with
+      StageArgs<R> g = a;
+      g.h0 = static_cast<cx<R>*>(b.cur_buf);
+      g.av = static_cast<const fx4<R>*>(b.av);
+      g.av2 = static_cast<const fx4<R>*>(b.av_b);
+      g.alf = static_cast<const cx<R>*>(b.alf);
+      g.ecur = b.ecur;
+      g.wm = b.wm;
+      g.wp = b.wp;
+      StageArgs<R> ag = a;
+      ag.cur = static_cast<const cx<R>*>(b.cur_buf);
+      ag.ecur = b.ecur;
+      ag.alf = static_cast<const cx<R>*>(b.alf);
       for (int stage = 0; stage < 2; ++stage) {  // predictor stage, corrector stage
         const int m = stage ? int(MODE_Y) : x_mode(b);
         float ms = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-          CUDA_TRY(c, v[k]->launch[m](&a, int(nt), ncl, c->stream));
+          if (b.cur) {
+            CUDA_TRY(c, v[k]->launch[MODE_AGRAD](&g, int(nt), 0, c->stream));
+            if (b.aslda) CUDA_TRY(c, v[k]->launch[MODE_KALPHA](&g, int(nt), 0, c->stream));
+            CUDA_TRY(c, v[k]->launch_gen[m](&ag, int(nt), 0, c->stream));
+            if (stage == 0)
+              for (int r = 0; r < (b.aslda ? 4 : 2); ++r) CUDA_TRY(c, v[k]->launch[MODE_GRAD](&g, int(nt), 0, c->stream));
+          } else {
+            CUDA_TRY(c, v[k]->launch[m](&a, int(nt), ncl, c->stream));
+          }
           CUDA_TRY(c, cudaEventRecord(e1, c->stream));
           CUDA_TRY(c, cudaEventSynchronize(e1));
           float t = 0.f;
