@@ -19,11 +19,11 @@
 // W'[ci][co][d] = W[co][ci][26 - d] (offsets mirrored, channels transposed)
 // gx[ci][r] = sum_d sum_co W'[ci][co][d] g[co][r + off(d)].
 //
-// Flow per CTA: weights of all 27 offsets into shared memory once; then nine
-// chunks of three offsets (one (dx, dy) pair each): the 128 threads gather and round
+// Flow per CTA: nine chunks of three offsets (one (dx, dy) pair each): the
+// 128 threads stage the chunk's weights and gather and round
 // their row of each A tile, one thread issues the chunk's MMAs and commits
 // them to an mbarrier, and the next chunk waits on it before reusing the A
-// buffer. Every wait is bounded; on a timeout bit 3 of the error word is set
+// and B buffers. Every wait is bounded; on a timeout bit 3 of the error word is set
 // and the kernel still waits (bounded) for its MMAs, frees its tensor memory
 // and returns.
 #include <cuda_bf16.h>
@@ -36,6 +36,7 @@ namespace wslda {
 namespace {
 
 constexpr int kRows = 128;          // GEMM rows (sites) per CTA
+constexpr int kThreads = 256;       // forward kernel: two threads gather each row
 constexpr int kChunk = 3;           // offsets per A buffer fill (one dx, dy pair: dz = -1, 0, 1)
 constexpr unsigned kCore = 128;     // bytes per 8 x 16-byte core matrix
 constexpr unsigned kTmemCols = 32;  // accumulator columns (N <= 32)
@@ -126,13 +127,13 @@ __device__ __forceinline__ bool mma_wait(unsigned bar, unsigned parity) {
 }
 
 template <int CINP, int NP>
-__global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
+__global__ void __launch_bounds__(kThreads) conv_tc_kernel(const ConvTcArgs a) {
   constexpr int KG = CINP / 8;                          // 16-byte channel groups (core matrices along K)
   constexpr unsigned B_D = unsigned(KG) * (NP / 8) * kCore;      // bytes of one offset's weight tile
   constexpr unsigned B_KG = unsigned(NP / 8) * kCore;            // K-direction core stride in B
   constexpr unsigned A_KG = unsigned(kRows / 8) * kCore;         // K-direction core stride in A (2048)
   constexpr unsigned A_D = unsigned(KG) * A_KG;                  // bytes of one offset's A tile
-  constexpr unsigned B_BYTES = 27 * B_D, A_BYTES = kChunk * A_D;
+  constexpr unsigned B_BYTES = kChunk * B_D, A_BYTES = kChunk * A_D;
   constexpr uint32_t IDESC = instr_desc(NP, kRows);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -142,9 +143,10 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
   uint64_t* barp = reinterpret_cast<uint64_t*>(As + A_BYTES + 8);
   const unsigned bar = smem_u32(barp);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid % kRows, part = tid / kRows;  // row of the tile and which half of its gathers
   const int M = a.nx * a.ny * a.nz;
   const int b = blockIdx.y;
-  const int s = blockIdx.x * kRows + tid;  // this thread's row (site)
+  const int s = blockIdx.x * kRows + row;  // this thread's row (site)
 
   if (tid == 0) {
     mbar_init1(bar);
@@ -154,21 +156,6 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  // weights of every offset: 16-byte rows of 8 channels, zero past cin / cout
-  for (int q = tid; q < 27 * KG * NP; q += kRows) {
-    const int d = q / (KG * NP), rem = q % (KG * NP), g = rem / NP, n = rem % NP;
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = 8 * g + j;
-      float w = 0.f;
-      if (n < a.cout && k < a.cin)
-        w = a.transposed ? a.w[(size_t(k) * a.cout + n) * 27 + (26 - d)] : a.w[(size_t(n) * a.cin + k) * 27 + d];
-      v[j] = w;
-    }
-    uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-    *reinterpret_cast<uint4*>(Bs + d * B_D + g * B_KG + (n >> 3) * kCore + (n & 7) * 16) = pk;
   }
   int ix = 0, iy = 0, iz = 0;
   if (s < M) {
@@ -188,13 +175,34 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
       ok = mma_wait(bar, unsigned(c - 1) & 1u) && ok;
       fence_after_sync();
     }
-    // this thread's row of the A tiles of offsets d = 3c + dl: dx = c / 3 - 1, dy = c % 3 - 1, dz = dl - 1
+    // the chunk's weights: 16-byte rows of 8 channels, zero past cin / cout
+    for (int q = tid; q < kChunk * KG * NP; q += kThreads) {
+      const int dl = q / (KG * NP), rem = q % (KG * NP), g = rem / NP, n = rem % NP;
+      const int d = c * kChunk + dl;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = 8 * g + j;
+        float w = 0.f;
+        if (n < a.cout && k < a.cin)
+          w = a.transposed ? a.w[(size_t(k) * a.cout + n) * 27 + (26 - d)] : a.w[(size_t(n) * a.cin + k) * 27 + d];
+        v[j] = w;
+      }
+      uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                            pack_bf16(v[6], v[7]));
+      *reinterpret_cast<uint4*>(Bs + dl * B_D + g * B_KG + (n >> 3) * kCore + (n & 7) * 16) = pk;
+    }
+    // this thread's half of its row of the A tiles of offsets d = 3c + dl:
+    // dx = c / 3 - 1, dy = c % 3 - 1, dz = dl - 1; (offset, channel group)
+    // pairs alternate between the row's two threads
+#pragma unroll
     for (int dl = 0; dl < kChunk; ++dl) {
       const int q = s < M ? (wrapi(ix + c / 3 - 1, a.nx) * a.ny + wrapi(iy + c % 3 - 1, a.ny)) * a.nz +
                                 wrapi(iz + dl - 1, a.nz)
                           : 0;
 #pragma unroll
       for (int g = 0; g < KG; ++g) {
+        if (((dl * KG + g) & 1) != part) continue;
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
         }
         uint4 pk = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                               pack_bf16(v[6], v[7]));
-        *reinterpret_cast<uint4*>(As + dl * A_D + g * A_KG + (tid >> 3) * kCore + (tid & 7) * 16) = pk;
+        *reinterpret_cast<uint4*>(As + dl * A_D + g * A_KG + (row >> 3) * kCore + (row & 7) * 16) = pk;
       }
     }
     fence_async_smem();
@@ -213,11 +221,10 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
       fence_after_sync();
       const unsigned a0 = smem_u32(As), b0 = smem_u32(Bs);
       for (int dl = 0; dl < kChunk; ++dl) {
-        const int d = c * kChunk + dl;
 #pragma unroll
         for (int kb = 0; kb < CINP / 16; ++kb) {
           const uint64_t ad = smem_desc(a0 + dl * A_D + 2 * kb * A_KG, A_KG, kCore);
-          const uint64_t bd = smem_desc(b0 + d * B_D + 2 * kb * B_KG, B_KG, kCore);
+          const uint64_t bd = smem_desc(b0 + dl * B_D + 2 * kb * B_KG, B_KG, kCore);
           mma_bf16(tmem, ad, bd, IDESC, (c | dl | kb) != 0);
         }
       }
@@ -230,7 +237,8 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
     mma_wait(bar, unsigned(NCH - 1) & 1u);
   }
   fence_after_sync();
-  // epilogue: lane = row of this warp's quarter of the accumulator
+  // epilogue (warps 0-3): lane = row of this warp's quarter of the accumulator
+  if (warp < kRows / 32) {
   float v[NP];
   const unsigned taddr = tmem + (unsigned(32 * warp) << 16);
   tmem_ld16(taddr, v);
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
       }
     }
   }
+  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(kRows) conv_tc_kernel(const ConvTcArgs a) {
 template <int CINP, int NP>
 cudaError_t launch_tc(const ConvTcArgs& a, int batch, cudaStream_t s) {
   // operands, tensor-memory slot and barrier, alignment slack
-  constexpr size_t bytes = 27 * size_t(CINP / 8) * (NP / 8) * kCore + kChunk * size_t(CINP / 8) * (kRows / 8) * kCore +
+  constexpr size_t bytes = kChunk * size_t(CINP / 8) * (NP / 8) * kCore + kChunk * size_t(CINP / 8) * (kRows / 8) * kCore +
                            16 + 1024;
   static bool configured = false;
   if (!configured) {
@@ -274,7 +283,7 @@ cudaError_t launch_tc(const ConvTcArgs& a, int batch, cudaStream_t s) {
   }
   const int M = a.nx * a.ny * a.nz;
   dim3 grid(unsigned((M + kRows - 1) / kRows), unsigned(batch));
-  conv_tc_kernel<CINP, NP><<<grid, kRows, bytes, s>>>(a);
+  conv_tc_kernel<CINP, NP><<<grid, kThreads, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
