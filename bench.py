@@ -159,6 +159,14 @@ def profiled_traffic(shape):
     return float(kv["mixed_bytes_per_state_site"])
 
 
+def host_ram_gb():
+    """Physical memory of the host in GB (None where the platform does not say)."""
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 1e9
+    except (ValueError, OSError, AttributeError):
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -673,7 +681,8 @@ def cpu_oracle_rate(wl, dt, seconds, max_states=2048, scheme="AB4AM5", A=1.0, as
     for _ in range(k):
         st = step(st)
     sec = time.perf_counter() - t0
-    return {"value": n * lat.M * k / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "n": n,
+    return {"value": n * lat.M * k / sec, "unit": UNIT, "cores": os.cpu_count(), "ram_gb": host_ram_gb(),
+            "kind": "oracle", "n": n,
             "sample": f"{n} of the workload's states on the same {shape[0]}x{shape[1]}x{shape[2]} trap, {k} {scheme} "
                       f"steps after a stationary start, {sec:.1f} s"}
 
@@ -702,7 +711,8 @@ def reference_arm(args, wl):
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(args, wl, "fp64 oracle (CPU)"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "ram_gb": host_ram_gb(),
+                             "kind": "oracle",
                              "sample": f"{n} states of the workload per step, {args.steps} steps, {sec:.1f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
